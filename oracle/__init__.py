@@ -1,0 +1,220 @@
+"""CPU oracle for the persistent-homology path of arXiv:1708.04710 -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may import this package. The product library never loads it, and the two
+share no code: the oracle is plain sequential C (``ph_oracle.c``) plus the numpy glue below.
+
+Functions (indices are 0-based global filtration positions, -1 means "none"):
+
+* ``vr_build``        Vietoris-Rips filtration and boundary matrix (Sec. 2.2-2.3).
+* ``boundary_from_simplices``  boundary matrix of an explicit, compatibly ordered complex.
+* ``beta``            beta of Definition 4 via Algorithm 4.
+* ``reduce_std``      Algorithm 1 (optionally with V, R = D V).
+* ``reduce_twist``    Algorithm 3 (clearing).
+* ``reduce_pms``      Algorithm 2, pass by pass (Phase 0 / I / II, clearing, Cor. 10 zero case).
+* ``pairs_and_essential``  the partition Pos / Neg / Ess of Sec. 2.3 from lowstar (Lemma 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "ph_oracle.c"
+_LIB_PATH = _HERE / "libph_oracle.so"
+_lib = None
+
+PS_FIELDS = ("active", "new_pivots", "zero_final", "cor10", "cleared", "targets", "adds",
+             "xors", "ess_est")
+
+
+def build_lib(force: bool = False) -> Path:
+    """Compile the oracle with the host C compiler (no GPU involved)."""
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", str(_SRC), "-o",
+                               str(tmp)])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build_lib()
+        L = ctypes.CDLL(str(_LIB_PATH))
+        P = ctypes.c_void_p
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        L.orc_vr_build.argtypes = [P, i32, i32, i32, i64, ctypes.POINTER(P)]
+        L.orc_vr_build.restype = ctypes.c_int
+        L.orc_complex_size.argtypes = [P]
+        L.orc_complex_size.restype = i64
+        L.orc_complex_nnz.argtypes = [P]
+        L.orc_complex_nnz.restype = i64
+        L.orc_complex_export.argtypes = [P, P, P, P, P, P]
+        L.orc_complex_export.restype = None
+        L.orc_complex_free.argtypes = [P]
+        L.orc_complex_free.restype = None
+        L.orc_beta.argtypes = [i64, P, P, P]
+        L.orc_beta.restype = ctypes.c_int
+        L.orc_reduce_std.argtypes = [i64, P, P, P, P, P, P]
+        L.orc_reduce_std.restype = ctypes.c_int
+        L.orc_reduce_twist.argtypes = [i64, P, P, P, P, P]
+        L.orc_reduce_twist.restype = ctypes.c_int
+        L.orc_reduce_pms.argtypes = [i64, P, P, P, P, i32, i32, i32, P, P, P, P, P]
+        L.orc_reduce_pms.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Complex(dict):
+    """Filtration + boundary matrix: keys dim, diam2, verts (m x 4), colptr, rows."""
+
+    @property
+    def m(self) -> int:
+        return int(self["dim"].shape[0])
+
+
+def vr_build(coords: np.ndarray, max_dim: int, max_diam2: int = -1) -> Complex:
+    """Vietoris-Rips filtration of int32 grid points (Sec. 2.2) with its boundary matrix."""
+    L = _load()
+    c = np.ascontiguousarray(coords, dtype=np.int32)
+    n, D = c.shape
+    h = ctypes.c_void_p()
+    rc = L.orc_vr_build(_ptr(c), n, D, max_dim, int(max_diam2), ctypes.byref(h))
+    if rc != 0:
+        raise RuntimeError(f"orc_vr_build failed: {rc}")
+    try:
+        m = L.orc_complex_size(h)
+        nnz = L.orc_complex_nnz(h)
+        K = Complex(dim=np.empty(m, np.int32), diam2=np.empty(m, np.int64),
+                    verts=np.empty((m, 4), np.int32), colptr=np.empty(m + 1, np.int64),
+                    rows=np.empty(max(nnz, 1), np.int32))
+        L.orc_complex_export(h, _ptr(K["dim"]), _ptr(K["diam2"]), _ptr(K["verts"]),
+                             _ptr(K["colptr"]), _ptr(K["rows"]))
+        K["rows"] = K["rows"][:nnz]
+    finally:
+        L.orc_complex_free(h)
+    return K
+
+
+def boundary_from_simplices(simplices) -> Complex:
+    """Boundary matrix (Eq. def:boundary_matrix) of an explicit complex given as a list of
+    vertex tuples in a compatible order (every face listed before its cofaces)."""
+    index = {}
+    dims, colptr, rows = [], [0], []
+    verts = np.full((len(simplices), 4), -1, np.int32)
+    for j, s in enumerate(simplices):
+        s = tuple(sorted(s))
+        index[s] = j
+        d = len(s) - 1
+        dims.append(d)
+        if len(s) <= 4:
+            verts[j, :len(s)] = s
+        if d > 0:
+            faces = sorted(index[s[:k] + s[k + 1:]] for k in range(len(s)))
+            rows.extend(faces)
+        colptr.append(len(rows))
+    return Complex(dim=np.array(dims, np.int32), diam2=np.zeros(len(simplices), np.int64),
+                   verts=verts, colptr=np.array(colptr, np.int64),
+                   rows=np.array(rows, np.int32))
+
+
+def beta(K: Complex) -> np.ndarray:
+    L = _load()
+    out = np.empty(K.m, np.int32)
+    rc = L.orc_beta(K.m, _ptr(K["colptr"]), _ptr(K["rows"]), _ptr(out))
+    if rc != 0:
+        raise RuntimeError(rc)
+    return out
+
+
+def reduce_std(K: Complex, track_v: bool = False):
+    """Algorithm 1. Returns (low, stats[adds, xors]) or, with track_v, (low, stats, R, V)."""
+    L = _load()
+    m = K.m
+    low = np.empty(m, np.int32)
+    st = np.zeros(2, np.int64)
+    R = V = None
+    if track_v:
+        R = np.zeros((m, m), np.uint8)
+        V = np.zeros((m, m), np.uint8)
+    rc = L.orc_reduce_std(m, _ptr(K["colptr"]), _ptr(K["rows"]), _ptr(low), _ptr(st),
+                          _ptr(R) if track_v else None, _ptr(V) if track_v else None)
+    if rc != 0:
+        raise RuntimeError(rc)
+    return (low, st, R, V) if track_v else (low, st)
+
+
+def reduce_twist(K: Complex):
+    """Algorithm 3. Returns (low, stats[adds, xors, cleared])."""
+    L = _load()
+    low = np.empty(K.m, np.int32)
+    st = np.zeros(3, np.int64)
+    rc = L.orc_reduce_twist(K.m, _ptr(K["colptr"]), _ptr(K["rows"]), _ptr(K["dim"]), _ptr(low),
+                            _ptr(st))
+    if rc != 0:
+        raise RuntimeError(rc)
+    return low, st
+
+
+class PmsResult(dict):
+    """low, passes, stats (rows per executed pass, columns PS_FIELDS), ess_est, proven,
+    converged."""
+
+    def __getattr__(self, k):
+        return self[k]
+
+
+def reduce_pms(K: Complex, max_passes: int = 100000, strict: bool = False, cor10: bool = True,
+               beta_arr: np.ndarray | None = None) -> PmsResult:
+    """Algorithm 2, pass by pass (see ph_oracle.c for the pass definition)."""
+    L = _load()
+    m = K.m
+    b = beta(K) if beta_arr is None else np.ascontiguousarray(beta_arr, np.int32)
+    low = np.empty(m, np.int32)
+    ps = np.zeros((max_passes + 1, len(PS_FIELDS)), np.int64)
+    npass = ctypes.c_int32(0)
+    ess = np.zeros(max(m, 1), np.uint8)
+    proven = np.zeros(max(m, 1), np.uint8)
+    rc = L.orc_reduce_pms(m, _ptr(K["colptr"]), _ptr(K["rows"]), _ptr(K["dim"]), _ptr(b),
+                          max_passes, int(strict), int(cor10), _ptr(low), _ptr(ps),
+                          ctypes.byref(npass), _ptr(ess), _ptr(proven))
+    if rc < 0:
+        raise RuntimeError(rc)
+    p = npass.value
+    return PmsResult(low=low, passes=p, stats=ps[:p + 1], ess_est=ess[:m].astype(bool),
+                     proven=proven[:m].astype(bool), converged=(rc == 0))
+
+
+def pairs_and_essential(low: np.ndarray, dim: np.ndarray):
+    """Pairs (lowstar(j), j) of negative columns and the essential set (Sec. 2.3, Lemma 1).
+
+    Returns (pairs int64 (P, 2) sorted by death index, essential int64 sorted)."""
+    low = np.asarray(low, np.int64)
+    deaths = np.nonzero(low >= 0)[0]
+    births = low[deaths]
+    pairs = np.stack([births, deaths], axis=1) if deaths.size else np.zeros((0, 2), np.int64)
+    paired = np.zeros(low.shape[0], bool)
+    paired[deaths] = True
+    paired[births] = True
+    essential = np.nonzero(~paired)[0].astype(np.int64)
+    return pairs.astype(np.int64), essential
+
+
+def persistence_summary(K: Complex, low: np.ndarray):
+    """Per dimension: (#finite pairs by birth dim, #essential by dim)."""
+    pairs, ess = pairs_and_essential(low, K["dim"])
+    maxd = int(K["dim"].max()) if K.m else 0
+    npairs = np.bincount(K["dim"][pairs[:, 0]], minlength=maxd + 1) if len(pairs) else np.zeros(
+        maxd + 1, np.int64)
+    ness = np.bincount(K["dim"][ess], minlength=maxd + 1)
+    return npairs, ness

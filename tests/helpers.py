@@ -1,0 +1,144 @@
+"""Test-side checks that are independent of both the oracle and the CUDA path.
+
+Nothing here reduces a boundary matrix the way the paper's algorithms do; these are the
+textbook characterisations the tests pin the oracle against:
+
+* GF(2) ranks by Gaussian elimination on Python-int bit rows.
+* The pairing lemma through the rank function (Edelsbrunner-Harer, Computational Topology,
+  VII.1): lowstar(j) = i iff r(i,j) - r(i+1,j) - r(i,j-1) + r(i+1,j-1) = 1, where r(a, b) is the
+  rank of the lower-left block D[a:, :b+1].
+* A reduction by randomly chosen left-to-right additions (any earlier column with the same low),
+  whose low must agree with every other reduction (Sec. 2.3: lowstar does not depend on the
+  reduction).
+"""
+from __future__ import annotations
+
+import itertools
+import random
+
+import numpy as np
+
+
+def dense_boundary(K) -> np.ndarray:
+    m = K.m
+    D = np.zeros((m, m), np.uint8)
+    cp, rows = K["colptr"], K["rows"]
+    for j in range(m):
+        D[rows[cp[j]:cp[j + 1]], j] = 1
+    return D
+
+
+def _insert(basis: dict, v: int) -> bool:
+    while v:
+        h = v.bit_length() - 1
+        b = basis.get(h)
+        if b is None:
+            basis[h] = v
+            return True
+        v ^= b
+    return False
+
+
+def gf2_rank(M: np.ndarray) -> int:
+    basis: dict = {}
+    r = 0
+    for row in np.asarray(M, np.uint8):
+        v = int("".join("1" if x else "0" for x in row[::-1]) or "0", 2)
+        r += _insert(basis, v)
+    return r
+
+
+def rank_pairing(D: np.ndarray) -> np.ndarray:
+    """lowstar from the rank function alone (no column operations)."""
+    m = D.shape[0]
+    # r[a][b] for a in 0..m, b in -1..m-1 (stored at b+1)
+    r = np.zeros((m + 1, m + 1), np.int64)
+    row_bits = []
+    for a in range(m):
+        v = 0
+        for j in np.nonzero(D[a])[0]:
+            v |= 1 << int(j)
+        row_bits.append(v)
+    for b in range(m):
+        mask = (1 << (b + 1)) - 1
+        basis: dict = {}
+        rank = 0
+        for a in range(m - 1, -1, -1):
+            rank += _insert(basis, row_bits[a] & mask)
+            r[a, b + 1] = rank
+    low = np.full(m, -1, np.int64)
+    for j in range(m):
+        for i in range(m):
+            x = r[i, j + 1] - r[i + 1, j + 1] - r[i, j] + r[i + 1, j]
+            if x == 1:
+                low[j] = i
+    return low
+
+
+def random_reduction(D: np.ndarray, seed: int) -> np.ndarray:
+    """Reduce by random valid left-to-right additions until low is injective."""
+    rng = random.Random(seed)
+    m = D.shape[0]
+    cols = [set(np.nonzero(D[:, j])[0].tolist()) for j in range(m)]
+    while True:
+        by_low: dict = {}
+        for j in range(m):
+            if cols[j]:
+                by_low.setdefault(max(cols[j]), []).append(j)
+        pairs = [(a, b) for js in by_low.values() if len(js) > 1
+                 for a, b in itertools.combinations(js, 2)]
+        if not pairs:
+            break
+        j0, j = rng.choice(pairs)
+        cols[j] ^= cols[j0]
+    return np.array([max(c) if c else -1 for c in cols], np.int64)
+
+
+def betti_by_rank(K) -> list:
+    """b_p = dim C_p - rank d_p - rank d_{p+1} over F2 (Sec. 2.1)."""
+    D = dense_boundary(K)
+    dims = K["dim"]
+    maxd = int(dims.max())
+    ranks = {}
+    for p in range(1, maxd + 1):
+        cols = np.nonzero(dims == p)[0]
+        rows = np.nonzero(dims == p - 1)[0]
+        ranks[p] = gf2_rank(D[np.ix_(rows, cols)].T) if len(cols) and len(rows) else 0
+    return [int((dims == p).sum()) - ranks.get(p, 0) - ranks.get(p + 1, 0)
+            for p in range(maxd + 1)]
+
+
+def closure(facets):
+    out = set()
+    for f in facets:
+        f = tuple(sorted(f))
+        for k in range(1, len(f) + 1):
+            out.update(itertools.combinations(f, k))
+    return out
+
+
+def ordered_by_dim_lex(simplices):
+    return sorted(simplices, key=lambda s: (len(s), s))
+
+
+def random_compatible_order(simplices, seed: int):
+    """A random filtration order: random values, each simplex above all its faces."""
+    rng = random.Random(seed)
+    val = {}
+    for s in sorted(simplices, key=len):
+        base = max((val[s[:k] + s[k + 1:]] for k in range(len(s))), default=0) if len(s) > 1 else 0
+        val[s] = base + rng.randint(0, 3)
+    return sorted(simplices, key=lambda s: (val[s], len(s), rng.random()))
+
+
+def icosahedron_facets():
+    phi = (1 + 5 ** 0.5) / 2
+    V = []
+    for a in (-1, 1):
+        for b in (-1, 1):
+            V += [(0, a, b * phi), (a, b * phi, 0), (b * phi, 0, a)]
+    V = np.array(V)
+    d = np.linalg.norm(V[:, None] - V[None], axis=2)
+    adj = np.isclose(d, 2.0)
+    return [t for t in itertools.combinations(range(12), 3)
+            if adj[t[0], t[1]] and adj[t[0], t[2]] and adj[t[1], t[2]]]

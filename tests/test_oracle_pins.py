@@ -1,0 +1,232 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+* Betti numbers of known triangulations (Sec. 2.1) and of complete skeleta (closed form).
+* The pairing lemma through GF(2) ranks, on every tiny complex (no column operations).
+* Order independence of lowstar (Sec. 2.3): Algorithms 1, 2 and 3 and random valid reductions.
+* R = D V with V upper-unitriangular and R reduced.
+* Theorem 5 (beta bounds), Lemma 11 (essential estimate), Theorem 8 (progress each pass).
+* Vietoris-Rips filtration properties (Sec. 2.2): counts, exact diameters, compatible order,
+  prefix property of every sublevel set, faces in the boundary matrix.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import pointclouds as pc
+from helpers import (betti_by_rank, closure, dense_boundary, gf2_rank, icosahedron_facets,
+                     ordered_by_dim_lex, random_compatible_order, random_reduction, rank_pairing)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _triangulations():
+    with open(os.path.join(GOLDEN, "triangulations.json")) as f:
+        data = json.load(f)
+    data.pop("_about")
+    data["icosahedron"] = {"facets": icosahedron_facets(), "betti": [1, 0, 1]}
+    return data
+
+
+TRI = _triangulations()
+
+
+def _essential_per_dim(orc, K, low):
+    _, ess = orc.pairs_and_essential(low, K["dim"])
+    maxd = int(K["dim"].max())
+    return np.bincount(K["dim"][ess], minlength=maxd + 1).tolist()
+
+
+@pytest.mark.parametrize("name", sorted(TRI))
+def test_triangulation_is_closed_manifold_or_disc(name):
+    # sanity of the fixture itself: Euler characteristic matches the stated Betti numbers
+    S = closure(TRI[name]["facets"])
+    chi = sum((-1) ** (len(s) - 1) for s in S)
+    b = TRI[name]["betti"]
+    assert chi == sum((-1) ** p * x for p, x in enumerate(b))
+
+
+@pytest.mark.parametrize("name", sorted(TRI))
+@pytest.mark.parametrize("order_seed", [None, 1, 2, 3])
+def test_betti_of_triangulations(orc, name, order_seed):
+    S = closure(TRI[name]["facets"])
+    order = ordered_by_dim_lex(S) if order_seed is None else random_compatible_order(S, order_seed)
+    K = orc.boundary_from_simplices(order)
+    expect = TRI[name]["betti"]
+    assert betti_by_rank(K) == expect  # independent rank computation agrees with the fixture
+    for low in (orc.reduce_std(K)[0], orc.reduce_twist(K)[0], orc.reduce_pms(K).low,
+                orc.reduce_pms(K, strict=True).low, orc.reduce_pms(K, cor10=False).low):
+        assert _essential_per_dim(orc, K, low) == expect
+
+
+@pytest.mark.parametrize("n,k", [(6, 1), (7, 2), (9, 2), (8, 3), (40, 2)])
+def test_complete_skeleton_closed_form(orc, n, k):
+    # k-skeleton of the (n-1)-simplex: b_0 = 1, b_k = C(n-1, k+1), all others 0
+    x = pc.random_cloud(n, 3, seed=n + k)
+    K = orc.vr_build(x, k)
+    assert K.m == sum(math.comb(n, d + 1) for d in range(k + 1))
+    expect = [1] + [0] * (k - 1) + [math.comb(n - 1, k + 1)] if k >= 1 else [1]
+    for low in (orc.reduce_twist(K)[0], orc.reduce_pms(K).low):
+        assert _essential_per_dim(orc, K, low) == expect
+
+
+def _tiny_complexes(orc):
+    out = []
+    for seed, (n, D, k) in enumerate([(7, 2, 2), (8, 3, 2), (6, 4, 3), (9, 2, 1)]):
+        out.append(("vr%d" % seed, orc.vr_build(pc.random_cloud(n, D, seed), k)))
+    x = pc.lattice_cloud(8, 2, seed=5, side=3)  # repeated points and many equal diameters
+    out.append(("lattice", orc.vr_build(x, 2)))
+    c = pc.random_cloud(10, 2, seed=9)
+    K = orc.vr_build(c, 2)
+    cut = int(np.quantile(K["diam2"][K["dim"] == 1], 0.5))
+    out.append(("truncated", orc.vr_build(c, 2, cut)))
+    for name in ("torus_7_vertex", "rp2_6_vertex", "octahedron"):
+        S = closure(TRI[name]["facets"])
+        out.append((name, orc.boundary_from_simplices(random_compatible_order(S, 11))))
+    return out
+
+
+def test_rank_function_pairing(orc):
+    for name, K in _tiny_complexes(orc):
+        D = dense_boundary(K)
+        assert K.m <= 120, name
+        expect = rank_pairing(D)
+        low_std = orc.reduce_std(K)[0]
+        assert np.array_equal(low_std, expect), name
+        assert np.array_equal(orc.reduce_twist(K)[0], expect), name
+        assert np.array_equal(orc.reduce_pms(K).low, expect), name
+        assert np.array_equal(orc.reduce_pms(K, strict=True).low, expect), name
+
+
+def test_order_independence_random_reductions(orc):
+    for name, K in _tiny_complexes(orc):
+        D = dense_boundary(K)
+        low = orc.reduce_std(K)[0]
+        for seed in range(3):
+            assert np.array_equal(random_reduction(D, seed), low), (name, seed)
+
+
+def test_R_equals_D_V(orc):
+    for name, K in _tiny_complexes(orc):
+        D = dense_boundary(K).astype(np.int64)
+        low, st, R, V = orc.reduce_std(K, track_v=True)
+        V = V.astype(np.int64)
+        assert np.array_equal((D @ V) % 2, R.astype(np.int64)), name
+        assert np.array_equal(np.triu(V), V) and np.all(np.diag(V) == 1), name
+        lows = [int(np.nonzero(R[:, j])[0].max()) if R[:, j].any() else -1 for j in range(K.m)]
+        assert np.array_equal(np.array(lows), low), name
+        nz = [x for x in lows if x >= 0]
+        assert len(nz) == len(set(nz)), name  # reduced: low injective on its support
+
+
+def test_beta_definition_and_theorem5(orc):
+    for name, K in _tiny_complexes(orc) + [("circle40", orc.vr_build(pc.circle40(), 2))]:
+        D = dense_boundary(K) if K.m <= 2000 else None
+        beta = orc.beta(K)
+        if D is not None:  # Definition 3 / 4 straight from the matrix
+            left = np.array([int(np.nonzero(D[i])[0].min()) if D[i].any() else -1
+                             for i in range(K.m)])
+            expect = np.full(K.m, -1)
+            for i in range(K.m):
+                if left[i] >= 0:
+                    expect[left[i]] = max(expect[left[i]], i)
+            assert np.array_equal(beta, expect), name
+        low0 = np.array([K["rows"][K["colptr"][j + 1] - 1] if K["colptr"][j + 1] > K["colptr"][j]
+                         else -1 for j in range(K.m)])
+        lowstar = orc.reduce_std(K)[0]
+        assert np.all(beta <= lowstar) and np.all(lowstar <= low0), name  # P.5
+        assert np.all(lowstar[beta >= 0] >= 0), name  # P.3: beta_j > 0 => negative
+
+
+def test_pms_per_pass_invariants(orc):
+    K = orc.vr_build(pc.circle40(), 2)
+    lowstar = orc.reduce_std(K)[0]
+    _, ess = orc.pairs_and_essential(lowstar, K["dim"])
+    beta = orc.beta(K)
+    full = orc.reduce_pms(K)
+    assert full.converged and np.array_equal(full.low, lowstar)
+    prev = None
+    for k in range(full.passes + 1):
+        r = orc.reduce_pms(K, max_passes=k)
+        assert r.converged == (k >= full.passes)
+        low = r.low
+        assert np.all(beta <= lowstar) and np.all(lowstar <= low)  # Thm 5 P.5, every pass
+        assert np.array_equal(low[r.proven], lowstar[r.proven])  # pivots are reduced
+        assert np.all(r.ess_est[ess])  # Lemma 11: Ess is contained in E^l
+        if prev is not None:
+            assert np.all(low <= prev)  # low never increases
+            # Thm 8: a pass that found collisions changed something
+            st = dict(zip(orc.PS_FIELDS, r.stats[k - 1]))
+            assert st["targets"] == 0 or (st["new_pivots"] + st["adds"] + st["cor10"]
+                                          + st["zero_final"] + st["cleared"]) > 0
+        prev = low
+
+
+def test_vr_filtration_properties(orc):
+    for (n, D, k, cut) in [(9, 2, 2, -1), (8, 5, 3, -1), (12, 3, 3, None), (10, 2, 2, None)]:
+        x = pc.random_cloud(n, D, seed=n * 10 + D)
+        if cut is None:
+            d2 = ((x[:, None, :].astype(np.int64) - x[None, :, :]) ** 2).sum(-1)
+            cut = int(np.median(d2[np.triu_indices(n, 1)]))
+        K = orc.vr_build(x, k, cut)
+        dims, diam2, verts = K["dim"], K["diam2"], K["verts"]
+        # every simplex appears once with its exact diameter, and nothing above the cut
+        seen = set()
+        for j in range(K.m):
+            v = tuple(verts[j, :dims[j] + 1])
+            assert v == tuple(sorted(v)) and v not in seen
+            seen.add(v)
+            pts = x[list(v)].astype(np.int64)
+            dd = max([int(((pts[a] - pts[b]) ** 2).sum()) for a, b in
+                      itertools.combinations(range(len(v)), 2)], default=0)
+            assert dd == diam2[j]
+            assert cut < 0 or dd <= cut
+        expect = sum(1 for d in range(k + 1) for s in itertools.combinations(range(n), d + 1)
+                     if all(((x[a].astype(np.int64) - x[b]) ** 2).sum() <= (cut if cut >= 0
+                            else 1 << 62) for a, b in itertools.combinations(s, 2)))
+        assert K.m == expect
+        # compatible ordering: (diam2, dim, lex) non-decreasing, faces before cofaces
+        keys = [(int(diam2[j]), int(dims[j]), tuple(verts[j, :dims[j] + 1])) for j in range(K.m)]
+        assert keys == sorted(keys)
+        index = {tuple(verts[j, :dims[j] + 1]): j for j in range(K.m)}
+        for j in range(K.m):
+            v = tuple(verts[j, :dims[j] + 1])
+            rows = K["rows"][K["colptr"][j]:K["colptr"][j + 1]]
+            faces = sorted(index[v[:i] + v[i + 1:]] for i in range(len(v))) if len(v) > 1 else []
+            assert list(rows) == faces and all(f < j for f in faces)
+        # every sublevel set {diam2 <= t} is a prefix of the order and a simplicial complex
+        for t in np.unique(diam2):
+            pre = np.nonzero(diam2 <= t)[0]
+            assert pre.max() == len(pre) - 1
+
+
+def test_euler_characteristic_vr(orc):
+    for seed in range(3):
+        x = pc.random_cloud(11, 3, seed)
+        K = orc.vr_build(x, 3, int(2.5 * 65536 ** 2))
+        ess = _essential_per_dim(orc, K, orc.reduce_pms(K).low)
+        chi = sum((-1) ** d * int((K["dim"] == d).sum()) for d in range(4))
+        assert chi == sum((-1) ** d * b for d, b in enumerate(ess))
+        assert ess == betti_by_rank(K)
+
+
+def test_counts_identity_and_pairs(orc):
+    K = orc.vr_build(pc.circle40(), 2)
+    low = orc.reduce_twist(K)[0]
+    pairs, ess = orc.pairs_and_essential(low, K["dim"])
+    assert K.m == 2 * len(pairs) + len(ess)
+    # Lemma 1: a negative simplex is paired with a positive one of one dimension lower
+    assert np.all(K["dim"][pairs[:, 0]] == K["dim"][pairs[:, 1]] - 1)
+    assert np.all(low[pairs[:, 0]] == -1)
+    assert np.all(K["diam2"][pairs[:, 0]] <= K["diam2"][pairs[:, 1]])
+
+
+def test_gf2_rank_helper_sanity():
+    # the helper itself: identity, a dependent row, and the all-ones 3x3 matrix
+    assert gf2_rank(np.eye(5, dtype=np.uint8)) == 5
+    assert gf2_rank(np.array([[1, 1, 0], [0, 1, 1], [1, 0, 1]], np.uint8)) == 2
+    assert gf2_rank(np.ones((3, 3), np.uint8)) == 1
