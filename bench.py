@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Throughput of the persistent-homology hot path: simplices reduced per second to full pairing.
+
+One step = the whole path on one synthetic workload: Vietoris-Rips filtration built on the
+device, Algorithm 2 reduction to full pairing, pairs and essential simplices extracted on the
+device. The default workload is the complete VR complex up to dimension 2 of 400 seeded points
+on the torus (R=2, r=1) in R^3 on the 2^-16 grid: 10,667,000 simplices.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (VR build + Algorithm 3, one core) on a bounded sample of
+the same workload. Under torchrun every rank reduces its own replica of the workload (a single
+filtration does not shard); value is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import pointclouds as pc  # noqa: E402
+
+METRIC = "simplices reduced/sec to full pairing (bit-exact vs oracle), passes, % HBM roofline"
+UNIT = "simplices/s"
+PEAKS = ROOT / "MEASURED_PEAKS.json"
+FALLBACK_HBM = 6800.0
+
+WORKLOADS = {
+    "torus400": dict(gen=pc.torus400, max_dim=2, max_diam2=-1,
+                     desc="complete VR <= dim 2, 400 points on the torus R=2 r=1 in R^3"),
+    "circle40": dict(gen=pc.circle40, max_dim=2, max_diam2=-1,
+                     desc="complete VR <= dim 2, 40 noisy points on the unit circle"),
+    "gauss8_120": dict(gen=pc.gauss8_120, max_dim=3, max_diam2=pc.GAUSS8_MAX_DIAM2,
+                       desc="VR <= dim 3, 120 points N(0, I_8), squared diameter <= 16"),
+}
+
+
+def _peak_hbm():
+    try:
+        return float(json.loads(PEAKS.read_text())["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def _profile_traffic(kernel: str, workload: str):
+    """dram bytes per launch of `kernel` recorded by the committed ncu summary, if any."""
+    p = ROOT / "profiles" / f"{kernel}_{workload}.md"
+    if not p.exists():
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", p.read_text())
+    return float(m.group(1)) if m else None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(n_sample: int):
+    """The oracle as it stands (VR build + Algorithm 3) on the first n_sample points of the
+    torus workload; returns (simplices, seconds)."""
+    import oracle
+
+    oracle.build_lib()
+    x = pc.torus400()[:n_sample]
+    t0 = time.perf_counter()
+    K = oracle.vr_build(x, 2)
+    oracle.reduce_twist(K)
+    return K.m, time.perf_counter() - t0
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n_sample = 200
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n_sample)
+    times, m = [], 0
+    for _ in range(args.steps):
+        m, t = cpu_oracle_sample(n_sample)
+        times.append(t)
+    total = sum(times)
+    value = m * len(times) / total
+    sample = (f"first {n_sample} of the 400 torus points: complete VR <= dim 2, m={m}; "
+              "oracle VR build + Algorithm 3 (twist), one core, per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "sample_points": n_sample, "m": m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="torus400", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1708_04710_gb300 import build as _build
+
+    _build.build()
+    import paper_1708_04710_gb300 as ph
+
+    wl = WORKLOADS[args.workload]
+    x = wl["gen"]()
+    coords = torch.from_numpy(x).to(dev)
+    ctx = ph.Context(collect_stats=True, time_kernels=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(c):
+        ctx.build_filtration(c, None, wl["max_dim"], wl["max_diam2"])
+        st = ctx.reduce()
+        ctx.pairs(0, on_device=True)
+        ctx.essential(0, on_device=True)
+        return st
+
+    for _ in range(max(args.warmup, 0)):
+        step(coords)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(dev.index) if rank == 0 else None
+    launches0 = ctx.kernel_launches()
+    total_ms, stats = 0.0, []
+    for _ in range(args.steps):
+        flush.fill_(1)  # write 256 MiB (> 129 MB L2) so no step starts from a warm L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(step(coords))
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    launches = ctx.kernel_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    m = ctx.m
+    value = m * args.steps * world / (total_ms / 1000.0)
+
+    # end to end through the public API with host buffers: H2D of the coordinates and D2H of
+    # every output (pairs and essential simplices) inside the timed region
+    x_pin = torch.from_numpy(x).pin_memory()
+    dev_buf = torch.empty_like(coords)
+    e2e_times, d2h = [], 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev_buf.copy_(x_pin, non_blocking=True)
+        ctx.build_filtration(dev_buf, None, wl["max_dim"], wl["max_diam2"])
+        ctx.reduce()
+        pr = ctx.pairs(0, on_device=False)
+        es = ctx.essential(0, on_device=False)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = sum(v.numel() * v.element_size() for v in list(pr.values()) + list(es.values()))
+    e2e_s = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = m * args.steps * world / float(e2e_s.item())
+
+    # parity of the last output against the stored oracle result
+    parity = None
+    gpath = ROOT / "tests" / "golden" / f"{args.workload}.json"
+    if gpath.exists():
+        g = json.loads(gpath.read_text())
+        b, d = pr["birth"].numpy(), pr["death"].numpy()
+        o = np.lexsort((b, d))
+        p = np.stack([b[o], d[o]], 1).astype(np.int64)
+        e = np.sort(es["idx"].numpy()).astype(np.int64)
+        parity = (hashlib.sha256(p.tobytes()).hexdigest() == g["pairs_sha"]
+                  and hashlib.sha256(e.tobytes()).hexdigest() == g["ess_sha"]
+                  and stats[-1]["passes"] == g["passes"])
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peak_hbm()
+    add_bytes = sum(s["add_bytes"] for s in stats)
+    add_ms = sum(s["ms_add"] for s in stats)
+    add_launches = sum(s["add_launches"] for s in stats)
+    achieved = (add_bytes / add_launches) / (add_ms / add_launches / 1e3) / 1e9 if add_ms else None
+    traffic = _profile_traffic("k_add", args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": traffic, "kernel": "k_add (Phase II column additions)",
+                "peak_kind": peak_kind,
+                "bytes_per_launch": add_bytes / max(add_launches, 1),
+                "ms_per_launch": add_ms / max(add_launches, 1),
+                "share_of_step": add_ms / total_ms * world if total_ms else None}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "m": m,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "l2": "256 MiB buffer written before every timed step"},
+            "passes": stats[-1]["passes"], "col_adds": stats[-1]["col_adds"],
+            "xors": stats[-1]["xors"], "bit_exact_vs_oracle": parity,
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches), "clocks": clk}
+    if world == 1 and not args.no_cpu_baseline:
+        n_sample = 250
+        ms, secs = cpu_oracle_sample(n_sample)
+        line["cpu_baseline"] = {
+            "value": ms / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_sample} of the 400 torus points: complete VR <= dim 2, m={ms}; "
+                      f"oracle VR build + Algorithm 3 (twist), {secs:.1f} s on one core"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

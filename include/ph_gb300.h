@@ -1,0 +1,203 @@
+/*
+ * ph_gb300.h -- C ABI of the GB300 parallel multi-scale reduction library.
+ *
+ * The library computes persistent homology of Vietoris-Rips filtrations over F2 following
+ * Mendoza-Smith & Tanner, "Parallel multi-scale reduction of persistent homology filtrations"
+ * (arXiv:1708.04710). Every step runs in the library's own CUDA kernels for sm_103a:
+ *   - the filtration (Sec. 2.2) and boundary matrix (Sec. 2.3) are built on the device;
+ *   - the boundary matrix is reduced by Algorithm 2 (Sec. 3.1), pass by pass;
+ *   - pairs and the essential set (Lemma 1, Eq. paired) are extracted on the device.
+ *
+ * Conventions
+ *   - Indices are 0-based; "none" is -1 (the paper is 1-based with 0 = none).
+ *   - A simplex's index is its position in the filtration of its own cloud, ordered by
+ *     (squared diameter, dimension, vertex tuple in lexicographic order): a compatible
+ *     ordering in the sense of Sec. 2.2.
+ *   - Coordinates are int32 grid units (value * 2^16); squared diameters are exact int64.
+ *   - `stream` arguments are cudaStream_t values passed as void*. All work of a context runs
+ *     on its stream. Calls return after enqueueing, except where a host-visible count or
+ *     host buffer is produced (those synchronise the stream).
+ *   - Pointers documented as "device" must be device (or managed) memory of the context's
+ *     device; "host" pointers are ordinary host memory.
+ *   - Every entry point returns an int status (PH_OK = 0, PH_NOT_CONVERGED = 1, negative on
+ *     error). No C++ exception crosses the ABI and no kernel traps; the text of the last error
+ *     of a context is available from ph_last_error.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PH_GB300_H
+#define PH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PH_OK = 0,
+  PH_NOT_CONVERGED = 1, /* max_passes reached; the state is a valid partial reduction */
+  PH_ERR_INVALID = -1,  /* bad argument or call order */
+  PH_ERR_ALLOC = -2,    /* device allocation failed */
+  PH_ERR_CUDA = -3,     /* a CUDA call failed (message in ph_last_error) */
+  PH_ERR_CAPACITY = -4  /* a size limit of the library was exceeded */
+};
+
+typedef struct ph_ctx ph_ctx;
+
+/* Device memory provider. alloc returns device memory of at least `bytes` bytes usable on
+ * `stream`, or NULL on failure; free releases it. Both are called from the thread that calls
+ * the library. With a NULL provider the library uses cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user, void* stream);
+  void (*free)(void* ptr, size_t bytes, void* user, void* stream);
+  void* user;
+} ph_allocator;
+
+typedef struct {
+  /* 1: Phase II adds only proven pivots, the rule printed in Algorithm 2.
+   * 0 (default): adds the left-most column with the same low, proven or not; both are
+   * left-to-right additions that strictly lower the target's low, so lowstar is the same
+   * (Sec. 2.3: lowstar does not depend on the reduction) and only pass counts differ. */
+  int32_t strict_phase2;
+  /* 1 (default): zero case of Corollary 10 -- a column with beta_j = 0 whose candidate rows
+   * (all rows of K_{d-1} up to low(j)) are all known to be paired is set to zero. */
+  int32_t use_cor10;
+  /* threads per block of the per-column kernels (0 = library default, 256) */
+  int32_t block_threads;
+  /* columns whose merged length exceeds this use the warp-cooperative symmetric difference;
+   * shorter ones are merged by one thread (0 = library default) */
+  int32_t warp_merge_min;
+  /* 1: per-pass counters are collected (column additions, XORs, pivots, ...) */
+  int32_t collect_stats;
+  /* 1: the pass loop runs inside one CUDA graph whose conditional while node reads a device
+   * flag, so no host round trip happens per pass (0 = host-driven loop, the default) */
+  int32_t use_graph;
+  /* 1: CUDA events time every launch of the Phase II addition kernel (ph_stats.ms_add) */
+  int32_t time_kernels;
+} ph_opts;
+
+/* Per-pass counters (rows of ph_get_pass_stats), in this order. */
+enum {
+  PH_PS_ACTIVE = 0,    /* active columns at the start of the pass */
+  PH_PS_NEW_PIVOTS,    /* columns proven reduced in this pass (Thm 5 test or Phase I) */
+  PH_PS_ZERO_FINAL,    /* active columns found empty (positive) */
+  PH_PS_COR10,         /* columns set to zero by the zero case of Corollary 10 */
+  PH_PS_CLEARED,       /* active columns set to zero by clearing (Lemma 1) */
+  PH_PS_TARGETS,       /* active columns whose low collides with an earlier column */
+  PH_PS_ADDS,          /* column additions done */
+  PH_PS_XORS,          /* nontrivial scalar XORs, |target union source| (Sec. 4.1) */
+  PH_PS_COPIED,        /* rows moved without an addition (survivors and new pivots) */
+  PH_PS_N
+};
+
+typedef struct {
+  int32_t passes;      /* passes that found collisions (iterations of Algorithm 2) */
+  int32_t status;      /* PH_OK or PH_NOT_CONVERGED */
+  int64_t m;           /* simplices in the context */
+  int64_t col_adds;    /* column additions, all passes (needs collect_stats) */
+  int64_t xors;        /* nontrivial XORs, all passes (needs collect_stats) */
+  int64_t alg_bytes;   /* algorithmic bytes of the reduction (needs collect_stats) */
+  int64_t add_bytes;   /* algorithmic bytes of the addition kernel (needs collect_stats):
+                          8 per XOR + 8 per copied row + 40 per active column per pass */
+  int64_t add_launches;/* launches of the addition kernel */
+  double ms_add;       /* summed duration of those launches (needs time_kernels) */
+} ph_stats;
+
+/* Fills `opts` with the defaults described above. */
+void ph_default_opts(ph_opts* opts);
+
+/* Creates a context bound to the current CUDA device and to `stream` (NULL = legacy default
+ * stream). `opts` and `alloc` may be NULL (defaults). On success *out owns all library
+ * workspace until ph_destroy. */
+int ph_create(ph_ctx** out, const ph_opts* opts, const ph_allocator* alloc, void* stream);
+
+/* Releases the context and all of its device memory. NULL is ignored. */
+void ph_destroy(ph_ctx* ctx);
+
+/* Builds the Vietoris-Rips filtrations (Sec. 2.2, f_r(sigma) = 1{diam(sigma) <= 2r}) of
+ * n_clouds point clouds, and the boundary matrix (Sec. 2.3) and beta (Definition 4,
+ * Algorithm 4) of each.
+ *   coords        device int32 [N][D], row-major, the clouds stored back to back.
+ *   cloud_offsets host int64 [n_clouds + 1]: cloud c owns points [off[c], off[c+1]).
+ *                 NULL with n_clouds == 1 means one cloud of N = coords rows given by
+ *                 n_points.
+ *   n_points      total number of points N (rows of coords).
+ *   D             coordinate dimension, 1..16.
+ *   max_dim       largest simplex dimension, 1..3.
+ *   max_diam2     simplices with squared diameter above this are left out; < 0 keeps all.
+ *   m_out         host, optional: total number of simplices over all clouds.
+ * Limits: 1..65535 points per cloud; at most 2^31 - 1 simplices in total.
+ * Replaces any filtration the context held. Synchronises the stream. */
+int ph_build_filtration(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets,
+                        int32_t n_clouds, int64_t n_points, int32_t D, int32_t max_dim,
+                        int64_t max_diam2, int64_t* m_out);
+
+/* Loads an explicit filtration of one complex instead of building a VR one.
+ *   m             number of simplices, in a compatible order (faces before cofaces).
+ *   dims          host int32 [m], dimension of each simplex (0..15).
+ *   colptr        host int64 [m + 1], CSC column pointers of the boundary matrix.
+ *   rows          host int32 [colptr[m]], row indices (global positions, ascending per
+ *                 column, each row of dimension dims[j] - 1).
+ * Squared diameters of loaded complexes are reported as 0. Synchronises the stream. */
+int ph_load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* colptr,
+                     const int32_t* rows);
+
+/* Reduces the boundary matrices of the context with Algorithm 2 (Sec. 3.1): each pass builds
+ * the table of left-most columns per low with atomicMin, marks pivots (Thm 5, Phase I /
+ * Algorithm 5 with Thms 6-7), zero columns and the zero case of Corollary 10, clears the
+ * partners of new pivots (Lemma 1), then adds every colliding column's left-most column into
+ * it, until no low collides (Thm 8). All clouds are reduced together.
+ *   max_passes    cap on passes with additions (< 0: no cap). When it is hit the call
+ *                 returns PH_NOT_CONVERGED and the state stays a valid partial reduction.
+ *   out           host, optional: summary counters.
+ * Synchronises the stream. May be called once per filtration. */
+int ph_reduce(ph_ctx* ctx, int32_t max_passes, ph_stats* out);
+
+/* Discards the reduction state (and extracted outputs) of the context; the next ph_reduce
+ * starts again from the unreduced boundary matrix. Synchronises the stream. */
+int ph_reset_reduction(ph_ctx* ctx);
+
+/* Copies the per-pass counters (PH_PS_N int64 per pass, passes + 1 rows including the final
+ * pass that found no collision) to host `out` with room for `max_rows` rows; *rows_out gets
+ * the number of rows available. Needs collect_stats. */
+int ph_get_pass_stats(ph_ctx* ctx, int64_t* out, int32_t max_rows, int32_t* rows_out);
+
+/* Persistence pairs (sigma_birth, sigma_death) of cloud `cloud` with lowstar(death) = birth
+ * (Lemma 1), ordered by (dimension of death, death index). Two-call protocol: with
+ * birth == NULL only *count is written. Output buffers (capacity >= count entries each) are
+ * device pointers when on_device != 0, host pointers otherwise; any of them may be NULL.
+ *   birth, death        int64 filtration indices within the cloud.
+ *   dim                 int32 dimension of the birth simplex.
+ *   birth_diam2, death_diam2   int64 squared diameters (grid units^2).
+ * Synchronises the stream. */
+int ph_get_pairs(ph_ctx* ctx, int32_t cloud, int64_t* birth, int64_t* death, int32_t* dim,
+                 int64_t* birth_diam2, int64_t* death_diam2, int64_t capacity, int64_t* count,
+                 int32_t on_device);
+
+/* Essential simplices of cloud `cloud`: positive simplices that are never paired (Sec. 2.3,
+ * set Ess), ordered by (dimension, index). Same protocol and buffer rules as ph_get_pairs.
+ *   idx    int64 filtration indices; dim int32; diam2 int64. */
+int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int64_t* diam2,
+                     int64_t capacity, int64_t* count, int32_t on_device);
+
+/* Inspection of the filtration of cloud `cloud` in filtration order, for testing the build
+ * against an independent implementation. Host buffers of `count` entries (any may be NULL):
+ *   dim int32; diam2 int64; verts int32 [count][4] (-1 padded); beta int32 (Definition 4, as
+ *   a filtration index, -1 = none); low int32 (current low, filtration index, -1 = zero).
+ * *count receives the number of simplices of the cloud; with dim == NULL nothing else is
+ * copied. Synchronises the stream. */
+int ph_get_filtration(ph_ctx* ctx, int32_t cloud, int32_t* dim, int64_t* diam2, int32_t* verts,
+                      int32_t* beta, int32_t* low, int64_t* count);
+
+/* Number of kernels the context has launched since it was created. */
+int64_t ph_kernel_launches(const ph_ctx* ctx);
+
+/* Text of the last error of the context (empty when none). Valid until the next call. */
+const char* ph_last_error(const ph_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PH_GB300_H */

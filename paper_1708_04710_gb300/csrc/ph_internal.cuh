@@ -1,0 +1,254 @@
+// Internal definitions of the GB300 persistent-homology library (not part of the ABI).
+//
+// Simplex identifiers ("ids") are dim-major over all clouds: every simplex of dimension d
+// lies in [dimoff[d], dimoff[d+1]); inside a dimension, cloud c owns the contiguous segment
+// s = d * n_clouds + c, and inside a segment simplices follow the filtration order of the
+// cloud. Rows of a column of dimension d are ids of dimension d-1 of the same cloud, so one
+// id space carries every table of the reduction (low, beta, owner, left-most table).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ph_gb300.h"
+
+namespace ph {
+
+constexpr int kMaxDim = 8;  // largest simplex dimension of a loaded complex
+constexpr int kMaxVrDim = 3;
+constexpr int kVertBits = 12;  // packed vertex tuples: 4 x 12 bits + 16-bit cloud
+constexpr int kMaxCloudPoints = 1 << kVertBits;
+constexpr int kMaxClouds = 65535;
+
+// column flags
+constexpr uint8_t F_PROVEN = 1;  // pivot: low(j) = lowstar(j) > 0 is known
+constexpr uint8_t F_FINAL = 2;   // column is zero and positive for good
+constexpr uint8_t F_NEWPIV = 4;  // proven in the current pass
+
+struct ColStore {  // a device buffer that holds column storage (int32 rows)
+  int32_t* p = nullptr;
+  int64_t cap = 0;  // words
+};
+
+struct ReduceState {
+  int32_t* act = nullptr;      // active ids, ascending
+  int32_t* act2 = nullptr;     // next active list
+  int64_t act_cap = 0;
+  int64_t n_act = 0;           // host copy of the active count
+  int32_t** cptr = nullptr;    // per id: pointer to its rows
+  int32_t* clen = nullptr;     // per id: number of rows
+  int32_t** nxt_ptr = nullptr; // per active slot: new location
+  int32_t* nxt_len = nullptr;
+  int32_t* owner = nullptr;    // per row id: proven pivot with that low, -1
+  int32_t* tab = nullptr;      // per row id: left-most column with that low (this pass)
+  int32_t* first_unp = nullptr;// per segment: first row id not known to be paired
+  uint8_t* flags = nullptr;
+  uint8_t* cleared = nullptr;  // per id: zeroed by clearing
+  // scan scratch
+  void* tiles = nullptr;
+  int64_t tiles_bytes = 0;
+  int64_t* totals = nullptr;   // device [8]: survivors, words, pivot words, targets, ...
+  int64_t* h_totals = nullptr; // pinned host mirror
+  int64_t* pass_stats = nullptr;  // device [stats_rows][PH_PS_N]
+  int32_t stats_rows = 0;
+  ColStore arena[2];
+  int cur = 0;                 // arena holding the active columns
+  std::vector<ColStore> pivots;  // chunks holding proven columns
+  int64_t piv_used = 0;        // words used in the last chunk
+  int64_t* piv_bump = nullptr; // device bump pointer of the last chunk
+  int32_t passes = 0;
+  int32_t next_pass = 0;      // pass index a resumed reduction starts from
+  bool init = false;
+  bool done = false;
+  int status = PH_OK;
+  std::vector<int64_t> h_stats;  // host copy of per-pass counters
+  std::vector<cudaEvent_t> ev;   // start/stop pairs around the addition kernel
+  int64_t add_launches = 0;
+  double ms_add = 0;
+};
+
+}  // namespace ph
+
+struct ph_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  ph_opts opts{};
+  ph_allocator alloc{};
+  bool has_alloc = false;
+  std::string err;
+  int64_t launches = 0;  // kernels launched by this context
+
+  struct Block {
+    void* p;
+    size_t bytes;
+  };
+  std::vector<Block> blocks;  // every device allocation of the context
+
+  // filtration
+  bool built = false;
+  bool reduced = false;
+  int32_t n_clouds = 0;
+  int32_t max_dim = 0;
+  int64_t m = 0;
+  std::vector<int64_t> pt_off;     // host [n_clouds + 1]
+  std::vector<int64_t> seg_start;  // host [nseg + 1], nseg = (max_dim + 1) * n_clouds
+  int64_t dimoff[ph::kMaxDim + 2] = {0};
+  int64_t* d_seg_start = nullptr;
+  int32_t* seg = nullptr;     // per id: segment
+  int32_t* low = nullptr;     // per id: low, as an id (-1 none)
+  int32_t* beta = nullptr;    // per id: beta, as an id (-1 none)
+  int32_t* key = nullptr;     // per id: dense squared-diameter rank (-1: vertex/loaded)
+  int64_t* gidx = nullptr;    // per id: filtration index within its cloud
+  uint64_t* verts = nullptr;  // per id: packed (cloud, v0..v3)
+  int64_t* d2tab = nullptr;   // dense rank -> squared diameter
+  int64_t n_d2 = 0;
+  int32_t* rows0 = nullptr;   // initial column storage (boundary matrix, CSC by id)
+  int64_t nnz = 0;
+
+  ph::ReduceState rs;
+
+  // extraction cache
+  bool extracted = false;
+  std::vector<int64_t> pair_off, ess_off;  // per cloud, host
+  int64_t n_pairs = 0, n_ess = 0;
+  int64_t *p_birth = nullptr, *p_death = nullptr, *p_bd2 = nullptr, *p_dd2 = nullptr;
+  int32_t* p_dim = nullptr;
+  int64_t *e_idx = nullptr, *e_d2 = nullptr;
+  int32_t* e_dim = nullptr;
+
+  void* dalloc(size_t bytes);
+  void dfree(void* p);
+  void free_all();
+};
+
+namespace ph {
+
+// ------------------------------------------------------------------------------------------
+// error handling
+// ------------------------------------------------------------------------------------------
+struct Fail {
+  int code;
+};
+
+#define PH_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                       \
+      throw ::ph::Fail{PH_ERR_CUDA};                                                       \
+    }                                                                                      \
+  } while (0)
+
+#define PH_CHECK_LAUNCH()      \
+  do {                         \
+    ctx->launches++;           \
+    PH_CUDA(cudaGetLastError()); \
+  } while (0)
+
+#define PH_REQUIRE(cond, code, msg) \
+  do {                              \
+    if (!(cond)) {                  \
+      ctx->err = (msg);             \
+      throw ::ph::Fail{code};       \
+    }                               \
+  } while (0)
+
+template <class T>
+T* alloc_n(ph_ctx* ctx, int64_t n) {
+  return static_cast<T*>(ctx->dalloc(sizeof(T) * (size_t)(n > 0 ? n : 1)));
+}
+
+inline int grid_for(ph_ctx* ctx, int64_t n, int threads, int per_sm = 8) {
+  int64_t want = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)ctx->num_sms * per_sm;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+// ------------------------------------------------------------------------------------------
+// device building blocks (256-thread blocks)
+// ------------------------------------------------------------------------------------------
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
+
+// inclusive warp scan of (a, b) sums
+template <class T>
+__device__ __forceinline__ T warp_incl_sum(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, v, o);
+    if ((int)lane_id() >= o) v += u;
+  }
+  return v;
+}
+
+// exclusive block scan (sum) of one value per thread; returns the exclusive prefix and the
+// block total. `sh` must hold kWarps + 1 elements.
+template <class T>
+__device__ __forceinline__ T block_excl_sum(T v, T* sh, T& total) {
+  T inc = warp_incl_sum(v);
+  int w = threadIdx.x >> 5;
+  if (lane_id() == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T x = (lane_id() < kWarps) ? sh[lane_id()] : T(0);
+    T xi = warp_incl_sum(x);
+    if (lane_id() < kWarps) sh[lane_id()] = xi - x;
+    if (lane_id() == kWarps - 1) sh[kWarps] = xi;
+  }
+  __syncthreads();
+  T res = inc - v + sh[w];
+  total = sh[kWarps];
+  __syncthreads();
+  return res;
+}
+
+// segmented running maximum: elements carry a segment id (non-decreasing along the array);
+// combine(a, b) for a before b keeps b's segment and takes the max only inside one segment.
+struct SegMax {
+  int32_t seg;
+  int32_t val;
+};
+
+__device__ __forceinline__ SegMax segmax_combine(SegMax a, SegMax b) {
+  SegMax r;
+  r.seg = b.seg;
+  r.val = (a.seg == b.seg) ? (a.val > b.val ? a.val : b.val) : b.val;
+  return r;
+}
+
+__device__ __forceinline__ SegMax warp_incl_segmax(SegMax v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    SegMax u;
+    u.seg = __shfl_up_sync(0xffffffffu, v.seg, o);
+    u.val = __shfl_up_sync(0xffffffffu, v.val, o);
+    if ((int)lane_id() >= o) v = segmax_combine(u, v);
+  }
+  return v;
+}
+
+}  // namespace ph
+
+// host entry points shared between translation units
+namespace ph {
+void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, int32_t n_clouds,
+              int64_t n_points, int32_t D, int32_t max_dim, int64_t max_diam2);
+void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* colptr,
+                   const int32_t* rows);
+void compute_beta(ph_ctx* ctx);
+void reduce_init(ph_ctx* ctx);
+int reduce_run(ph_ctx* ctx, int32_t max_passes);
+void extract_all(ph_ctx* ctx);
+void free_reduce_state(ph_ctx* ctx);
+// generic device helpers (ph_scan.cu)
+void excl_scan_i64(ph_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev);
+void radix_sort_u64(ph_ctx* ctx, uint64_t* keys, uint64_t* vals, int64_t n, int lo_bit,
+                    int hi_bit, uint64_t* tmp_keys, uint64_t* tmp_vals);
+}  // namespace ph

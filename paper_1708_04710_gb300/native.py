@@ -1,0 +1,258 @@
+"""ctypes binding of the C ABI in ``include/ph_gb300.h``: argument marshalling only.
+
+Every computation runs in the CUDA library ``libph_gb300.so``. PyTorch supplies device memory
+(through its caching allocator, handed to the library as a ``ph_allocator``) and the stream.
+There is no fallback: if the library is missing or no GPU is present, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import (CFUNCTYPE, POINTER, Structure, byref, c_char_p, c_double, c_int, c_int32,
+                    c_int64, c_size_t, c_void_p)
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "libph_gb300.so"
+
+PH_OK, PH_NOT_CONVERGED = 0, 1
+PS_FIELDS = ("active", "new_pivots", "zero_final", "cor10", "cleared", "targets", "adds",
+             "xors", "copied")
+
+
+class PHError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ph error {code}: {msg}")
+        self.code = code
+
+
+class PhOpts(Structure):
+    _fields_ = [("strict_phase2", c_int32), ("use_cor10", c_int32), ("block_threads", c_int32),
+                ("warp_merge_min", c_int32), ("collect_stats", c_int32), ("use_graph", c_int32),
+                ("time_kernels", c_int32)]
+
+
+class PhStats(Structure):
+    _fields_ = [("passes", c_int32), ("status", c_int32), ("m", c_int64), ("col_adds", c_int64),
+                ("xors", c_int64), ("alg_bytes", c_int64), ("add_bytes", c_int64),
+                ("add_launches", c_int64), ("ms_add", c_double)]
+
+
+ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
+class PhAllocator(Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
+
+
+# exported symbols and their signatures: the ABI the tests check against include/ph_gb300.h
+SIGNATURES = {
+    "ph_default_opts": (None, [POINTER(PhOpts)]),
+    "ph_create": (c_int, [POINTER(c_void_p), POINTER(PhOpts), POINTER(PhAllocator), c_void_p]),
+    "ph_destroy": (None, [c_void_p]),
+    "ph_build_filtration": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32,
+                                    c_int32, c_int64, POINTER(c_int64)]),
+    "ph_load_boundary": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "ph_reduce": (c_int, [c_void_p, c_int32, POINTER(PhStats)]),
+    "ph_reset_reduction": (c_int, [c_void_p]),
+    "ph_get_pass_stats": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
+    "ph_get_pairs": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                             c_int64, POINTER(c_int64), c_int32]),
+    "ph_get_essential": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int64,
+                                 POINTER(c_int64), c_int32]),
+    "ph_get_filtration": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, POINTER(c_int64)]),
+    "ph_kernel_launches": (c_int64, [c_void_p]),
+    "ph_last_error": (c_char_p, [c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: Path | str = LIB_PATH):
+    """Loads the CUDA library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = Path(path)
+    if not path.exists():
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() (or "
+                          "python paper_1708_04710_gb300/build.py) first")
+    lib = ctypes.CDLL(str(path))
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("the persistent-homology library needs a CUDA GPU")
+    return torch
+
+
+def _ptr(t) -> c_void_p:
+    if t is None:
+        return c_void_p(None)
+    if isinstance(t, np.ndarray):
+        return c_void_p(t.ctypes.data)
+    return c_void_p(t.data_ptr())
+
+
+class Context:
+    """One library context: a filtration (of one or many clouds) and its reduction."""
+
+    def __init__(self, *, strict_phase2: bool = False, use_cor10: bool = True,
+                 collect_stats: bool = False, warp_merge_min: int = 0, use_graph: bool = False,
+                 time_kernels: bool = False, stream=None):
+        torch = _torch()
+        self._torch = torch
+        self.lib = load_library()
+        opts = PhOpts()
+        self.lib.ph_default_opts(byref(opts))
+        opts.strict_phase2 = int(strict_phase2)
+        opts.use_cor10 = int(use_cor10)
+        opts.collect_stats = int(collect_stats)
+        if warp_merge_min:
+            opts.warp_merge_min = int(warp_merge_min)
+        opts.use_graph = int(use_graph)
+        opts.time_kernels = int(time_kernels)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        dev_index = self.device.index if self.device.index is not None else 0
+
+        def _alloc(nbytes, user, stream):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev_index, stream or 0)
+            except Exception:  # out of memory: the library reports PH_ERR_ALLOC
+                return None
+
+        def _free(ptr, nbytes, user, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))  # keep the callbacks alive
+        self._allocator = PhAllocator(self._cb[0], self._cb[1], None)
+        self._h = c_void_p()
+        with torch.cuda.device(self.device):
+            self._check(self.lib.ph_create(byref(self._h), byref(opts), byref(self._allocator),
+                                           c_void_p(self.stream.cuda_stream)))
+        self.n_clouds = 0
+        self.m = 0
+
+    # -- helpers --------------------------------------------------------------------------
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            msg = self.lib.ph_last_error(self._h).decode() if self._h else ""
+            raise PHError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.ph_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- ABI ------------------------------------------------------------------------------
+    def build_filtration(self, coords, cloud_offsets=None, max_dim: int = 2,
+                         max_diam2: int = -1) -> int:
+        """coords: int32 CUDA tensor (N, D) in grid units; cloud_offsets: int64 (n_clouds+1)."""
+        torch = self._torch
+        assert coords.is_cuda and coords.dtype == torch.int32 and coords.dim() == 2
+        coords = coords.contiguous()
+        self._coords = coords
+        N, D = coords.shape
+        if cloud_offsets is None:
+            offs = None
+            nc = 1
+        else:
+            offs = np.ascontiguousarray(np.asarray(cloud_offsets, dtype=np.int64))
+            nc = len(offs) - 1
+        m = c_int64(0)
+        self._check(self.lib.ph_build_filtration(self._h, _ptr(coords), _ptr(offs), nc, N, D,
+                                                 max_dim, int(max_diam2), byref(m)))
+        self.n_clouds = nc
+        self.m = m.value
+        return self.m
+
+    def load_boundary(self, dims, colptr, rows):
+        dims = np.ascontiguousarray(dims, np.int32)
+        colptr = np.ascontiguousarray(colptr, np.int64)
+        rows = np.ascontiguousarray(rows, np.int32)
+        self._check(self.lib.ph_load_boundary(self._h, len(dims), _ptr(dims), _ptr(colptr),
+                                              _ptr(rows)))
+        self.n_clouds = 1
+        self.m = len(dims)
+
+    def reduce(self, max_passes: int = -1) -> dict:
+        st = PhStats()
+        rc = self._check(self.lib.ph_reduce(self._h, max_passes, byref(st)))
+        return dict(passes=st.passes, status=st.status, converged=(rc == PH_OK), m=st.m,
+                    col_adds=st.col_adds, xors=st.xors, alg_bytes=st.alg_bytes,
+                    add_bytes=st.add_bytes, add_launches=st.add_launches, ms_add=st.ms_add)
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.ph_kernel_launches(self._h))
+
+    def reset_reduction(self):
+        self._check(self.lib.ph_reset_reduction(self._h))
+
+    def pass_stats(self) -> np.ndarray:
+        rows = c_int32(0)
+        self._check(self.lib.ph_get_pass_stats(self._h, None, 0, byref(rows)))
+        out = np.zeros((rows.value, len(PS_FIELDS)), np.int64)
+        self._check(self.lib.ph_get_pass_stats(self._h, _ptr(out), rows.value, byref(rows)))
+        return out
+
+    def pairs(self, cloud: int = 0, on_device: bool = True) -> dict:
+        torch = self._torch
+        n = c_int64(0)
+        self._check(self.lib.ph_get_pairs(self._h, cloud, None, None, None, None, None, 0,
+                                          byref(n), 0))
+        k = n.value
+        if on_device:
+            mk = lambda dt: torch.empty(k, dtype=dt, device=self.device)  # noqa: E731
+        else:
+            mk = lambda dt: torch.empty(k, dtype=dt)  # noqa: E731
+        out = dict(birth=mk(torch.int64), death=mk(torch.int64), dim=mk(torch.int32),
+                   birth_diam2=mk(torch.int64), death_diam2=mk(torch.int64))
+        self._check(self.lib.ph_get_pairs(self._h, cloud, _ptr(out["birth"]), _ptr(out["death"]),
+                                          _ptr(out["dim"]), _ptr(out["birth_diam2"]),
+                                          _ptr(out["death_diam2"]), k, byref(n),
+                                          int(on_device)))
+        return out
+
+    def essential(self, cloud: int = 0, on_device: bool = True) -> dict:
+        torch = self._torch
+        n = c_int64(0)
+        self._check(self.lib.ph_get_essential(self._h, cloud, None, None, None, 0, byref(n), 0))
+        k = n.value
+        dev = self.device if on_device else "cpu"
+        out = dict(idx=torch.empty(k, dtype=torch.int64, device=dev),
+                   dim=torch.empty(k, dtype=torch.int32, device=dev),
+                   diam2=torch.empty(k, dtype=torch.int64, device=dev))
+        self._check(self.lib.ph_get_essential(self._h, cloud, _ptr(out["idx"]), _ptr(out["dim"]),
+                                              _ptr(out["diam2"]), k, byref(n), int(on_device)))
+        return out
+
+    def filtration(self, cloud: int = 0) -> dict:
+        n = c_int64(0)
+        self._check(self.lib.ph_get_filtration(self._h, cloud, None, None, None, None, None,
+                                               byref(n)))
+        k = n.value
+        out = dict(dim=np.empty(k, np.int32), diam2=np.empty(k, np.int64),
+                   verts=np.empty((k, 4), np.int32), beta=np.empty(k, np.int32),
+                   low=np.empty(k, np.int32))
+        self._check(self.lib.ph_get_filtration(self._h, cloud, _ptr(out["dim"]),
+                                               _ptr(out["diam2"]), _ptr(out["verts"]),
+                                               _ptr(out["beta"]), _ptr(out["low"]), byref(n)))
+        return out

@@ -1,0 +1,289 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Everything is integer work, so every comparison is exact: the filtration (dimension, squared
+diameter, vertex tuple), beta, the initial and final low, the persistence pairs, the essential
+set and -- because every decision of a pass is taken from the pass's starting state -- the
+per-pass counters of Algorithm 2 (pivots, zeroings, clearings, targets, additions, XORs).
+"""
+import hashlib
+import json
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import pointclouds as pc
+
+pytestmark = pytest.mark.gpu
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+@pytest.fixture(scope="module")
+def ph():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1708_04710_gb300 import build
+
+    build.build()
+    import paper_1708_04710_gb300 as ph
+
+    return ph
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+
+    oracle.build_lib()
+    return oracle
+
+
+def _gpu(ph, coords, max_dim, max_diam2=-1, offsets=None, **kw):
+    import torch
+
+    ctx = ph.Context(collect_stats=True, **kw)
+    ctx.build_filtration(torch.from_numpy(np.ascontiguousarray(coords, np.int32)).cuda(),
+                         offsets, max_dim, max_diam2)
+    return ctx
+
+
+def _canon(pairs_b, pairs_d, ess):
+    p = np.stack([pairs_b, pairs_d], 1) if len(pairs_b) else np.zeros((0, 2), np.int64)
+    o = np.lexsort((p[:, 0], p[:, 1])) if len(p) else np.zeros(0, int)
+    return p[o].astype(np.int64), np.sort(np.asarray(ess, np.int64))
+
+
+def _gpu_pairs(ctx, cloud):
+    pr = ctx.pairs(cloud, on_device=False)
+    es = ctx.essential(cloud, on_device=False)
+    return {k: v.numpy() for k, v in pr.items()}, {k: v.numpy() for k, v in es.items()}
+
+
+def _check_filtration(orc, ctx, cloud, K, low=None):
+    f = ctx.filtration(cloud)
+    assert np.array_equal(f["dim"], K["dim"])
+    assert np.array_equal(f["diam2"], K["diam2"])
+    vk = K["verts"].copy()
+    assert np.array_equal(f["verts"], vk)
+    assert np.array_equal(f["beta"], orc.beta(K))
+    if low is not None:
+        assert np.array_equal(f["low"], low)
+    return f
+
+
+def _check_reduced(orc, ctx, cloud, K, strict=False, cor10=True, stats=True):
+    ref = orc.reduce_pms(K, strict=strict, cor10=cor10)
+    assert ref.converged
+    f = ctx.filtration(cloud)
+    assert np.array_equal(f["low"], ref.low), "final low differs from the oracle"
+    pr, es = _gpu_pairs(ctx, cloud)
+    gp, ge = _canon(pr["birth"], pr["death"], es["idx"])
+    op, oe = _canon(*orc.pairs_and_essential(ref.low, K["dim"])[0].T,
+                    orc.pairs_and_essential(ref.low, K["dim"])[1])
+    assert np.array_equal(gp, op)
+    assert np.array_equal(ge, oe)
+    # dims and diameters of the reported pairs / essentials
+    d_by_idx = K["dim"]
+    order = np.lexsort((pr["birth"], pr["death"]))
+    assert np.array_equal(pr["dim"][order], d_by_idx[gp[:, 0]])
+    assert np.array_equal(pr["birth_diam2"][order], K["diam2"][gp[:, 0]])
+    assert np.array_equal(pr["death_diam2"][order], K["diam2"][gp[:, 1]])
+    eo = np.argsort(es["idx"])
+    assert np.array_equal(es["dim"][eo], d_by_idx[ge])
+    assert np.array_equal(es["diam2"][eo], K["diam2"][ge])
+    return ref
+
+
+CASES = [
+    ("gauss_3d_dim2", lambda: pc.random_cloud(24, 3, 1), 2, -1),
+    ("gauss_2d_dim3", lambda: pc.random_cloud(14, 2, 2), 3, -1),
+    ("gauss_5d_dim3_cut", lambda: pc.random_cloud(22, 5, 3), 3, int(6.0 * 65536 ** 2)),
+    ("lattice_ties", lambda: pc.lattice_cloud(30, 2, 4, side=4), 2, -1),
+    ("duplicates", lambda: np.repeat(pc.random_cloud(9, 3, 5), 2, axis=0), 2, -1),
+    ("circle40", pc.circle40, 2, -1),
+    ("edges_only", lambda: pc.random_cloud(50, 2, 6), 1, -1),
+    ("one_point", lambda: pc.random_cloud(1, 3, 7), 2, -1),
+    ("two_points", lambda: pc.random_cloud(2, 3, 8), 2, -1),
+    ("three_points", lambda: pc.random_cloud(3, 3, 9), 3, -1),
+    ("all_cut", lambda: pc.random_cloud(10, 3, 10), 2, 0),
+]
+
+
+@pytest.mark.parametrize("name,gen,max_dim,cut", CASES, ids=[c[0] for c in CASES])
+def test_filtration_and_reduction(ph, orc, name, gen, max_dim, cut):
+    x = gen()
+    K = orc.vr_build(x, max_dim, cut)
+    ctx = _gpu(ph, x, max_dim, cut)
+    assert ctx.m == K.m
+    low0 = np.array([K["rows"][K["colptr"][j + 1] - 1] if K["colptr"][j + 1] > K["colptr"][j]
+                     else -1 for j in range(K.m)], np.int32)
+    _check_filtration(orc, ctx, 0, K, low0)
+    st = ctx.reduce()
+    assert st["converged"]
+    ref = _check_reduced(orc, ctx, 0, K)
+    assert st["passes"] == ref.passes
+    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+
+
+@pytest.mark.parametrize("strict,cor10", [(True, True), (False, False), (True, False)])
+def test_modes(ph, orc, strict, cor10):
+    x = pc.random_cloud(40, 3, 11)
+    K = orc.vr_build(x, 2)
+    ctx = _gpu(ph, x, 2, strict_phase2=strict, use_cor10=cor10)
+    st = ctx.reduce()
+    ref = _check_reduced(orc, ctx, 0, K, strict=strict, cor10=cor10)
+    assert st["passes"] == ref.passes
+    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+
+
+def test_merge_paths_agree(ph, orc):
+    # every column through the warp-cooperative merge, then every column through one thread
+    x = pc.random_cloud(60, 3, 12)
+    K = orc.vr_build(x, 2)
+    ref = orc.reduce_pms(K)
+    for wmin in (1, 1 << 30):
+        ctx = _gpu(ph, x, 2, warp_merge_min=wmin)
+        ctx.reduce()
+        assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+
+
+def test_batched_clouds(ph, orc):
+    sizes = [1, 2, 3, 17, 40, 5, 60, 33]
+    clouds = [pc.random_cloud(n, 3, 100 + i) for i, n in enumerate(sizes)]
+    x = np.concatenate(clouds)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ctx = _gpu(ph, x, 2, offsets=off)
+    assert ctx.n_clouds == len(sizes)
+    st = ctx.reduce()
+    agg = None
+    for c, xc in enumerate(clouds):
+        K = orc.vr_build(xc, 2)
+        _check_filtration(orc, ctx, c, K)
+        ref = _check_reduced(orc, ctx, c, K)
+        s = ref.stats[:, :8]
+        if agg is None:
+            agg = s
+        else:
+            n = max(len(agg), len(s))
+            agg = np.pad(agg, ((0, n - len(agg)), (0, 0))) + np.pad(s, ((0, n - len(s)), (0, 0)))
+    assert np.array_equal(ctx.pass_stats()[:, :8], agg)
+    assert st["passes"] == len(agg) - 1
+
+
+def test_max_passes_partial_state(ph, orc):
+    x = pc.circle40()
+    K = orc.vr_build(x, 2)
+    for k in (0, 1, 3, 7):
+        ctx = _gpu(ph, x, 2)
+        st = ctx.reduce(max_passes=k)
+        ref = orc.reduce_pms(K, max_passes=k)
+        assert not st["converged"] and not ref.converged
+        assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+        ctx.reset_reduction()
+        st = ctx.reduce()
+        assert st["converged"]
+        _check_reduced(orc, ctx, 0, K)
+
+
+def test_triangulations(ph, orc):
+    from helpers import closure, random_compatible_order
+
+    data = json.loads((GOLDEN / "triangulations.json").read_text())
+    data.pop("_about")
+    for name, t in data.items():
+        S = random_compatible_order(closure(t["facets"]), 5)
+        K = orc.boundary_from_simplices(S)
+        ctx = ph.Context(collect_stats=True)
+        ctx.load_boundary(K["dim"], K["colptr"], K["rows"])
+        ctx.reduce()
+        es = ctx.essential(0, on_device=False)
+        betti = np.bincount(es["dim"].numpy(), minlength=len(t["betti"])).tolist()
+        assert betti == t["betti"], name
+        ref = orc.reduce_pms(K)
+        assert np.array_equal(ctx.filtration(0)["low"], ref.low), name
+        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8]), name
+
+
+def test_invalid_arguments(ph):
+    import torch
+
+    ctx = ph.Context()
+    x = torch.zeros((4, 3), dtype=torch.int32, device="cuda")
+    with pytest.raises(ph.PHError):
+        ctx.build_filtration(x, None, 4)  # max_dim out of range
+    with pytest.raises(ph.PHError):
+        ctx.build_filtration(x, [0, 2, 3], 2)  # offsets must end at N
+    big = torch.full((3, 2), 1 << 25, dtype=torch.int32, device="cuda")
+    with pytest.raises(ph.PHError):
+        ctx.build_filtration(big, None, 2)  # coordinates beyond the grid bound
+    with pytest.raises(ph.PHError):
+        ctx.reduce()  # no filtration
+    ctx.build_filtration(x, None, 2)
+    ctx.reduce()
+    assert ctx.essential(0, on_device=False)["idx"].numel() == 2  # b0 = b2 = 1
+
+
+# ------------------------------------------------------------------------------------------
+# full-size workloads against stored oracle results (tests/golden/make_golden.py)
+# ------------------------------------------------------------------------------------------
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def _golden(name):
+    p = GOLDEN / f"{name}.json"
+    if not p.exists():
+        pytest.skip(f"{p.name} not generated")
+    return json.loads(p.read_text())
+
+
+@pytest.mark.parametrize("name", ["circle40", "gauss8_120", "torus400"])
+def test_full_size_single(ph, name):
+    g = _golden(name)
+    x = {"circle40": pc.circle40, "gauss8_120": pc.gauss8_120, "torus400": pc.torus400}[name]()
+    assert _sha(x) == g["coords_sha"], "generator drift: coordinates differ from the golden's"
+    max_dim = 3 if name == "gauss8_120" else 2
+    ctx = _gpu(ph, x, max_dim, g.get("max_diam2", -1))
+    assert ctx.m == g["m"]
+    st = ctx.reduce()
+    assert st["converged"] and st["passes"] == g["passes"]
+    assert np.array_equal(ctx.pass_stats()[:, :8], np.array(g["pass_stats"], np.int64))
+    pr, es = _gpu_pairs(ctx, 0)
+    gp, ge = _canon(pr["birth"], pr["death"], es["idx"])
+    assert _sha(gp) == g["pairs_sha"]
+    assert _sha(ge) == g["ess_sha"]
+    assert np.bincount(es["dim"], minlength=max_dim + 1).tolist() == g["ess_per_dim"]
+
+
+def test_full_size_batch512(ph):
+    g = _golden("batch512")
+    x, off = pc.batch512()
+    assert _sha(x) == g["coords_sha"] and _sha(off) == g["offsets_sha"]
+    ctx = _gpu(ph, x, 2, offsets=off)
+    assert ctx.m == g["m"]
+    st = ctx.reduce()
+    assert st["converged"] and st["passes"] == g["passes"]
+    assert np.array_equal(ctx.pass_stats()[:, :8], np.array(g["pass_stats"], np.int64))
+    h = hashlib.sha256()
+    for c in range(len(off) - 1):
+        pr, es = _gpu_pairs(ctx, c)
+        gp, ge = _canon(pr["birth"], pr["death"], es["idx"])
+        h.update(gp.tobytes())
+        h.update(ge.tobytes())
+    assert h.hexdigest() == g["all_sha"]
+
+
+def test_closed_form_complete_skeleton_large(ph):
+    # b_2 of the complete 2-skeleton on n points is C(n-1, 3), at a size no oracle runs
+    x = pc.to_grid(pc.sphere(160, pc.rng_for(9)))
+    ctx = _gpu(ph, x, 2)
+    assert ctx.m == 160 + math.comb(160, 2) + math.comb(160, 3)
+    ctx.reduce()
+    es = ctx.essential(0, on_device=False)
+    assert np.bincount(es["dim"].numpy(), minlength=3).tolist() == [1, 0, math.comb(159, 3)]
+    pr = ctx.pairs(0, on_device=False)
+    assert np.all(pr["birth_diam2"].numpy() <= pr["death_diam2"].numpy())
