@@ -45,6 +45,9 @@ WORKLOADS = {
                      desc="complete VR <= dim 2, 40 noisy points on the unit circle"),
     "gauss8_120": dict(gen=pc.gauss8_120, max_dim=3, max_diam2=pc.GAUSS8_MAX_DIAM2,
                        desc="VR <= dim 3, 120 points N(0, I_8), squared diameter <= 16"),
+    # smaller case of the same law for ncu captures (2.6M simplices)
+    "torus250": dict(gen=lambda: pc.torus400()[:250], max_dim=2, max_diam2=-1,
+                     desc="complete VR <= dim 2, first 250 of the 400 torus points"),
 }
 
 
