@@ -190,6 +190,27 @@ int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int
 int ph_get_filtration(ph_ctx* ctx, int32_t cloud, int32_t* dim, int64_t* diam2, int32_t* verts,
                       int32_t* beta, int32_t* low, int64_t* count);
 
+/* Allocation-free beta, for callers that cannot allocate device memory: code running inside
+ * another framework's memory pool or arena, programs that forbid allocation after start-up,
+ * and callers that hold no library context. The paper has no counterpart of this entry point;
+ * it computes beta of Definition 4 like ph_build_filtration does, but keeps its only scratch
+ * (left(i) of Definition 3, one int32 per row) in a fixed device array of the library.
+ *   rows          device int32 [n_cols][rows_per_col]: boundary rows of n_cols columns of one
+ *                 dimension, columns in filtration order; a row is the 0-based filtration
+ *                 position of a face among the n_rows simplices one dimension lower.
+ *   n_rows        at most 4,194,304; larger values return PH_ERR_CAPACITY. The scratch array
+ *                 (16 MiB) stays resident on every GPU that loads the library until exit.
+ *   beta          device int32 [n_cols], output: largest row whose first column is j, or -1.
+ *   stream        cudaStream_t as void*.
+ * Allocates nothing (no cudaMalloc, cudaFree or allocator call). The first call on a device
+ * looks up the scratch's device address with cudaGetSymbolAddress; make that first call before
+ * any stream capture on that device. Every call shares the one scratch array, which it resets
+ * at its start: calls that overlap on the GPU (other streams or threads) race and give wrong
+ * results. Rows outside [0, n_rows) are skipped and make the call return PH_ERR_INVALID.
+ * Synchronises `stream`. */
+int ph_beta_static(const int32_t* rows, int64_t n_cols, int32_t rows_per_col, int64_t n_rows,
+                   int32_t* beta, void* stream);
+
 /* Number of kernels the context has launched since it was created. */
 int64_t ph_kernel_launches(const ph_ctx* ctx);
 

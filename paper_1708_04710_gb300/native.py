@@ -63,6 +63,7 @@ SIGNATURES = {
                                  POINTER(c_int64), c_int32]),
     "ph_get_filtration": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, POINTER(c_int64)]),
+    "ph_beta_static": (c_int, [c_void_p, c_int64, c_int32, c_int64, c_void_p, c_void_p]),
     "ph_kernel_launches": (c_int64, [c_void_p]),
     "ph_last_error": (c_char_p, [c_void_p]),
 }
