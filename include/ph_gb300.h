@@ -65,9 +65,13 @@ typedef struct {
   int32_t use_cor10;
   /* threads per block of the per-column kernels (0 = library default, 256) */
   int32_t block_threads;
-  /* columns whose merged length exceeds this use the warp-cooperative symmetric difference;
-   * shorter ones are merged by one thread (0 = library default) */
-  int32_t warp_merge_min;
+  /* Phase II merges of more rows than this (target + source) run from global memory; shorter
+   * ones are staged in shared memory first (0 = library default = the largest staged size,
+   * 1024) */
+  int32_t staged_merge_max;
+  /* merge-path positions per lane in Phase II (1..64); 0 (default) picks one per warp from
+   * the mean length of its merges (4 below 32 rows, 8 below 80, 16 below 160, else 32) */
+  int32_t merge_items;
   /* 1: per-pass counters are collected (column additions, XORs, pivots, ...) */
   int32_t collect_stats;
   /* 1: the pass loop runs inside one CUDA graph whose conditional while node reads a device

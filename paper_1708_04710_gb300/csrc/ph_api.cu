@@ -268,7 +268,8 @@ void ph_default_opts(ph_opts* o) {
   o->strict_phase2 = 0;
   o->use_cor10 = 1;
   o->block_threads = 256;
-  o->warp_merge_min = 48;
+  o->staged_merge_max = 0;
+  o->merge_items = 0;
   o->collect_stats = 0;
   o->use_graph = 0;
   o->time_kernels = 0;

@@ -118,6 +118,13 @@ __global__ void k_pairwise(const int32_t* __restrict__ x, int D, CloudTabs ct, i
   if ((threadIdx.x & 31) == 0) atomicMax(maxd2, mx);
 }
 
+// count one kept candidate for cloud c with one atomic per group of lanes sharing c
+__device__ __forceinline__ void count_kept(int64_t* count_per_cloud, int c, bool keep) {
+  const unsigned peers = __match_any_sync(__activemask(), keep ? c : -1);
+  if (keep && (threadIdx.x & 31) == __ffs(peers) - 1)
+    atomicAdd((unsigned long long*)&count_per_cloud[c], (unsigned long long)__popc(peers));
+}
+
 // edge candidates in (cloud, lex) order; truncated edges get key = sent
 __global__ void k_edge_cand(CloudTabs ct, const int64_t* __restrict__ cand, int64_t ncand,
                             const int64_t* __restrict__ d2, int64_t max_d2, uint64_t sent,
@@ -132,7 +139,7 @@ __global__ void k_edge_cand(CloudTabs ct, const int64_t* __restrict__ cand, int6
     bool keep = max_d2 < 0 || e <= max_d2;
     keys[t] = keep ? (uint64_t)e : sent;
     vals[t] = pack_simplex((uint32_t)c, 2, v);
-    if (keep) atomicAdd((unsigned long long*)&count_per_cloud[c], 1ull);
+    count_kept(count_per_cloud, c, keep);
   }
 }
 
@@ -223,7 +230,7 @@ __global__ void k_simplex_cand(CloudTabs ct, const int64_t* __restrict__ cand, i
       }
     keys[t] = keep ? (uint64_t)mx : sent;
     vals[t] = pack_simplex((uint32_t)c, k, v);
-    if (keep) atomicAdd((unsigned long long*)&count_per_cloud[c], 1ull);
+    count_kept(count_per_cloud, c, keep);
   }
 }
 

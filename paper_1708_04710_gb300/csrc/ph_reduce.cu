@@ -28,7 +28,6 @@ namespace ph {
 
 constexpr int kRItems = 8;
 constexpr int kRTile = kThreads * kRItems;
-constexpr int kMergeK = 4;  // merged elements per lane per round of the warp merge
 
 struct RArgs {
   int32_t* act;
@@ -50,15 +49,18 @@ struct RArgs {
   int strict;
   int cor10;
   int do_adds;
-  SegMax* tile_sm;
+  SegMax* tile_sm;    // [ntiles] Phase I tile aggregates (scanned in place to prefixes)
+  SegMax* chunk_sm;   // [ntiles][kRItems] aggregate of each 256-entry chunk alone
   int64_t* tile_cnt;  // [ntiles][2] survivors, words (scanned in place to prefixes)
   int64_t* tile_aux;  // [ntiles][2] pivot words, targets
+  int64_t* chunk_cnt; // [ntiles][kRItems][2] survivors, words of each chunk alone
   int64_t* totals;    // [4] survivors, words, pivot words, targets
   int32_t* arena_next;
   int32_t* piv_base;
   unsigned long long* piv_bump;
   int64_t* stats;  // this pass's counters or nullptr
-  int warp_min;
+  int staged_max;  // merges of more rows than this run from global memory
+  int force_km;    // > 0: merge-path positions per lane for every warp
 };
 
 __device__ __forceinline__ void stat_add(int64_t* stats, int k, int64_t v) {
@@ -139,8 +141,9 @@ __global__ void k_p1_tiles(RArgs a) {
   for (int it = 0; it < kRItems; it++) {
     SegMax v = p1_value(a, tile0 + it * kThreads + threadIdx.x);
     SegMax tot;
-    block_scan_segmax(v, carry, sh, tot);
-    carry = tot;
+    block_scan_segmax(v, SegMax{-1, -1}, sh, tot);  // this chunk alone
+    if (threadIdx.x == 0) a.chunk_sm[(int64_t)blockIdx.x * kRItems + it] = tot;
+    carry = segmax_combine(carry, tot);
   }
   if (threadIdx.x == 0) a.tile_sm[blockIdx.x] = carry;
 }
@@ -158,17 +161,19 @@ __global__ void k_p1_top(SegMax* tile_sm, int64_t ntiles) {
   }
 }
 
+// one block per 256-entry chunk; its prefix is the tile's prefix combined with the aggregates
+// of the earlier chunks of the same tile
 __global__ void k_mark(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
-  int64_t tile0 = (int64_t)blockIdx.x * kRTile;
-  SegMax carry = a.tile_sm[blockIdx.x];
+  const int64_t chunk = blockIdx.x, tile = chunk / kRItems;
+  SegMax carry = a.tile_sm[tile];
+  for (int64_t c = tile * kRItems; c < chunk; c++) carry = segmax_combine(carry, a.chunk_sm[c]);
   int64_t n_zero = 0, n_piv = 0, n_c10 = 0;
-  for (int it = 0; it < kRItems; it++) {
-    int64_t e = tile0 + it * kThreads + threadIdx.x;
+  {
+    int64_t e = chunk * kThreads + threadIdx.x;
     SegMax v = p1_value(a, e);
     SegMax tot;
     SegMax pre = block_scan_segmax(v, carry, sh, tot);
-    carry = tot;
     if (e < a.n_act) {
       int32_t j = a.act[e];
       int32_t l = a.low[j];
@@ -241,17 +246,22 @@ __device__ __forceinline__ Job job_of(const RArgs& a, int64_t e) {
 __global__ void k_s2_tiles(RArgs a) {
   __shared__ int64_t sh[kWarps + 1];
   int64_t tile0 = (int64_t)blockIdx.x * kRTile;
-  int64_t surv = 0, words = 0, pivw = 0, targ = 0;
+  int64_t t0 = 0, t1 = 0, pivw = 0, targ = 0;
   for (int it = 0; it < kRItems; it++) {
     Job jb = job_of(a, tile0 + it * kThreads + threadIdx.x);
-    surv += jb.surv;
-    words += jb.words;
+    int64_t cs, cw;
+    block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, cs);
+    block_excl_sum<int64_t>(jb.words, sh, cw);
+    if (threadIdx.x == 0) {
+      a.chunk_cnt[2 * ((int64_t)blockIdx.x * kRItems + it)] = cs;
+      a.chunk_cnt[2 * ((int64_t)blockIdx.x * kRItems + it) + 1] = cw;
+    }
+    t0 += cs;
+    t1 += cw;
     targ += jb.target;
     if (jb.newpiv) pivw += a.clen[jb.j];
   }
-  int64_t t0, t1, t2, t3;
-  block_excl_sum<int64_t>(surv, sh, t0);
-  block_excl_sum<int64_t>(words, sh, t1);
+  int64_t t2, t3;
   block_excl_sum<int64_t>(pivw, sh, t2);
   block_excl_sum<int64_t>(targ, sh, t3);
   if (threadIdx.x == 0) {
@@ -297,28 +307,6 @@ __global__ void k_s2_top(RArgs a, int64_t ntiles) {
 // ------------------------------------------------------------------------------------------
 // column arithmetic over F2: symmetric difference of two ascending row lists
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ int thread_symdiff(const int32_t* __restrict__ A, int na,
-                                              const int32_t* __restrict__ B, int nb,
-                                              int32_t* __restrict__ dst) {
-  int i = 0, k = 0, o = 0;
-  while (i < na && k < nb) {
-    int32_t x = A[i], y = B[k];
-    if (x < y) {
-      dst[o++] = x;
-      i++;
-    } else if (y < x) {
-      dst[o++] = y;
-      k++;
-    } else {
-      i++;
-      k++;
-    }
-  }
-  while (i < na) dst[o++] = A[i++];
-  while (k < nb) dst[o++] = B[k++];
-  return o;
-}
-
 // merge-path split on diagonal d with ties taken from A first; an equal pair A[x-1] == B[y]
 // is kept on the same side of the split so that cancellations never straddle two lanes
 __device__ __forceinline__ void merge_split(const int32_t* __restrict__ A, int na,
@@ -334,21 +322,21 @@ __device__ __forceinline__ void merge_split(const int32_t* __restrict__ A, int n
   if (x > 0 && y < nb && A[x - 1] == B[y]) y++;
 }
 
-// warp-cooperative symmetric difference; every lane returns the output length and the last
-// (largest) row written, or -1 for an empty result
+// warp-cooperative symmetric difference straight from global memory (used for merges too long
+// to stage in shared memory); every lane returns the output length and the last row written
 __device__ __forceinline__ int warp_symdiff(const int32_t* __restrict__ A, int na,
                                             const int32_t* __restrict__ B, int nb,
                                             int32_t* __restrict__ dst, int32_t& last) {
+  constexpr int K = 4;
   const int lane = lane_id();
   const int N = na + nb;
   int out = 0;
   last = -1;
-  for (int base = 0; base < N; base += 32 * kMergeK) {
-    int d0 = min(base + lane * kMergeK, N), d1 = min(base + (lane + 1) * kMergeK, N);
+  for (int base = 0; base < N; base += 32 * K) {
+    int d0 = min(base + lane * K, N), d1 = min(base + (lane + 1) * K, N);
     int x0, y0, x1, y1;
     merge_split(A, na, B, nb, d0, x0, y0);
     merge_split(A, na, B, nb, d1, x1, y1);
-    // pass 1: count
     int cnt = 0;
     {
       int i = x0, k = y0;
@@ -390,76 +378,268 @@ __device__ __forceinline__ int warp_symdiff(const int32_t* __restrict__ A, int n
   return out;
 }
 
-__global__ void __launch_bounds__(kThreads) k_add(RArgs a) {
-  __shared__ int64_t sh[kWarps + 1];
-  const int lane = lane_id();
-  int64_t tile0 = (int64_t)blockIdx.x * kRTile;
-  int64_t cs = a.tile_cnt[2 * blockIdx.x];      // survivors before this tile
-  int64_t cw = a.tile_cnt[2 * blockIdx.x + 1];  // words before this tile
-  int64_t n_add = 0, n_xor = 0, n_copy = 0;
-  for (int it = 0; it < kRItems; it++) {
-    int64_t e = tile0 + it * kThreads + threadIdx.x;
-    Job jb = job_of(a, e);
-    int64_t ts, tw;
-    int64_t ps = block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, ts);
-    int64_t pw = block_excl_sum<int64_t>(jb.words, sh, tw);
-    int64_t pos = cs + ps, off = cw + pw;
-    cs += ts;
-    cw += tw;
+// Per-warp shared staging: the columns (A then B) of a batch of the warp's jobs, stored back
+// to back, and per-job bookkeeping. kStage rows per warp bound a staged merge.
+constexpr int kStage = 1024;
+struct WarpStage {
+  int32_t in[kStage];
+  int32_t na[32];
+  int32_t nin[32];      // rows staged for the job (na + nb), 0 if not staged
+  int32_t in_off[33];   // exclusive prefix of nin over the warp's lanes
+  int32_t pad_off[33];  // exclusive prefix of nin rounded up to km
+  int32_t jstart[32];   // first output row of the job, relative to the warp's output base
+  int32_t jcnt[32];     // output rows of the job
+  int32_t jlow[32];     // largest output row (new low), -1 if none
+};
+constexpr size_t kAddSmem = sizeof(WarpStage) * kWarps;
 
-    // describe the job: copy (src == nullptr) or symmetric difference into dst
-    const int32_t* A = nullptr;
-    const int32_t* B = nullptr;
-    int na = 0, nb = 0;
-    int32_t* dst = nullptr;
-    bool active = false;
-    if (jb.j >= 0) {
-      if (jb.newpiv) {
-        na = a.clen[jb.j];
-        A = a.cptr[jb.j];
-        unsigned long long w0 = atomicAdd(a.piv_bump, (unsigned long long)na);
-        dst = a.piv_base + w0;
-        active = true;
-      } else if (jb.surv) {
-        a.act2[pos] = jb.j;
-        na = a.clen[jb.j];
-        A = a.cptr[jb.j];
-        if (jb.src >= 0) {
-          B = a.cptr[jb.src];
-          nb = a.clen[jb.src];
-        }
-        dst = a.arena_next + off;
-        active = true;
-      } else {
-        a.nxt_ptr[e] = nullptr;
-        a.nxt_len[e] = 0;
-      }
+// merge the staged rows A[x0..x1), B[y0..y1) of one lane's range; equal rows cancel.
+// With WRITE, the surviving rows go to dst; returns their count and the last one in *last.
+template <bool WRITE>
+__device__ __forceinline__ int lane_symdiff(const int32_t* __restrict__ sA, int x0, int x1,
+                                            const int32_t* __restrict__ sB, int y0, int y1,
+                                            int32_t* __restrict__ dst, int32_t* last) {
+  int cnt = 0;
+  int32_t va = x0 < x1 ? sA[x0] : INT32_MAX;
+  int32_t vb = y0 < y1 ? sB[y0] : INT32_MAX;
+  int i = x0, j = y0;
+  int32_t v = -1;
+  while (i < x1 || j < y1) {
+    if (va == vb) {
+      ++i;
+      ++j;
+      va = i < x1 ? sA[i] : INT32_MAX;
+      vb = j < y1 ? sB[j] : INT32_MAX;
+    } else if (va < vb) {
+      v = va;
+      if (WRITE) dst[cnt] = v;
+      ++cnt;
+      ++i;
+      va = i < x1 ? sA[i] : INT32_MAX;
+    } else {
+      v = vb;
+      if (WRITE) dst[cnt] = v;
+      ++cnt;
+      ++j;
+      vb = j < y1 ? sB[j] : INT32_MAX;
     }
-    bool big = active && (na + nb) > a.warp_min;
-    if (active && !big) {
-      int len;
+  }
+  if (WRITE) *last = v;
+  return cnt;
+}
+
+// Phase II for one 256-entry chunk of the active list per block. After one block scan for the
+// output offsets, every warp works on its own 32 jobs: new pivots are copied to the pivot store;
+// survivors (with or without an addition) are staged in shared memory and merged by a merge
+// path over the concatenation of all of the batch's jobs, each job padded to a multiple of km
+// positions so that a lane's km positions never span two jobs (km is chosen per warp from the
+// mean merge length); outputs are written compactly and in order into the warp's region of the
+// next arena. Merges longer than the staging bound run from global memory.
+__global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
+  __shared__ int64_t sh[kWarps + 1];
+  extern __shared__ __align__(16) unsigned char add_smem[];
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[w];
+  const int64_t chunk = blockIdx.x, tile = chunk / kRItems;
+  int64_t cs = a.tile_cnt[2 * tile], cw = a.tile_cnt[2 * tile + 1];
+  for (int64_t c = tile * kRItems; c < chunk; c++) {
+    cs += a.chunk_cnt[2 * c];
+    cw += a.chunk_cnt[2 * c + 1];
+  }
+  const int64_t e = chunk * kThreads + threadIdx.x;
+  Job jb = job_of(a, e);
+  int64_t ts, tw;
+  const int64_t pos = cs + block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, ts);
+  const int64_t off = cw + block_excl_sum<int64_t>(jb.words, sh, tw);
+  int64_t n_add = 0, n_xor = 0, n_copy = 0;
+
+  const int32_t* A = nullptr;
+  const int32_t* B = nullptr;
+  int na = 0, nb = 0;
+  if (jb.j >= 0 && (jb.newpiv || jb.surv)) {
+    A = a.cptr[jb.j];
+    na = a.clen[jb.j];
+    if (jb.surv && jb.src >= 0) {
+      B = a.cptr[jb.src];
+      nb = a.clen[jb.src];
+    }
+  }
+  if (jb.j >= 0 && !jb.newpiv && !jb.surv) {
+    a.nxt_ptr[e] = nullptr;
+    a.nxt_len[e] = 0;
+  }
+  if (jb.surv) a.act2[pos] = jb.j;
+
+  // ---- new pivots: their columns never change again; move them to the pivot store
+  unsigned pmask = __ballot_sync(0xffffffffu, jb.newpiv);
+  while (pmask) {
+    const int src = __ffs(pmask) - 1;
+    pmask &= pmask - 1;
+    const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src);
+    const int wna = __shfl_sync(0xffffffffu, na, src);
+    unsigned long long w0 = 0;
+    if (lane == src) w0 = atomicAdd(a.piv_bump, (unsigned long long)wna);
+    w0 = __shfl_sync(0xffffffffu, w0, src);
+    int32_t* dst = a.piv_base + w0;
+    for (int q = lane; q < wna; q += 32) dst[q] = wA[q];
+    if (lane == src) {
+      a.nxt_ptr[e] = dst;
+      a.nxt_len[e] = wna;
+      n_copy += wna;
+    }
+  }
+
+  // ---- survivors
+  const unsigned smask = __ballot_sync(0xffffffffu, jb.surv);
+  if (smask) {
+    const int first = __ffs(smask) - 1;
+    const int64_t wbase = __shfl_sync(0xffffffffu, off, first);  // warp's output region
+    const int N = jb.surv ? na + nb : 0;
+    const bool big = N > a.staged_max;
+    const int nin = big ? 0 : N;
+    const int in_ex = warp_incl_sum(nin) - nin;
+    const int small_total = __shfl_sync(0xffffffffu, in_ex + nin, 31);
+    const int n_staged = __popc(__ballot_sync(0xffffffffu, nin > 0));
+    const int mean = n_staged ? small_total / n_staged : 0;
+    // longer chunks amortise the two merge-path splits, shorter ones keep lanes balanced
+    const int km = a.force_km > 0 ? a.force_km
+                                  : (mean >= 160 ? 32 : (mean >= 80 ? 16 : (mean >= 32 ? 8 : 4)));
+    const int npad = (nin + km - 1) / km * km;
+    const int pad_ex = warp_incl_sum(npad) - npad;
+    const int bigN = big ? N : 0;
+    const int big_ex = warp_incl_sum(bigN) - bigN;
+    S.na[lane] = na;
+    S.nin[lane] = nin;
+    S.in_off[lane] = in_ex;
+    S.pad_off[lane] = pad_ex;
+    S.jstart[lane] = 0;
+    S.jcnt[lane] = 0;
+    S.jlow[lane] = -1;
+    if (lane == 31) {
+      S.in_off[32] = in_ex + nin;
+      S.pad_off[32] = pad_ex + npad;
+    }
+    __syncwarp();
+    int32_t* out = a.arena_next + wbase;  // compact outputs of the staged jobs
+    int ocur = 0;
+    int c = 0;
+    while (c < 32) {
+      // batch: jobs c.. whose staged rows fit together
+      const int in_c = S.in_off[c];
+      const bool fits = lane >= c && S.in_off[lane] + S.nin[lane] - in_c <= kStage;
+      const int c_end = c + __popc(__ballot_sync(0xffffffffu, fits));
+      const int nch = (S.pad_off[c_end] - S.pad_off[c]) / km;
+      const bool mine = lane >= c && lane < c_end && nin > 0;
+      if (__ballot_sync(0xffffffffu, mine)) {
+        // stage: columns of 32+ rows by the whole warp (coalesced), shorter ones by their lane
+        unsigned lmask = __ballot_sync(0xffffffffu, mine && nin >= 32);
+        while (lmask) {
+          const int src = __ffs(lmask) - 1;
+          lmask &= lmask - 1;
+          const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src);
+          const int32_t* wB = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)B, src);
+          const int wna = __shfl_sync(0xffffffffu, na, src);
+          const int wn = __shfl_sync(0xffffffffu, nin, src);
+          int32_t* d = S.in + (__shfl_sync(0xffffffffu, in_ex, src) - in_c);
+          for (int q = lane; q < wn; q += 64) {
+            const int q2 = q + 32;
+            const int32_t v0 = q < wna ? __ldg(wA + q) : __ldg(wB + (q - wna));
+            int32_t v1 = 0;
+            if (q2 < wn) v1 = q2 < wna ? __ldg(wA + q2) : __ldg(wB + (q2 - wna));
+            d[q] = v0;
+            if (q2 < wn) d[q2] = v1;
+          }
+        }
+        if (mine && nin < 32) {
+          int32_t* d = S.in + (in_ex - in_c);
+          int q = 0;
+          for (; q + 4 <= na; q += 4) {
+            const int32_t v0 = __ldg(A + q), v1 = __ldg(A + q + 1), v2 = __ldg(A + q + 2),
+                          v3 = __ldg(A + q + 3);
+            d[q] = v0;
+            d[q + 1] = v1;
+            d[q + 2] = v2;
+            d[q + 3] = v3;
+          }
+          for (; q < na; q++) d[q] = __ldg(A + q);
+          int r = 0;
+          for (; r + 4 <= nb; r += 4) {
+            const int32_t v0 = __ldg(B + r), v1 = __ldg(B + r + 1), v2 = __ldg(B + r + 2),
+                          v3 = __ldg(B + r + 3);
+            d[na + r] = v0;
+            d[na + r + 1] = v1;
+            d[na + r + 2] = v2;
+            d[na + r + 3] = v3;
+          }
+          for (; r < nb; r++) d[na + r] = __ldg(B + r);
+        }
+        __syncwarp();
+        // merge: lane takes one km-position chunk per round
+        const int p0 = S.pad_off[c];
+        for (int h0 = 0; h0 < nch; h0 += 32) {
+          const int h = h0 + lane;
+          int cnt = 0, k = -1, x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+          const int32_t* sA = S.in;
+          const int32_t* sB = S.in;
+          if (h < nch) {
+            const int gp = p0 + h * km;
+            int lo = c, hi = c_end - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (S.pad_off[mid] <= gp) lo = mid; else hi = mid - 1;
+            }
+            k = lo;
+            const int d = gp - S.pad_off[k];
+            const int nk = S.nin[k];
+            if (d < nk) {
+              sA = S.in + (S.in_off[k] - in_c);
+              const int ka = S.na[k], kb = nk - ka;
+              sB = sA + ka;
+              merge_split(sA, ka, sB, kb, d, x0, y0);
+              merge_split(sA, ka, sB, kb, min(d + km, nk), x1, y1);
+              cnt = lane_symdiff<false>(sA, x0, x1, sB, y0, y1, nullptr, nullptr);
+            }
+          }
+          const int incl = warp_incl_sum(cnt);
+          const int o = ocur + incl - cnt;
+          if (k >= 0) {
+            if (h * km == S.pad_off[k] - p0) S.jstart[k] = o;
+            if (cnt) {
+              int32_t last;
+              lane_symdiff<true>(sA, x0, x1, sB, y0, y1, out + o, &last);
+              atomicAdd(&S.jcnt[k], cnt);
+              atomicMax(&S.jlow[k], last);
+            }
+          }
+          ocur += __shfl_sync(0xffffffffu, incl, 31);
+        }
+      }
+      __syncwarp();
+      c = c_end;
+    }
+    __syncwarp();
+    if (jb.surv && !big) {
+      const int len = S.jcnt[lane];
+      a.nxt_ptr[e] = out + S.jstart[lane];
+      a.nxt_len[e] = len;
       if (B) {
-        len = thread_symdiff(A, na, B, nb, dst);
-        a.low[jb.j] = len ? dst[len - 1] : -1;
+        a.low[jb.j] = S.jlow[lane];
         n_add++;
         n_xor += (na + nb + len) / 2;
       } else {
-        for (int q = 0; q < na; q++) dst[q] = A[q];
-        len = na;
         n_copy += na;
       }
-      a.nxt_ptr[e] = dst;
-      a.nxt_len[e] = len;
     }
-    unsigned bigmask = __ballot_sync(0xffffffffu, big);
-    while (bigmask) {
-      int src_lane = __ffs(bigmask) - 1;
-      bigmask &= bigmask - 1;
-      const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src_lane);
-      const int32_t* wB = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)B, src_lane);
-      int32_t* wd = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)dst, src_lane);
-      int wna = __shfl_sync(0xffffffffu, na, src_lane);
-      int wnb = __shfl_sync(0xffffffffu, nb, src_lane);
+    // merges too long to stage: straight from global memory, after the staged outputs
+    unsigned bmask = __ballot_sync(0xffffffffu, big);
+    while (bmask) {
+      const int src = __ffs(bmask) - 1;
+      bmask &= bmask - 1;
+      const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src);
+      const int32_t* wB = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)B, src);
+      const int wna = __shfl_sync(0xffffffffu, na, src);
+      const int wnb = __shfl_sync(0xffffffffu, nb, src);
+      int32_t* wd = a.arena_next + wbase + small_total + __shfl_sync(0xffffffffu, big_ex, src);
       int len;
       int32_t last = -1;
       if (wB) {
@@ -468,7 +648,7 @@ __global__ void __launch_bounds__(kThreads) k_add(RArgs a) {
         for (int q = lane; q < wna; q += 32) wd[q] = wA[q];
         len = wna;
       }
-      if (lane == src_lane) {
+      if (lane == src) {
         if (B) {
           a.low[jb.j] = last;
           n_add++;
@@ -476,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) k_add(RArgs a) {
         } else {
           n_copy += na;
         }
-        a.nxt_ptr[e] = dst;
+        a.nxt_ptr[e] = wd;
         a.nxt_len[e] = len;
       }
     }
@@ -571,7 +751,7 @@ void reduce_init(ph_ctx* ctx) {
   int nseg = (int)ctx->seg_start.size() - 1;
   rs.first_unp = alloc_n<int32_t>(ctx, nseg);
   int64_t ntiles = (m + kRTile - 1) / kRTile;
-  rs.tiles_bytes = ntiles * (sizeof(SegMax) + 4 * sizeof(int64_t));
+  rs.tiles_bytes = ntiles * ((1 + kRItems) * sizeof(SegMax) + (4 + 2 * kRItems) * sizeof(int64_t));
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
   rs.totals = alloc_n<int64_t>(ctx, 8);
   PH_CUDA(cudaMallocHost(&rs.h_totals, 8 * sizeof(int64_t)));
@@ -632,7 +812,9 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   a.cor10 = ctx->opts.use_cor10;
   a.totals = rs.totals;
   a.piv_bump = (unsigned long long*)rs.piv_bump;
-  a.warp_min = ctx->opts.warp_merge_min > 0 ? ctx->opts.warp_merge_min : 48;
+  a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
+                                                 : kStage;
+  a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
 
   for (int pass = rs.next_pass;; pass++) {
     const int64_t n_act = rs.n_act;
@@ -640,9 +822,12 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     a.act = rs.act;
     a.act2 = rs.act2;
     a.n_act = n_act;
+    const int64_t nchunks = std::max<int64_t>((n_act + kThreads - 1) / kThreads, 1);
     a.tile_sm = (SegMax*)rs.tiles;
-    a.tile_cnt = (int64_t*)((char*)rs.tiles + ntiles * sizeof(SegMax));
+    a.chunk_sm = a.tile_sm + ntiles;
+    a.tile_cnt = (int64_t*)(a.chunk_sm + ntiles * kRItems);
     a.tile_aux = a.tile_cnt + 2 * ntiles;
+    a.chunk_cnt = a.tile_aux + 2 * ntiles;
     a.do_adds = pass < max_passes;
     if (stats) {
       if (pass >= rs.stats_rows) {
@@ -670,7 +855,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     PH_CHECK_LAUNCH();
     k_p1_top<<<1, kThreads, 0, st>>>(a.tile_sm, ntiles);
     PH_CHECK_LAUNCH();
-    k_mark<<<(unsigned)ntiles, kThreads, 0, st>>>(a);
+    k_mark<<<(unsigned)nchunks, kThreads, 0, st>>>(a);
     PH_CHECK_LAUNCH();
     k_s2_tiles<<<(unsigned)ntiles, kThreads, 0, st>>>(a);
     PH_CHECK_LAUNCH();
@@ -705,7 +890,9 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
       rs.ev.push_back(e1);
       PH_CUDA(cudaEventRecord(e0, st));
     }
-    k_add<<<(unsigned)ntiles, kThreads, 0, st>>>(a);
+    PH_CUDA(cudaFuncSetAttribute(k_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kAddSmem));
+    k_add<<<(unsigned)nchunks, kThreads, kAddSmem, st>>>(a);
     PH_CHECK_LAUNCH();
     rs.add_launches++;
     if (ctx->opts.time_kernels) PH_CUDA(cudaEventRecord(rs.ev.back(), st));

@@ -28,8 +28,8 @@ class PHError(RuntimeError):
 
 class PhOpts(Structure):
     _fields_ = [("strict_phase2", c_int32), ("use_cor10", c_int32), ("block_threads", c_int32),
-                ("warp_merge_min", c_int32), ("collect_stats", c_int32), ("use_graph", c_int32),
-                ("time_kernels", c_int32)]
+                ("staged_merge_max", c_int32), ("merge_items", c_int32),
+                ("collect_stats", c_int32), ("use_graph", c_int32), ("time_kernels", c_int32)]
 
 
 class PhStats(Structure):
@@ -109,8 +109,8 @@ class Context:
     """One library context: a filtration (of one or many clouds) and its reduction."""
 
     def __init__(self, *, strict_phase2: bool = False, use_cor10: bool = True,
-                 collect_stats: bool = False, warp_merge_min: int = 0, use_graph: bool = False,
-                 time_kernels: bool = False, stream=None):
+                 collect_stats: bool = False, staged_merge_max: int = 0, merge_items: int = 0,
+                 use_graph: bool = False, time_kernels: bool = False, stream=None):
         torch = _torch()
         self._torch = torch
         self.lib = load_library()
@@ -119,8 +119,9 @@ class Context:
         opts.strict_phase2 = int(strict_phase2)
         opts.use_cor10 = int(use_cor10)
         opts.collect_stats = int(collect_stats)
-        if warp_merge_min:
-            opts.warp_merge_min = int(warp_merge_min)
+        if staged_merge_max:
+            opts.staged_merge_max = int(staged_merge_max)
+        opts.merge_items = int(merge_items)
         opts.use_graph = int(use_graph)
         opts.time_kernels = int(time_kernels)
         self.stream = stream if stream is not None else torch.cuda.current_stream()

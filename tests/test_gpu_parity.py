@@ -138,16 +138,17 @@ def test_modes(ph, orc, strict, cor10):
     assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
 
 
-def test_merge_paths_agree(ph, orc):
-    # every column through the warp-cooperative merge, then every column through one thread
+@pytest.mark.parametrize("staged_max,items", [(1, 4), (16, 2), (0, 1), (0, 3), (0, 8),
+                                              (40, 8), (0, 32), (100, 16), (0, 0), (0, 64)])
+def test_merge_paths_agree(ph, orc, staged_max, items):
+    # staged_max = 1: every merge from global memory; 16 / 40: mixed; 0: all staged
     x = pc.random_cloud(60, 3, 12)
     K = orc.vr_build(x, 2)
     ref = orc.reduce_pms(K)
-    for wmin in (1, 1 << 30):
-        ctx = _gpu(ph, x, 2, warp_merge_min=wmin)
-        ctx.reduce()
-        assert np.array_equal(ctx.filtration(0)["low"], ref.low)
-        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+    ctx = _gpu(ph, x, 2, staged_merge_max=staged_max, merge_items=items)
+    ctx.reduce()
+    assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
 
 
 def test_batched_clouds(ph, orc):
