@@ -137,6 +137,14 @@ int ph_build_filtration(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud
                         int32_t n_clouds, int64_t n_points, int32_t D, int32_t max_dim,
                         int64_t max_diam2, int64_t* m_out);
 
+/* As ph_build_filtration, from fp32 coordinates (device float [N][D], plain units): each is
+ * rounded on the device to the 2^-16 grid, rint(x * 65536) with ties to even, and must be
+ * finite with |x| <= 256 (PH_ERR_INVALID otherwise). The pairing is computed from the rounded
+ * values; ph_diagram_loss / ph_diagram_backward use the fp32 values. */
+int ph_build_filtration_f32(ph_ctx* ctx, const float* coords, const int64_t* cloud_offsets,
+                            int32_t n_clouds, int64_t n_points, int32_t D, int32_t max_dim,
+                            int64_t max_diam2, int64_t* m_out);
+
 /* Loads an explicit filtration of one complex instead of building a VR one.
  *   m             number of simplices, in a compatible order (faces before cofaces).
  *   dims          host int32 [m], dimension of each simplex (0..15).
@@ -193,6 +201,26 @@ int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int
  * copied. Synchronises the stream. */
 int ph_get_filtration(ph_ctx* ctx, int32_t cloud, int32_t* dim, int64_t* diam2, int32_t* verts,
                       int32_t* beta, int32_t* low, int64_t* count);
+
+/* Diagram loss of a reduced VR filtration: over the finite pairs (sigma_b, sigma_d) whose birth
+ * simplex has dimension `dim` (Lemma 1), b and d are the fp32 Euclidean lengths of the edges that
+ * realise the diameters of sigma_b and sigma_d (Sec. 2.2: the VR value of a simplex is its
+ * diameter; a simplex's realising edge is itself for an edge, else the realising edge of its
+ * last face in the filtration), and loss = sum (d - b)^2 per cloud. The pairing is exact and
+ * piecewise constant, so only b and d carry gradient.
+ *   coords   device float [N][D], the coordinates the filtration was built from.
+ *   loss     device float [n_clouds + 1]: per-cloud losses, then their sum.
+ *   n_pairs  host, optional: number of pairs summed.
+ * Needs ph_reduce first and dim + 1 <= max_dim. Synchronises the stream. */
+int ph_diagram_loss(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim, float* loss,
+                    int64_t* n_pairs);
+
+/* Gradient of the per-cloud losses of ph_diagram_loss with respect to the coordinates:
+ * grad_coords (device float [N][D]) += sum over clouds of grad_loss[c] * d loss_c / d coords,
+ * scattered to the two points of each realising edge (a zero-length edge contributes nothing).
+ *   grad_loss  device float [n_clouds]. Asynchronous. */
+int ph_diagram_backward(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim,
+                        const float* grad_loss, float* grad_coords);
 
 /* Allocation-free beta, for callers that cannot allocate device memory: code running inside
  * another framework's memory pool or arena, programs that forbid allocation after start-up,

@@ -218,3 +218,52 @@ def persistence_summary(K: Complex, low: np.ndarray):
         maxd + 1, np.int64)
     ness = np.bincount(K["dim"][ess], minlength=maxd + 1)
     return npairs, ness
+
+
+# ----------------------------------------------------------------------------------------------
+# Differentiable diagram loss (FP64 reference). The pairing comes from lowstar; the birth and
+# death values of a pair are Euclidean diameters (Sec. 2.2); a simplex's diameter is realised by
+# an edge: an edge by itself, a higher simplex by the realising edge of its last face in the
+# filtration (the largest row of its boundary column).
+# ----------------------------------------------------------------------------------------------
+def realising_edge(K: Complex, x: int):
+    while K["dim"][x] > 1:
+        x = int(K["rows"][K["colptr"][x + 1] - 1])
+    return int(K["verts"][x, 0]), int(K["verts"][x, 1])
+
+
+def diagram_edges(K: Complex, low: np.ndarray, dim: int) -> np.ndarray:
+    """(p, q, r, s) per finite pair whose birth simplex has dimension `dim`: birth realised by
+    edge (p, q) (-1, -1 for a vertex birth), death by edge (r, s)."""
+    out = []
+    for j in np.nonzero((np.asarray(low) >= 0) & (K["dim"] == dim + 1))[0]:
+        r, s = realising_edge(K, int(j))
+        b = int(low[j])
+        p, q = realising_edge(K, b) if K["dim"][b] >= 1 else (-1, -1)
+        out.append((p, q, r, s))
+    return np.array(out, np.int64).reshape(-1, 4)
+
+
+def diagram_loss_grad(x: np.ndarray, edges: np.ndarray):
+    """loss = sum over pairs (d - b)^2 with b = |x_p - x_q|, d = |x_r - x_s| (float64), and its
+    gradient with respect to x; zero-length edges contribute no gradient."""
+    x = np.asarray(x, np.float64)
+    grad = np.zeros_like(x)
+    loss = 0.0
+    for p, q, r, s in edges:
+        dv = x[r] - x[s]
+        d = float(np.sqrt(dv @ dv))
+        if p >= 0:
+            bv = x[p] - x[q]
+            b = float(np.sqrt(bv @ bv))
+        else:
+            bv, b = None, 0.0
+        loss += (d - b) ** 2
+        g = 2.0 * (d - b)
+        if d > 0:
+            grad[r] += g * dv / d
+            grad[s] -= g * dv / d
+        if p >= 0 and b > 0:
+            grad[p] -= g * bv / b
+            grad[q] += g * bv / b
+    return loss, grad

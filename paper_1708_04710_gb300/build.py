@@ -15,7 +15,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libph_gb300.so"
-SOURCES = ["ph_scan.cu", "ph_build.cu", "ph_reduce.cu", "ph_api.cu", "ph_noalloc.cu"]
+SOURCES = ["ph_scan.cu", "ph_build.cu", "ph_reduce.cu", "ph_api.cu", "ph_diff.cu",
+           "ph_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -46,7 +46,7 @@ void ph_ctx::free_all() {
     else cudaFreeAsync(b.p, stream);
   }
   blocks.clear();
-  built = reduced = extracted = false;
+  built = reduced = extracted = is_vr = false;
   seg = low = beta = key = rows0 = nullptr;
   gidx = nullptr;
   verts = nullptr;
@@ -313,6 +313,7 @@ int ph_build_filtration(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud
   ctx->free_all();
   ph::build_vr(ctx, coords, cloud_offsets, n_clouds, n_points, D, max_dim, max_diam2);
   ctx->built = true;
+  ctx->is_vr = true;
   if (m_out) *m_out = ctx->m;
   return PH_OK;
   PH_API_END

@@ -91,6 +91,7 @@ struct ph_ctx {
   // filtration
   bool built = false;
   bool reduced = false;
+  bool is_vr = false;  // built from points (vertex tuples known)
   int32_t n_clouds = 0;
   int32_t max_dim = 0;
   int64_t m = 0;

@@ -53,7 +53,12 @@ SIGNATURES = {
     "ph_destroy": (None, [c_void_p]),
     "ph_build_filtration": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int64, c_int32,
                                     c_int32, c_int64, POINTER(c_int64)]),
+    "ph_build_filtration_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int64,
+                                        c_int32, c_int32, c_int64, POINTER(c_int64)]),
     "ph_load_boundary": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "ph_diagram_loss": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p,
+                                POINTER(c_int64)]),
+    "ph_diagram_backward": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
     "ph_reduce": (c_int, [c_void_p, c_int32, POINTER(PhStats)]),
     "ph_reset_reduction": (c_int, [c_void_p]),
     "ph_get_pass_stats": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
@@ -185,6 +190,44 @@ class Context:
         self.n_clouds = nc
         self.m = m.value
         return self.m
+
+    def build_filtration_f32(self, coords, cloud_offsets=None, max_dim: int = 2,
+                             max_diam2: int = -1) -> int:
+        """coords: float32 CUDA tensor (N, D); rounded to the grid on the device."""
+        torch = self._torch
+        assert coords.is_cuda and coords.dtype == torch.float32 and coords.dim() == 2
+        coords = coords.contiguous()
+        N, D = coords.shape
+        offs = None if cloud_offsets is None else np.ascontiguousarray(
+            np.asarray(cloud_offsets, dtype=np.int64))
+        nc = 1 if offs is None else len(offs) - 1
+        m = c_int64(0)
+        self._check(self.lib.ph_build_filtration_f32(self._h, _ptr(coords), _ptr(offs), nc, N, D,
+                                                     max_dim, int(max_diam2), byref(m)))
+        self.n_clouds = nc
+        self.m = m.value
+        return self.m
+
+    def diagram_loss(self, coords, dim: int = 1):
+        """Per-cloud losses followed by their sum (float32 tensor, n_clouds + 1)."""
+        torch = self._torch
+        coords = coords.contiguous()
+        out = torch.empty(self.n_clouds + 1, dtype=torch.float32, device=coords.device)
+        n = c_int64(0)
+        self._check(self.lib.ph_diagram_loss(self._h, _ptr(coords), coords.shape[1], dim,
+                                             _ptr(out), byref(n)))
+        self.last_pairs = n.value
+        return out
+
+    def diagram_backward(self, coords, grad_loss, dim: int = 1, grad=None):
+        torch = self._torch
+        coords = coords.contiguous()
+        if grad is None:
+            grad = torch.zeros_like(coords)
+        g = grad_loss.contiguous().to(torch.float32)
+        self._check(self.lib.ph_diagram_backward(self._h, _ptr(coords), coords.shape[1], dim,
+                                                 _ptr(g), _ptr(grad)))
+        return grad
 
     def load_boundary(self, dims, colptr, rows):
         dims = np.ascontiguousarray(dims, np.int32)

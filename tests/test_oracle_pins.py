@@ -230,3 +230,38 @@ def test_gf2_rank_helper_sanity():
     assert gf2_rank(np.eye(5, dtype=np.uint8)) == 5
     assert gf2_rank(np.array([[1, 1, 0], [0, 1, 1], [1, 0, 1]], np.uint8)) == 2
     assert gf2_rank(np.ones((3, 3), np.uint8)) == 1
+
+
+def test_diagram_gradient_central_differences(orc):
+    # the oracle's analytic gradient against FP64 central differences (h = 1e-3) of the loss
+    # with the pairing frozen (the pairing is piecewise constant in the coordinates)
+    rng = np.random.Generator(np.random.PCG64(17))
+    x = pc.sphere(24, rng, noise=0.02)
+    K = orc.vr_build(pc.to_grid(x), 2)
+    low = orc.reduce_twist(K)[0]
+    for dim in (0, 1):
+        edges = orc.diagram_edges(K, low, dim)
+        assert len(edges) > 0
+        loss, g = orc.diagram_loss_grad(x, edges)
+        h = 1e-3
+        fd = np.zeros_like(x)
+        for i in range(x.shape[0]):
+            for k in range(x.shape[1]):
+                xp = x.copy()
+                xp[i, k] += h
+                xm = x.copy()
+                xm[i, k] -= h
+                fd[i, k] = (orc.diagram_loss_grad(xp, edges)[0]
+                            - orc.diagram_loss_grad(xm, edges)[0]) / (2 * h)
+        assert np.abs(fd - g).max() <= 1e-4 * np.abs(g).max()
+
+
+def test_diagram_edges_realise_diameters(orc):
+    # every realising edge has exactly the squared diameter of its simplex (Sec. 2.2)
+    x = pc.random_cloud(14, 3, 33)
+    K = orc.vr_build(x, 3)
+    for j in range(K.m):
+        if K["dim"][j] >= 1:
+            p, q = orc.realising_edge(K, j)
+            d2 = int(((x[p].astype(np.int64) - x[q]) ** 2).sum())
+            assert d2 == K["diam2"][j]
