@@ -154,6 +154,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus400", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -182,15 +183,15 @@ def main():
     wl = WORKLOADS[args.workload]
     x = wl["gen"]()
     coords = torch.from_numpy(x).to(dev)
-    ctx = ph.Context(collect_stats=True, time_kernels=True)
+    ctx = ph.Context()  # the library's defaults: pass loop in one CUDA graph
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(c):
-        ctx.build_filtration(c, None, wl["max_dim"], wl["max_diam2"])
-        st = ctx.reduce()
-        ctx.pairs(0, on_device=True)
-        ctx.essential(0, on_device=True)
+    def step(c, context=ctx):
+        context.build_filtration(c, None, wl["max_dim"], wl["max_diam2"])
+        st = context.reduce()
+        context.pairs(0, on_device=True)
+        context.essential(0, on_device=True)
         return st
 
     for _ in range(max(args.warmup, 0)):
@@ -259,10 +260,17 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
+
+    # the dominant kernel, k_add, timed with CUDA events on the library's stream around every
+    # launch: the same workload through the host-driven pass loop (events cannot sit inside the
+    # graph's conditional body), with per-pass counters for its algorithmic bytes
+    prof = ph.Context(use_graph=False, collect_stats=True, time_kernels=True)
+    step(coords, prof)
+    pst = [step(coords, prof) for _ in range(2)]
     peak, peak_kind = _peak_hbm()
-    add_bytes = sum(s["add_bytes"] for s in stats)
-    add_ms = sum(s["ms_add"] for s in stats)
-    add_launches = sum(s["add_launches"] for s in stats)
+    add_bytes = sum(s["add_bytes"] for s in pst)
+    add_ms = sum(s["ms_add"] for s in pst)
+    add_launches = sum(s["add_launches"] for s in pst)
     achieved = (add_bytes / add_launches) / (add_ms / add_launches / 1e3) / 1e9 if add_ms else None
     traffic = _profile_traffic("k_add", args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -271,20 +279,26 @@ def main():
                 "peak_kind": peak_kind,
                 "bytes_per_launch": add_bytes / max(add_launches, 1),
                 "ms_per_launch": add_ms / max(add_launches, 1),
-                "share_of_step": add_ms / total_ms * world if total_ms else None}
+                "launches_per_step": add_launches / len(pst),
+                "share_of_step": (add_ms / len(pst)) / (total_ms / args.steps),
+                "timing": "CUDA events around each k_add launch, host-driven pass loop, "
+                          "same workload, 2 steps after 1 warm-up"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "m": m,
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "pass_loop": "CUDA graph, conditional while node",
                        "l2": "256 MiB buffer written before every timed step"},
-            "passes": stats[-1]["passes"], "col_adds": stats[-1]["col_adds"],
-            "xors": stats[-1]["xors"], "bit_exact_vs_oracle": parity,
+            "passes": stats[-1]["passes"], "col_adds": pst[-1]["col_adds"],
+            "xors": pst[-1]["xors"], "bit_exact_vs_oracle": parity,
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "clocks": clk}
+    if world == 1 and not args.no_forms:
+        line["forms"] = compare_forms(ph, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         n_sample = 250
         ms, secs = cpu_oracle_sample(n_sample)
@@ -295,6 +309,68 @@ def main():
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _timed(torch, fn, reps=2):
+    fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps
+
+
+def compare_forms(ph, torch, dev):
+    """The batched and differentiable forms against the plain form on the same GPU."""
+    out = {}
+    # batched: 512 uneven clouds in one filtration vs one plain filtration per cloud
+    xb, off = pc.batch512()
+    cb = torch.from_numpy(xb).to(dev)
+    ctx = ph.Context()
+
+    def batched():
+        ctx.build_filtration(cb, off, 2)
+        ctx.reduce()
+        ctx.pairs(0)
+
+    def looped():
+        for c in range(len(off) - 1):
+            ctx.build_filtration(cb[off[c]:off[c + 1]].contiguous(), None, 2)
+            ctx.reduce()
+            ctx.pairs(0)
+
+    tb = _timed(torch, batched)
+    mb = ctx.m
+    tl = _timed(torch, looped, reps=1)
+    out["batched"] = {"workload": "batch512: 512 clouds, n ~ U{20..120}, sphere/torus/N(0,I3), "
+                                  "complete VR <= dim 2", "m": mb,
+                      "batched_simplices_per_s": mb / tb, "looped_plain_simplices_per_s": mb / tl,
+                      "batched_ms": 1e3 * tb, "looped_plain_ms": 1e3 * tl}
+    # differentiable: loss + gradient over 256 clouds vs the plain build + reduce of the same
+    from paper_1708_04710_gb300.diff import diagram_loss
+
+    xd, offd = pc.diff256()
+    cd = torch.from_numpy(xd).to(dev)
+    dctx = ph.Context()
+
+    def fwd_bwd():
+        xx = cd.clone().requires_grad_(True)
+        diagram_loss(xx, offd, 1, dctx).sum().backward()
+
+    def plain():
+        dctx.build_filtration_f32(cd, offd, 2)
+        dctx.reduce()
+
+    tf = _timed(torch, fwd_bwd)
+    tp = _timed(torch, plain)
+    out["differentiable"] = {"workload": "diff256: 256 clouds x 64 points on S^2 + noise, "
+                                         "complete VR <= dim 2, loss over H1 pairs",
+                             "m": dctx.m, "forward_backward_ms": 1e3 * tf,
+                             "plain_build_reduce_ms": 1e3 * tp,
+                             "forward_backward_simplices_per_s": dctx.m / tf,
+                             "plain_simplices_per_s": dctx.m / tp}
+    return out
 
 
 if __name__ == "__main__":

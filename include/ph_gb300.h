@@ -74,10 +74,12 @@ typedef struct {
   int32_t merge_items;
   /* 1: per-pass counters are collected (column additions, XORs, pivots, ...) */
   int32_t collect_stats;
-  /* 1: the pass loop runs inside one CUDA graph whose conditional while node reads a device
-   * flag, so no host round trip happens per pass (0 = host-driven loop, the default) */
+  /* 1 (default): the pass loop runs inside one CUDA graph whose conditional while node reads
+   * a device flag, so no host round trip happens per pass; 0: the host launches each pass and
+   * reads the flag. Both run the same kernels on the same device state. */
   int32_t use_graph;
-  /* 1: CUDA events time every launch of the Phase II addition kernel (ph_stats.ms_add) */
+  /* 1: CUDA events time every launch of the Phase II addition kernel (ph_stats.ms_add); only
+   * with use_graph = 0 (events cannot sit inside a conditional graph body) */
   int32_t time_kernels;
 } ph_opts;
 

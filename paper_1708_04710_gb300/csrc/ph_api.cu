@@ -47,6 +47,10 @@ void ph_ctx::free_all() {
   }
   blocks.clear();
   built = reduced = extracted = is_vr = false;
+  // every pointer into the freed blocks must go: a stale one handed to dfree later could match
+  // a new allocation at the same address and free it while it is in use
+  p_birth = p_death = p_bd2 = p_dd2 = e_idx = e_d2 = nullptr;
+  p_dim = e_dim = nullptr;
   seg = low = beta = key = rows0 = nullptr;
   gidx = nullptr;
   verts = nullptr;
@@ -271,7 +275,7 @@ void ph_default_opts(ph_opts* o) {
   o->staged_merge_max = 0;
   o->merge_items = 0;
   o->collect_stats = 0;
-  o->use_graph = 0;
+  o->use_graph = 1;
   o->time_kernels = 0;
 }
 

@@ -34,10 +34,9 @@ struct ColStore {  // a device buffer that holds column storage (int32 rows)
 };
 
 struct ReduceState {
-  int32_t* act = nullptr;      // active ids, ascending
-  int32_t* act2 = nullptr;     // next active list
+  int32_t* act = nullptr;      // active list buffers (which one is current: device state)
+  int32_t* act2 = nullptr;
   int64_t act_cap = 0;
-  int64_t n_act = 0;           // host copy of the active count
   int32_t** cptr = nullptr;    // per id: pointer to its rows
   int32_t* clen = nullptr;     // per id: number of rows
   int32_t** nxt_ptr = nullptr; // per active slot: new location
@@ -47,20 +46,17 @@ struct ReduceState {
   int32_t* first_unp = nullptr;// per segment: first row id not known to be paired
   uint8_t* flags = nullptr;
   uint8_t* cleared = nullptr;  // per id: zeroed by clearing
-  // scan scratch
-  void* tiles = nullptr;
+  void* tiles = nullptr;       // scan scratch
   int64_t tiles_bytes = 0;
-  int64_t* totals = nullptr;   // device [8]: survivors, words, pivot words, targets, ...
-  int64_t* h_totals = nullptr; // pinned host mirror
+  void* dstate = nullptr;      // per-pass state in device memory
+  void* hstate = nullptr;      // pinned host mirror of it
   int64_t* pass_stats = nullptr;  // device [stats_rows][PH_PS_N]
   int32_t stats_rows = 0;
-  ColStore arena[2];
-  int cur = 0;                 // arena holding the active columns
+  ColStore arena[2];           // pass p writes its survivors into arena[p & 1]
   std::vector<ColStore> pivots;  // chunks holding proven columns
-  int64_t piv_used = 0;        // words used in the last chunk
-  int64_t* piv_bump = nullptr; // device bump pointer of the last chunk
+  cudaGraph_t graph = nullptr;   // one pass as the body of a conditional while node
+  cudaGraphExec_t graph_exec = nullptr;
   int32_t passes = 0;
-  int32_t next_pass = 0;      // pass index a resumed reduction starts from
   bool init = false;
   bool done = false;
   int status = PH_OK;

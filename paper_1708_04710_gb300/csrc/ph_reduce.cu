@@ -6,10 +6,13 @@
 //                that is not known to be paired (for Corollary 10).
 //   k_tab        tab[low(j)] <- min j over the active columns (atomicMin): the left-most column
 //                with each low, which defines the neighbour sets N(j) (Eq. neighbours).
-//   k_p1_tiles / k_p1_top / k_mark
+//   k_p1_tiles / k_p1_top
 //                Phase I (Algorithm 5) as a segmented exclusive prefix-max over the active
-//                columns of each (cloud, dim): P_j = largest low of an earlier colliding column.
-//                j is proven if it is left-most for its low and low(j) = beta_j (Thm 5) or
+//                columns of each (cloud, dim): P_j = largest low of an earlier colliding column;
+//                also upper bounds of the space this pass can need.
+//   k_check      stops the pass before anything changes if the bounds exceed the space the host
+//                provided (the host then grows it and the pass runs again).
+//   k_mark       j is proven if it is left-most for its low and low(j) = beta_j (Thm 5) or
 //                low(j) > P_j (Thms 6-7). Empty columns become final; the zero case of
 //                Corollary 10 zeroes a column whose candidate rows are all paired. Each new
 //                pivot clears column low(j) (Lemma 1).
@@ -18,8 +21,13 @@
 //   k_add        Phase II: every colliding column l gets column tab[low(l)] added (XOR of two
 //                sorted row lists). Sources are left-most, hence never targets, so additions
 //                are independent. Survivors are written compactly into the other arena, new
-//                pivots move to the pivot store (their columns never change again).
+//                pivots move to the pivot store (their columns never change again). Blocks
+//                take 256-column chunks from a device work queue.
 //   k_commit     publishes the new column locations and the next active list.
+//   k_end        advances the pass, decides convergence (no collision left, Thm 8) and, inside a
+//                CUDA graph, sets the conditional that repeats the pass.
+// All per-pass state lives in device memory (DevState), so the same kernel sequence runs either
+// from a host loop or as the body of a graph's conditional while node.
 #include <algorithm>
 
 #include "ph_internal.cuh"
@@ -29,10 +37,31 @@ namespace ph {
 constexpr int kRItems = 8;
 constexpr int kRTile = kThreads * kRItems;
 
-struct RArgs {
-  int32_t* act;
-  int32_t* act2;
+enum : int32_t { ST_RUN = 0, ST_DONE = 1, ST_CAPPED = 2, ST_HOST = 3 };
+
+struct DevState {
+  int32_t* act;   // active ids, ascending
+  int32_t* act2;  // next active list
   int64_t n_act;
+  int32_t* arena[2];  // pass p writes its survivors into arena[p & 1]
+  int64_t arena_cap[2];
+  int32_t* piv_base;  // current chunk of the pivot store
+  int64_t piv_cap;
+  unsigned long long piv_used;
+  int64_t* stats;  // [stats_rows][PH_PS_N] or nullptr
+  int32_t stats_rows;
+  int32_t pass;
+  int32_t max_passes;
+  int32_t status;
+  int32_t passes;
+  int32_t host_reason;  // 1 arena, 2 pivot store, 4 counter rows
+  int64_t totals[4];    // survivors, words, pivot words, targets of the current pass
+  unsigned long long bound_words, bound_piv;
+  unsigned int queue;  // next chunk for k_add
+};
+
+struct RArgs {
+  DevState* ds;
   int32_t* low;
   const int32_t* beta;
   uint8_t* flags;
@@ -45,23 +74,45 @@ struct RArgs {
   int32_t* tab;
   int32_t* first_unp;
   const int32_t* seg;
+  int64_t rows_end;
   int nc;
   int strict;
   int cor10;
-  int do_adds;
   SegMax* tile_sm;    // [ntiles] Phase I tile aggregates (scanned in place to prefixes)
   SegMax* chunk_sm;   // [ntiles][kRItems] aggregate of each 256-entry chunk alone
   int64_t* tile_cnt;  // [ntiles][2] survivors, words (scanned in place to prefixes)
   int64_t* tile_aux;  // [ntiles][2] pivot words, targets
   int64_t* chunk_cnt; // [ntiles][kRItems][2] survivors, words of each chunk alone
-  int64_t* totals;    // [4] survivors, words, pivot words, targets
+  int staged_max;     // merges of more rows than this run from global memory
+  int force_km;       // > 0: merge-path positions per lane for every warp
+};
+
+// per-pass values, read once at kernel start (no kernel changes them while others read them)
+struct PV {
+  int32_t* act;
+  int32_t* act2;
+  int64_t n_act;
+  int64_t ntiles;
+  int64_t nchunks;
+  int do_adds;
+  int64_t* stats;
   int32_t* arena_next;
   int32_t* piv_base;
-  unsigned long long* piv_bump;
-  int64_t* stats;  // this pass's counters or nullptr
-  int staged_max;  // merges of more rows than this run from global memory
-  int force_km;    // > 0: merge-path positions per lane for every warp
 };
+
+__device__ __forceinline__ PV pass_view(const DevState* ds) {
+  PV v;
+  v.act = ds->act;
+  v.act2 = ds->act2;
+  v.n_act = ds->n_act;
+  v.ntiles = (v.n_act + kRTile - 1) / kRTile;
+  v.nchunks = (v.n_act + kThreads - 1) / kThreads;
+  v.do_adds = ds->pass < ds->max_passes;
+  v.stats = ds->stats ? ds->stats + (int64_t)ds->pass * PH_PS_N : nullptr;
+  v.arena_next = ds->arena[ds->pass & 1];
+  v.piv_base = ds->piv_base;
+  return v;
+}
 
 __device__ __forceinline__ void stat_add(int64_t* stats, int k, int64_t v) {
   // warp-aggregated counter update
@@ -71,23 +122,31 @@ __device__ __forceinline__ void stat_add(int64_t* stats, int k, int64_t v) {
   if (lane_id() == 0 && s != 0) atomicAdd((unsigned long long*)&stats[k], (unsigned long long)s);
 }
 
+
 // ------------------------------------------------------------------------------------------
-__global__ void k_tab_init(int64_t rows_end, const int32_t* __restrict__ owner,
-                           const uint8_t* __restrict__ flags, const int32_t* __restrict__ beta,
-                           const int32_t* __restrict__ seg, int32_t* tab, int32_t* first_unp) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < rows_end;
+__global__ void k_tab_init(RArgs a) {
+  DevState* ds = a.ds;
+  if (ds->status != ST_RUN) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ds->bound_words = 0;
+    ds->bound_piv = 0;
+    ds->queue = 0;
+  }
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < a.rows_end;
        x += (int64_t)gridDim.x * blockDim.x) {
-    int32_t o = owner[x];
-    tab[x] = o < 0 ? INT32_MAX : o;
-    bool paired = (flags[x] & F_PROVEN) || beta[x] >= 0 || o >= 0;
-    if (!paired) atomicMin(&first_unp[seg[x]], (int32_t)x);
+    int32_t o = a.owner[x];
+    a.tab[x] = o < 0 ? INT32_MAX : o;
+    bool paired = (a.flags[x] & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
+    if (!paired) atomicMin(&a.first_unp[a.seg[x]], (int32_t)x);
   }
 }
 
 __global__ void k_tab(RArgs a) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_act;
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.n_act;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t j = a.act[i];
+    int32_t j = v.act[i];
     int32_t l = a.low[j];
     if (l >= 0 && a.tab[l] > j) atomicMin(&a.tab[l], j);
   }
@@ -96,14 +155,14 @@ __global__ void k_tab(RArgs a) {
 // ------------------------------------------------------------------------------------------
 // Phase I scan
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ SegMax p1_value(const RArgs& a, int64_t e) {
-  if (e >= a.n_act) return SegMax{INT32_MAX, -1};
-  int32_t j = a.act[e];
+__device__ __forceinline__ SegMax p1_value(const RArgs& a, const PV& v, int64_t e) {
+  if (e >= v.n_act) return SegMax{INT32_MAX, -1};
+  int32_t j = v.act[e];
   int32_t l = a.low[j];
-  SegMax v;
-  v.seg = a.seg[j];
-  v.val = (l >= 0 && a.tab[l] != j) ? l : -1;  // low of a colliding column
-  return v;
+  SegMax r;
+  r.seg = a.seg[j];
+  r.val = (l >= 0 && a.tab[l] != j) ? l : -1;  // low of a colliding column
+  return r;
 }
 
 // exclusive block scan with carry-in; returns the exclusive prefix, sets the running total
@@ -134,55 +193,101 @@ __device__ __forceinline__ SegMax block_scan_segmax(SegMax v, SegMax carry, SegM
   return ex;
 }
 
+// per tile: Phase I aggregates of each chunk and of the tile, and upper bounds of the arena
+// words (target + source) and pivot-store words (only a left-most column can become a pivot)
 __global__ void k_p1_tiles(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
-  int64_t tile0 = (int64_t)blockIdx.x * kRTile;
-  SegMax carry{-1, -1};
-  for (int it = 0; it < kRItems; it++) {
-    SegMax v = p1_value(a, tile0 + it * kThreads + threadIdx.x);
-    SegMax tot;
-    block_scan_segmax(v, SegMax{-1, -1}, sh, tot);  // this chunk alone
-    if (threadIdx.x == 0) a.chunk_sm[(int64_t)blockIdx.x * kRItems + it] = tot;
-    carry = segmax_combine(carry, tot);
+  __shared__ int64_t shs[kWarps + 1];
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
+  int64_t bw = 0, bp = 0;
+  for (int64_t t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const int64_t tile0 = t * kRTile;
+    SegMax carry{-1, -1};
+    for (int it = 0; it < kRItems; it++) {
+      const int64_t e = tile0 + it * kThreads + threadIdx.x;
+      SegMax val = p1_value(a, v, e);
+      SegMax tot;
+      block_scan_segmax(val, SegMax{-1, -1}, sh, tot);  // this chunk alone
+      if (threadIdx.x == 0) a.chunk_sm[t * kRItems + it] = tot;
+      carry = segmax_combine(carry, tot);
+      if (e < v.n_act) {
+        const int32_t j = v.act[e];
+        const int32_t n = a.clen[j];
+        bw += n;
+        const int32_t l = a.low[j];
+        if (l >= 0) {
+          const int32_t s = a.tab[l];
+          if (s != j) bw += a.clen[s];  // a target: its source may be added
+          else bp += n;                 // left-most: it may be proven and move
+        }
+      }
+    }
+    if (threadIdx.x == 0) a.tile_sm[t] = carry;
   }
-  if (threadIdx.x == 0) a.tile_sm[blockIdx.x] = carry;
+  int64_t tw, tp;
+  block_excl_sum<int64_t>(bw, shs, tw);
+  block_excl_sum<int64_t>(bp, shs, tp);
+  if (threadIdx.x == 0 && (tw || tp)) {
+    atomicAdd(&a.ds->bound_words, (unsigned long long)tw);
+    atomicAdd(&a.ds->bound_piv, (unsigned long long)tp);
+  }
 }
 
-__global__ void k_p1_top(SegMax* tile_sm, int64_t ntiles) {
+__global__ void k_p1_top(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
   SegMax carry{-1, -1};
-  for (int64_t base = 0; base < ntiles; base += kThreads) {
+  for (int64_t base = 0; base < v.ntiles; base += kThreads) {
     int64_t i = base + threadIdx.x;
-    SegMax v = i < ntiles ? tile_sm[i] : SegMax{INT32_MAX, -1};
+    SegMax val = i < v.ntiles ? a.tile_sm[i] : SegMax{INT32_MAX, -1};
     SegMax tot;
-    SegMax ex = block_scan_segmax(v, carry, sh, tot);
-    if (i < ntiles) tile_sm[i] = ex;
+    SegMax ex = block_scan_segmax(val, carry, sh, tot);
+    if (i < v.ntiles) a.tile_sm[i] = ex;
     carry = tot;
   }
 }
 
-// one block per 256-entry chunk; its prefix is the tile's prefix combined with the aggregates
-// of the earlier chunks of the same tile
+// the space this pass can need, against what the host provided; nothing has changed yet, so a
+// pass stopped here runs again unchanged once the host has grown the buffers
+__global__ void k_check(RArgs a) {
+  DevState* ds = a.ds;
+  if (ds->status != ST_RUN || threadIdx.x != 0 || blockIdx.x != 0) return;
+  int reason = 0;
+  if (ds->bound_words > (unsigned long long)ds->arena_cap[ds->pass & 1]) reason |= 1;
+  if (ds->bound_piv + ds->piv_used > (unsigned long long)ds->piv_cap) reason |= 2;
+  if (ds->stats && ds->pass >= ds->stats_rows) reason |= 4;
+  if (reason) {
+    ds->host_reason = reason;
+    ds->status = ST_HOST;
+  }
+}
+
+// one 256-entry chunk per block iteration; its prefix is the tile's prefix combined with the
+// aggregates of the earlier chunks of the same tile
 __global__ void k_mark(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
-  const int64_t chunk = blockIdx.x, tile = chunk / kRItems;
-  SegMax carry = a.tile_sm[tile];
-  for (int64_t c = tile * kRItems; c < chunk; c++) carry = segmax_combine(carry, a.chunk_sm[c]);
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
   int64_t n_zero = 0, n_piv = 0, n_c10 = 0;
-  {
-    int64_t e = chunk * kThreads + threadIdx.x;
-    SegMax v = p1_value(a, e);
+  for (int64_t chunk = blockIdx.x; chunk < v.nchunks; chunk += gridDim.x) {
+    const int64_t tile = chunk / kRItems;
+    SegMax carry = a.tile_sm[tile];
+    for (int64_t c = tile * kRItems; c < chunk; c++) carry = segmax_combine(carry, a.chunk_sm[c]);
+    const int64_t e = chunk * kThreads + threadIdx.x;
+    SegMax val = p1_value(a, v, e);
     SegMax tot;
-    SegMax pre = block_scan_segmax(v, carry, sh, tot);
-    if (e < a.n_act) {
-      int32_t j = a.act[e];
+    SegMax pre = block_scan_segmax(val, carry, sh, tot);
+    if (e < v.n_act) {
+      int32_t j = v.act[e];
       int32_t l = a.low[j];
       uint8_t f = a.flags[j];
       if (l < 0) {
         a.flags[j] = f | F_FINAL;
         n_zero++;
       } else {
-        int32_t P = (pre.seg == v.seg) ? pre.val : -1;
+        int32_t P = (pre.seg == val.seg) ? pre.val : -1;
         bool leftmost = a.tab[l] == j;
         int32_t b = a.beta[j];
         if (leftmost && (l == b || l > P)) {
@@ -190,17 +295,17 @@ __global__ void k_mark(RArgs a) {
           a.owner[l] = j;
           a.cleared[l] = 1;  // clearing (Lemma 1): column l is positive and paired with j
           n_piv++;
-        } else if (a.cor10 && b < 0 && l < a.first_unp[v.seg - a.nc]) {
+        } else if (a.cor10 && b < 0 && l < a.first_unp[val.seg - a.nc]) {
           a.flags[j] = f | F_FINAL;  // Corollary 10, zero case
           n_c10++;
         }
       }
     }
   }
-  if (a.stats) {
-    stat_add(a.stats, PH_PS_ZERO_FINAL, n_zero);
-    stat_add(a.stats, PH_PS_NEW_PIVOTS, n_piv);
-    stat_add(a.stats, PH_PS_COR10, n_c10);
+  if (v.stats) {
+    stat_add(v.stats, PH_PS_ZERO_FINAL, n_zero);
+    stat_add(v.stats, PH_PS_NEW_PIVOTS, n_piv);
+    stat_add(v.stats, PH_PS_COR10, n_c10);
   }
 }
 
@@ -216,10 +321,10 @@ struct Job {
   int64_t words;  // arena words reserved (survivors only)
 };
 
-__device__ __forceinline__ Job job_of(const RArgs& a, int64_t e) {
+__device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
   Job jb{-1, -1, false, false, false, 0};
-  if (e >= a.n_act) return jb;
-  int32_t j = a.act[e];
+  if (e >= v.n_act) return jb;
+  int32_t j = v.act[e];
   jb.j = j;
   uint8_t f = a.flags[j];
   jb.newpiv = (f & F_NEWPIV) != 0;
@@ -230,7 +335,7 @@ __device__ __forceinline__ Job job_of(const RArgs& a, int64_t e) {
     jb.words = a.clen[j];
     if (s != j) {
       jb.target = true;
-      if (a.do_adds) {
+      if (v.do_adds) {
         uint8_t fs = a.flags[s];
         bool ok = !(fs & F_FINAL) && !a.cleared[s] && (!a.strict || (fs & F_PROVEN));
         if (ok) {
@@ -245,48 +350,55 @@ __device__ __forceinline__ Job job_of(const RArgs& a, int64_t e) {
 
 __global__ void k_s2_tiles(RArgs a) {
   __shared__ int64_t sh[kWarps + 1];
-  int64_t tile0 = (int64_t)blockIdx.x * kRTile;
-  int64_t t0 = 0, t1 = 0, pivw = 0, targ = 0;
-  for (int it = 0; it < kRItems; it++) {
-    Job jb = job_of(a, tile0 + it * kThreads + threadIdx.x);
-    int64_t cs, cw;
-    block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, cs);
-    block_excl_sum<int64_t>(jb.words, sh, cw);
-    if (threadIdx.x == 0) {
-      a.chunk_cnt[2 * ((int64_t)blockIdx.x * kRItems + it)] = cs;
-      a.chunk_cnt[2 * ((int64_t)blockIdx.x * kRItems + it) + 1] = cw;
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
+  for (int64_t t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const int64_t tile0 = t * kRTile;
+    int64_t t0 = 0, t1 = 0, pivw = 0, targ = 0;
+    for (int it = 0; it < kRItems; it++) {
+      Job jb = job_of(a, v, tile0 + it * kThreads + threadIdx.x);
+      int64_t cs, cw;
+      block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, cs);
+      block_excl_sum<int64_t>(jb.words, sh, cw);
+      if (threadIdx.x == 0) {
+        a.chunk_cnt[2 * (t * kRItems + it)] = cs;
+        a.chunk_cnt[2 * (t * kRItems + it) + 1] = cw;
+      }
+      t0 += cs;
+      t1 += cw;
+      targ += jb.target;
+      if (jb.newpiv) pivw += a.clen[jb.j];
     }
-    t0 += cs;
-    t1 += cw;
-    targ += jb.target;
-    if (jb.newpiv) pivw += a.clen[jb.j];
-  }
-  int64_t t2, t3;
-  block_excl_sum<int64_t>(pivw, sh, t2);
-  block_excl_sum<int64_t>(targ, sh, t3);
-  if (threadIdx.x == 0) {
-    a.tile_cnt[2 * blockIdx.x] = t0;
-    a.tile_cnt[2 * blockIdx.x + 1] = t1;
-    a.tile_aux[2 * blockIdx.x] = t2;
-    a.tile_aux[2 * blockIdx.x + 1] = t3;
+    int64_t t2, t3;
+    block_excl_sum<int64_t>(pivw, sh, t2);
+    block_excl_sum<int64_t>(targ, sh, t3);
+    if (threadIdx.x == 0) {
+      a.tile_cnt[2 * t] = t0;
+      a.tile_cnt[2 * t + 1] = t1;
+      a.tile_aux[2 * t] = t2;
+      a.tile_aux[2 * t + 1] = t3;
+    }
   }
 }
 
-__global__ void k_s2_top(RArgs a, int64_t ntiles) {
+__global__ void k_s2_top(RArgs a) {
   __shared__ int64_t sh[kWarps + 1];
+  DevState* ds = a.ds;
+  if (ds->status != ST_RUN) return;
+  const PV v = pass_view(ds);
   int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-  for (int64_t base = 0; base < ntiles; base += kThreads) {
+  for (int64_t base = 0; base < v.ntiles; base += kThreads) {
     int64_t i = base + threadIdx.x;
-    int64_t v0 = i < ntiles ? a.tile_cnt[2 * i] : 0;
-    int64_t v1 = i < ntiles ? a.tile_cnt[2 * i + 1] : 0;
-    int64_t v2 = i < ntiles ? a.tile_aux[2 * i] : 0;
-    int64_t v3 = i < ntiles ? a.tile_aux[2 * i + 1] : 0;
+    int64_t v0 = i < v.ntiles ? a.tile_cnt[2 * i] : 0;
+    int64_t v1 = i < v.ntiles ? a.tile_cnt[2 * i + 1] : 0;
+    int64_t v2 = i < v.ntiles ? a.tile_aux[2 * i] : 0;
+    int64_t v3 = i < v.ntiles ? a.tile_aux[2 * i + 1] : 0;
     int64_t t0, t1, t2, t3;
     int64_t e0 = block_excl_sum<int64_t>(v0, sh, t0);
     int64_t e1 = block_excl_sum<int64_t>(v1, sh, t1);
     block_excl_sum<int64_t>(v2, sh, t2);
     block_excl_sum<int64_t>(v3, sh, t3);
-    if (i < ntiles) {
+    if (i < v.ntiles) {
       a.tile_cnt[2 * i] = c0 + e0;
       a.tile_cnt[2 * i + 1] = c1 + e1;
     }
@@ -296,11 +408,11 @@ __global__ void k_s2_top(RArgs a, int64_t ntiles) {
     c3 += t3;
   }
   if (threadIdx.x == 0) {
-    a.totals[0] = c0;
-    a.totals[1] = c1;
-    a.totals[2] = c2;
-    a.totals[3] = c3;
-    if (a.stats) a.stats[PH_PS_TARGETS] = c3;
+    ds->totals[0] = c0;
+    ds->totals[1] = c1;
+    ds->totals[2] = c2;
+    ds->totals[3] = c3;
+    if (v.stats) v.stats[PH_PS_TARGETS] = c3;
   }
 }
 
@@ -428,30 +540,28 @@ __device__ __forceinline__ int lane_symdiff(const int32_t* __restrict__ sA, int 
   return cnt;
 }
 
-// Phase II for one 256-entry chunk of the active list per block. After one block scan for the
-// output offsets, every warp works on its own 32 jobs: new pivots are copied to the pivot store;
+// Phase II for one 256-entry chunk of the active list. After one block scan for the output
+// offsets, every warp works on its own 32 jobs: new pivots are copied to the pivot store;
 // survivors (with or without an addition) are staged in shared memory and merged by a merge
 // path over the concatenation of all of the batch's jobs, each job padded to a multiple of km
 // positions so that a lane's km positions never span two jobs (km is chosen per warp from the
 // mean merge length); outputs are written compactly and in order into the warp's region of the
 // next arena. Merges longer than the staging bound run from global memory.
-__global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
-  __shared__ int64_t sh[kWarps + 1];
-  extern __shared__ __align__(16) unsigned char add_smem[];
-  const int lane = lane_id(), w = threadIdx.x >> 5;
-  WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[w];
-  const int64_t chunk = blockIdx.x, tile = chunk / kRItems;
+__device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
+                                          WarpStage& S, int64_t* sh, int64_t& n_add,
+                                          int64_t& n_xor, int64_t& n_copy) {
+  const int lane = lane_id();
+  const int64_t tile = chunk / kRItems;
   int64_t cs = a.tile_cnt[2 * tile], cw = a.tile_cnt[2 * tile + 1];
   for (int64_t c = tile * kRItems; c < chunk; c++) {
     cs += a.chunk_cnt[2 * c];
     cw += a.chunk_cnt[2 * c + 1];
   }
   const int64_t e = chunk * kThreads + threadIdx.x;
-  Job jb = job_of(a, e);
+  Job jb = job_of(a, v, e);
   int64_t ts, tw;
   const int64_t pos = cs + block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, ts);
   const int64_t off = cw + block_excl_sum<int64_t>(jb.words, sh, tw);
-  int64_t n_add = 0, n_xor = 0, n_copy = 0;
 
   const int32_t* A = nullptr;
   const int32_t* B = nullptr;
@@ -468,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
     a.nxt_ptr[e] = nullptr;
     a.nxt_len[e] = 0;
   }
-  if (jb.surv) a.act2[pos] = jb.j;
+  if (jb.surv) v.act2[pos] = jb.j;
 
   // ---- new pivots: their columns never change again; move them to the pivot store
   unsigned pmask = __ballot_sync(0xffffffffu, jb.newpiv);
@@ -478,9 +588,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
     const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src);
     const int wna = __shfl_sync(0xffffffffu, na, src);
     unsigned long long w0 = 0;
-    if (lane == src) w0 = atomicAdd(a.piv_bump, (unsigned long long)wna);
+    if (lane == src) w0 = atomicAdd(&a.ds->piv_used, (unsigned long long)wna);
     w0 = __shfl_sync(0xffffffffu, w0, src);
-    int32_t* dst = a.piv_base + w0;
+    int32_t* dst = v.piv_base + w0;
     for (int q = lane; q < wna; q += 32) dst[q] = wA[q];
     if (lane == src) {
       a.nxt_ptr[e] = dst;
@@ -520,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
       S.pad_off[32] = pad_ex + npad;
     }
     __syncwarp();
-    int32_t* out = a.arena_next + wbase;  // compact outputs of the staged jobs
+    int32_t* out = v.arena_next + wbase;  // compact outputs of the staged jobs
     int ocur = 0;
     int c = 0;
     while (c < 32) {
@@ -639,7 +749,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
       const int32_t* wB = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)B, src);
       const int wna = __shfl_sync(0xffffffffu, na, src);
       const int wnb = __shfl_sync(0xffffffffu, nb, src);
-      int32_t* wd = a.arena_next + wbase + small_total + __shfl_sync(0xffffffffu, big_ex, src);
+      int32_t* wd = v.arena_next + wbase + small_total + __shfl_sync(0xffffffffu, big_ex, src);
       int len;
       int32_t last = -1;
       if (wB) {
@@ -661,18 +771,38 @@ __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
       }
     }
   }
-  if (a.stats) {
-    stat_add(a.stats, PH_PS_ADDS, n_add);
-    stat_add(a.stats, PH_PS_XORS, n_xor);
-    stat_add(a.stats, PH_PS_COPIED, n_copy);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
+  __shared__ int64_t sh[kWarps + 1];
+  __shared__ int64_t s_chunk;
+  extern __shared__ __align__(16) unsigned char add_smem[];
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
+  WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[threadIdx.x >> 5];
+  int64_t n_add = 0, n_xor = 0, n_copy = 0;
+  for (;;) {  // device work queue of chunks
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&a.ds->queue, 1u);
+    __syncthreads();
+    const int64_t chunk = s_chunk;
+    __syncthreads();
+    if (chunk >= v.nchunks) break;
+    add_chunk(a, v, chunk, S, sh, n_add, n_xor, n_copy);
+  }
+  if (v.stats) {
+    stat_add(v.stats, PH_PS_ADDS, n_add);
+    stat_add(v.stats, PH_PS_XORS, n_xor);
+    stat_add(v.stats, PH_PS_COPIED, n_copy);
   }
 }
 
 __global__ void k_commit(RArgs a) {
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
   int64_t n_clear = 0, n_act = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.n_act;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < v.n_act;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t j = a.act[e];
+    int32_t j = v.act[e];
     uint8_t f = a.flags[j];
     uint8_t c = a.cleared[j];
     n_act++;
@@ -691,14 +821,37 @@ __global__ void k_commit(RArgs a) {
       a.clen[j] = 0;
     }
   }
-  if (a.stats) {
-    stat_add(a.stats, PH_PS_ACTIVE, n_act);
-    stat_add(a.stats, PH_PS_CLEARED, n_clear);
+  if (v.stats) {
+    stat_add(v.stats, PH_PS_ACTIVE, n_act);
+    stat_add(v.stats, PH_PS_CLEARED, n_clear);
   }
 }
 
+// end of a pass: the next active list, convergence (no collision left) or the pass cap
+__global__ void k_end(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevState* ds = a.ds;
+  if (ds->status == ST_RUN) {
+    const int32_t p = ds->pass;
+    ds->n_act = ds->totals[0];
+    int32_t* t = ds->act;
+    ds->act = ds->act2;
+    ds->act2 = t;
+    if (ds->totals[3] == 0) {
+      ds->status = ST_DONE;
+      ds->passes = p;
+    } else if (p >= ds->max_passes) {
+      ds->status = ST_CAPPED;
+      ds->passes = p;
+    } else {
+      ds->pass = p + 1;
+    }
+  }
+  if (in_graph) cudaGraphSetConditional(cond, ds->status == ST_RUN ? 1u : 0u);
+}
+
 // ------------------------------------------------------------------------------------------
-// set-up
+// set-up and host orchestration
 // ------------------------------------------------------------------------------------------
 struct InitLayout {
   int64_t dimoff[kMaxDim + 2];
@@ -726,6 +879,78 @@ __global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0, int32_t**
   }
 }
 
+static RArgs make_args(ph_ctx* ctx) {
+  ReduceState& rs = ctx->rs;
+  const int64_t ntiles = (ctx->m + kRTile - 1) / kRTile;
+  RArgs a{};
+  a.ds = static_cast<DevState*>(rs.dstate);
+  a.low = ctx->low;
+  a.beta = ctx->beta;
+  a.flags = rs.flags;
+  a.cleared = rs.cleared;
+  a.cptr = rs.cptr;
+  a.clen = rs.clen;
+  a.nxt_ptr = rs.nxt_ptr;
+  a.nxt_len = rs.nxt_len;
+  a.owner = rs.owner;
+  a.tab = rs.tab;
+  a.first_unp = rs.first_unp;
+  a.seg = ctx->seg;
+  a.rows_end = ctx->dimoff[ctx->max_dim];
+  a.nc = ctx->n_clouds;
+  a.strict = ctx->opts.strict_phase2;
+  a.cor10 = ctx->opts.use_cor10;
+  a.tile_sm = (SegMax*)rs.tiles;
+  a.chunk_sm = a.tile_sm + ntiles;
+  a.tile_cnt = (int64_t*)(a.chunk_sm + ntiles * kRItems);
+  a.tile_aux = a.tile_cnt + 2 * ntiles;
+  a.chunk_cnt = a.tile_aux + 2 * ntiles;
+  a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
+                                                 : kStage;
+  a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
+  return a;
+}
+
+// the kernels of one pass, in order; grids are fixed (persistent blocks loop over the work)
+static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
+                        bool in_graph, bool time_add, cudaStream_t st) {
+  ReduceState& rs = ctx->rs;
+  const int sms = ctx->num_sms;
+  const int nseg = (int)ctx->seg_start.size() - 1;
+  PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, nseg * sizeof(int32_t), st));
+  k_tab_init<<<grid_for(ctx, a.rows_end, kThreads), kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_tab<<<sms * 8, kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_p1_tiles<<<sms * 4, kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_p1_top<<<1, kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_check<<<1, 32, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_mark<<<sms * 8, kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_s2_tiles<<<sms * 4, kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_s2_top<<<1, kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  if (time_add) {
+    cudaEvent_t e0, e1;
+    PH_CUDA(cudaEventCreate(&e0));
+    PH_CUDA(cudaEventCreate(&e1));
+    rs.ev.push_back(e0);
+    rs.ev.push_back(e1);
+    PH_CUDA(cudaEventRecord(e0, st));
+  }
+  k_add<<<sms * 4, kThreads, kAddSmem, st>>>(a);
+  PH_CHECK_LAUNCH();
+  if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
+  k_commit<<<sms * 8, kThreads, 0, st>>>(a);
+  PH_CHECK_LAUNCH();
+  k_end<<<1, 32, 0, st>>>(a, cond, in_graph ? 1 : 0);
+  PH_CHECK_LAUNCH();
+}
+
 static void grow_store(ph_ctx* ctx, ColStore& s, int64_t need_words) {
   if (need_words <= s.cap) return;
   if (s.p) ctx->dfree(s.p);
@@ -736,6 +961,7 @@ static void grow_store(ph_ctx* ctx, ColStore& s, int64_t need_words) {
 
 void reduce_init(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
+  cudaStream_t st = ctx->stream;
   const int64_t m = ctx->m;
   rs.act = alloc_n<int32_t>(ctx, m);
   rs.act2 = alloc_n<int32_t>(ctx, m);
@@ -753,10 +979,8 @@ void reduce_init(ph_ctx* ctx) {
   int64_t ntiles = (m + kRTile - 1) / kRTile;
   rs.tiles_bytes = ntiles * ((1 + kRItems) * sizeof(SegMax) + (4 + 2 * kRItems) * sizeof(int64_t));
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
-  rs.totals = alloc_n<int64_t>(ctx, 8);
-  PH_CUDA(cudaMallocHost(&rs.h_totals, 8 * sizeof(int64_t)));
-  rs.stats_rows = 0;
-  rs.pass_stats = nullptr;
+  rs.dstate = ctx->dalloc(sizeof(DevState));
+  PH_CUDA(cudaMallocHost(&rs.hstate, sizeof(DevState)));
   rs.h_stats.clear();
   InitLayout L{};
   L.maxd = ctx->max_dim;
@@ -766,155 +990,174 @@ void reduce_init(ph_ctx* ctx) {
     L.rowbase[d] = rb;
     rb += (d > 0 ? d + 1 : 0) * (ctx->dimoff[d + 1] - ctx->dimoff[d]);
   }
-  k_reduce_init<<<grid_for(ctx, m, kThreads), kThreads, 0, ctx->stream>>>(
+  k_reduce_init<<<grid_for(ctx, m, kThreads), kThreads, 0, st>>>(
       m, L, ctx->rows0, rs.cptr, rs.clen, ctx->low, rs.act, rs.owner, rs.flags, rs.cleared);
   PH_CHECK_LAUNCH();
-  rs.n_act = m;
-  rs.cur = 0;
-  rs.arena[0].p = ctx->rows0;  // the boundary matrix is the first arena
-  rs.arena[0].cap = ctx->nnz;
-  rs.arena[1] = ColStore{};
-  rs.pivots.clear();
-  rs.piv_used = 0;
-  rs.piv_bump = alloc_n<int64_t>(ctx, 1);
-  PH_CUDA(cudaMemsetAsync(rs.piv_bump, 0, sizeof(int64_t), ctx->stream));
+  // first arenas: pass 0 needs at most the boundary matrix twice over
+  grow_store(ctx, rs.arena[0], 2 * ctx->nnz + 1);
+  grow_store(ctx, rs.arena[1], ctx->nnz + 1);
+  ColStore c{};
+  grow_store(ctx, c, ctx->nnz / 4 + 1);
+  rs.pivots.push_back(c);
+  if (ctx->opts.collect_stats) {
+    rs.stats_rows = 256;
+    rs.pass_stats = alloc_n<int64_t>(ctx, (int64_t)rs.stats_rows * PH_PS_N);
+    PH_CUDA(cudaMemsetAsync(rs.pass_stats, 0, (size_t)rs.stats_rows * PH_PS_N * 8, st));
+  }
+  DevState& h = *static_cast<DevState*>(rs.hstate);
+  h = DevState{};
+  h.act = rs.act;
+  h.act2 = rs.act2;
+  h.n_act = m;
+  for (int i = 0; i < 2; i++) {
+    h.arena[i] = rs.arena[i].p;
+    h.arena_cap[i] = rs.arena[i].cap;
+  }
+  h.piv_base = c.p;
+  h.piv_cap = c.cap;
+  h.piv_used = 0;
+  h.stats = rs.pass_stats;
+  h.stats_rows = rs.stats_rows;
+  h.pass = 0;
+  h.status = ST_RUN;
+  PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  PH_CUDA(cudaFuncSetAttribute(k_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kAddSmem));
   rs.passes = 0;
-  rs.next_pass = 0;
   rs.init = true;
   rs.done = false;
   rs.status = PH_OK;
 }
 
+// grows whatever the stopped pass asked for, in the host mirror h
+static void serve_host_request(ph_ctx* ctx, DevState& h) {
+  ReduceState& rs = ctx->rs;
+  cudaStream_t st = ctx->stream;
+  if (h.host_reason & 1) {  // the arena this pass writes into; its contents are dead
+    ColStore& s = rs.arena[h.pass & 1];
+    grow_store(ctx, s, (int64_t)h.bound_words);
+    h.arena[h.pass & 1] = s.p;
+    h.arena_cap[h.pass & 1] = s.cap;
+  }
+  if (h.host_reason & 2) {  // a new pivot chunk; the old ones stay (their columns live there)
+    ColStore c{};
+    grow_store(ctx, c, std::max<int64_t>(2 * (int64_t)h.bound_piv, ctx->nnz / 4 + 1));
+    rs.pivots.push_back(c);
+    h.piv_base = c.p;
+    h.piv_cap = c.cap;
+    h.piv_used = 0;
+  }
+  if (h.host_reason & 4) {
+    int32_t rows = std::max(256, rs.stats_rows * 2);
+    while (rows <= h.pass) rows *= 2;
+    int64_t* ns = alloc_n<int64_t>(ctx, (int64_t)rows * PH_PS_N);
+    PH_CUDA(cudaMemsetAsync(ns, 0, (size_t)rows * PH_PS_N * 8, st));
+    PH_CUDA(cudaMemcpyAsync(ns, rs.pass_stats, (size_t)rs.stats_rows * PH_PS_N * 8,
+                            cudaMemcpyDeviceToDevice, st));
+    ctx->dfree(rs.pass_stats);
+    rs.pass_stats = ns;
+    rs.stats_rows = rows;
+    h.stats = ns;
+    h.stats_rows = rows;
+  }
+  h.host_reason = 0;
+  h.status = ST_RUN;
+}
+
+static void build_graph(ph_ctx* ctx, const RArgs& a) {
+  ReduceState& rs = ctx->rs;
+  cudaGraph_t g;
+  PH_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond;
+  PH_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  PH_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  // capture on a private stream (the legacy default stream cannot capture); the graph is
+  // then launched on the context's stream
+  cudaStream_t cs;
+  PH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t ce = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    cudaGraphDestroy(g);
+    PH_CUDA(ce);
+  }
+  const int64_t counted = ctx->launches;  // captured launches run later, counted per pass
+  try {
+    launch_pass(ctx, a, cond, true, false, cs);
+    ctx->launches = counted;
+  } catch (...) {
+    cudaStreamEndCapture(cs, &body);
+    cudaStreamDestroy(cs);
+    cudaGraphDestroy(g);
+    throw;
+  }
+  ce = cudaStreamEndCapture(cs, &body);
+  cudaStreamDestroy(cs);
+  if (ce != cudaSuccess) cudaGraphDestroy(g);
+  PH_CUDA(ce);
+  cudaGraphExec_t exec;
+  PH_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  rs.graph = g;
+  rs.graph_exec = exec;
+}
+
 int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   ReduceState& rs = ctx->rs;
   cudaStream_t st = ctx->stream;
-  const int64_t m = ctx->m;
-  const int64_t rows_end = ctx->dimoff[ctx->max_dim];
-  const int nseg = (int)ctx->seg_start.size() - 1;
-  const bool stats = ctx->opts.collect_stats != 0;
-  if (max_passes < 0) max_passes = INT32_MAX;
-
-  RArgs a{};
-  a.low = ctx->low;
-  a.beta = ctx->beta;
-  a.flags = rs.flags;
-  a.cleared = rs.cleared;
-  a.cptr = rs.cptr;
-  a.clen = rs.clen;
-  a.nxt_ptr = rs.nxt_ptr;
-  a.nxt_len = rs.nxt_len;
-  a.owner = rs.owner;
-  a.tab = rs.tab;
-  a.first_unp = rs.first_unp;
-  a.seg = ctx->seg;
-  a.nc = ctx->n_clouds;
-  a.strict = ctx->opts.strict_phase2;
-  a.cor10 = ctx->opts.use_cor10;
-  a.totals = rs.totals;
-  a.piv_bump = (unsigned long long*)rs.piv_bump;
-  a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
-                                                 : kStage;
-  a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
-
-  for (int pass = rs.next_pass;; pass++) {
-    const int64_t n_act = rs.n_act;
-    const int64_t ntiles = std::max<int64_t>((n_act + kRTile - 1) / kRTile, 1);
-    a.act = rs.act;
-    a.act2 = rs.act2;
-    a.n_act = n_act;
-    const int64_t nchunks = std::max<int64_t>((n_act + kThreads - 1) / kThreads, 1);
-    a.tile_sm = (SegMax*)rs.tiles;
-    a.chunk_sm = a.tile_sm + ntiles;
-    a.tile_cnt = (int64_t*)(a.chunk_sm + ntiles * kRItems);
-    a.tile_aux = a.tile_cnt + 2 * ntiles;
-    a.chunk_cnt = a.tile_aux + 2 * ntiles;
-    a.do_adds = pass < max_passes;
-    if (stats) {
-      if (pass >= rs.stats_rows) {
-        int32_t rows = std::max(64, rs.stats_rows * 2);
-        int64_t* ns = alloc_n<int64_t>(ctx, (int64_t)rows * PH_PS_N);
-        PH_CUDA(cudaMemsetAsync(ns, 0, (size_t)rows * PH_PS_N * sizeof(int64_t), st));
-        if (rs.pass_stats) {
-          PH_CUDA(cudaMemcpyAsync(ns, rs.pass_stats,
-                                  (size_t)rs.stats_rows * PH_PS_N * sizeof(int64_t),
-                                  cudaMemcpyDeviceToDevice, st));
-          ctx->dfree(rs.pass_stats);
-        }
-        rs.pass_stats = ns;
-        rs.stats_rows = rows;
-      }
-      a.stats = rs.pass_stats + (int64_t)pass * PH_PS_N;
-    }
-    PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, nseg * sizeof(int32_t), st));
-    k_tab_init<<<grid_for(ctx, rows_end, kThreads), kThreads, 0, st>>>(
-        rows_end, rs.owner, rs.flags, ctx->beta, ctx->seg, rs.tab, rs.first_unp);
-    PH_CHECK_LAUNCH();
-    k_tab<<<grid_for(ctx, n_act, kThreads), kThreads, 0, st>>>(a);
-    PH_CHECK_LAUNCH();
-    k_p1_tiles<<<(unsigned)ntiles, kThreads, 0, st>>>(a);
-    PH_CHECK_LAUNCH();
-    k_p1_top<<<1, kThreads, 0, st>>>(a.tile_sm, ntiles);
-    PH_CHECK_LAUNCH();
-    k_mark<<<(unsigned)nchunks, kThreads, 0, st>>>(a);
-    PH_CHECK_LAUNCH();
-    k_s2_tiles<<<(unsigned)ntiles, kThreads, 0, st>>>(a);
-    PH_CHECK_LAUNCH();
-    k_s2_top<<<1, kThreads, 0, st>>>(a, ntiles);
-    PH_CHECK_LAUNCH();
-    PH_CUDA(cudaMemcpyAsync(rs.h_totals, rs.totals, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                            st));
-    PH_CUDA(cudaStreamSynchronize(st));
-    const int64_t surv = rs.h_totals[0], words = rs.h_totals[1], pivw = rs.h_totals[2],
-                  targets = rs.h_totals[3];
-    // capacity: next arena and pivot store
-    ColStore& nxt = rs.arena[1 - rs.cur];
-    if (nxt.p == ctx->rows0) {  // never overwrite the boundary matrix in place
-      nxt = ColStore{};
-    }
-    grow_store(ctx, nxt, words);
-    if (rs.pivots.empty() || rs.piv_used + pivw > rs.pivots.back().cap) {
-      ColStore c{};
-      grow_store(ctx, c, std::max<int64_t>(pivw, ctx->nnz / 4 + 1));
-      rs.pivots.push_back(c);
-      rs.piv_used = 0;
-      PH_CUDA(cudaMemsetAsync(rs.piv_bump, 0, sizeof(int64_t), st));
-    }
-    a.arena_next = nxt.p;
-    a.piv_base = rs.pivots.back().p;
-    rs.piv_used += pivw;
-    if (ctx->opts.time_kernels) {
-      cudaEvent_t e0, e1;
-      PH_CUDA(cudaEventCreate(&e0));
-      PH_CUDA(cudaEventCreate(&e1));
-      rs.ev.push_back(e0);
-      rs.ev.push_back(e1);
-      PH_CUDA(cudaEventRecord(e0, st));
-    }
-    PH_CUDA(cudaFuncSetAttribute(k_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kAddSmem));
-    k_add<<<(unsigned)nchunks, kThreads, kAddSmem, st>>>(a);
-    PH_CHECK_LAUNCH();
-    rs.add_launches++;
-    if (ctx->opts.time_kernels) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
-    k_commit<<<grid_for(ctx, n_act, kThreads), kThreads, 0, st>>>(a);
-    PH_CHECK_LAUNCH();
-    std::swap(rs.act, rs.act2);
-    rs.n_act = surv;
-    // the old arena is dead now unless it is the boundary matrix, which stays for reuse
-    rs.cur = 1 - rs.cur;
-    if (targets == 0) {
-      rs.passes = pass;
-      rs.status = PH_OK;
-      break;
-    }
-    if (pass >= max_passes) {
-      rs.passes = pass;
-      rs.next_pass = pass + 1;
-      rs.status = PH_NOT_CONVERGED;
-      break;
-    }
+  const bool use_graph = ctx->opts.use_graph != 0;
+  const bool time_add = ctx->opts.time_kernels != 0 && !use_graph;
+  DevState& h = *static_cast<DevState*>(rs.hstate);
+  // a resumed reduction continues after the pass that hit the previous cap
+  PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  PH_CUDA(cudaStreamSynchronize(st));
+  if (h.status == ST_CAPPED) {
+    h.pass = h.passes + 1;
+    h.status = ST_RUN;
   }
-  if (stats) {
+  h.max_passes = max_passes < 0 ? INT32_MAX : max_passes;
+  PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  const RArgs a = make_args(ctx);
+  if (use_graph && !rs.graph_exec) build_graph(ctx, a);
+  for (;;) {
+    const int32_t first_pass = h.pass;
+    if (use_graph) {
+      PH_CUDA(cudaGraphLaunch(rs.graph_exec, st));
+    } else {
+      launch_pass(ctx, a, 0, false, time_add, st);
+      if (time_add) rs.add_launches++;
+    }
+    PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    PH_CUDA(cudaStreamSynchronize(st));
+    if (use_graph) {  // 11 kernels per executed pass of the graph's loop
+      const int32_t last = (h.status == ST_DONE || h.status == ST_CAPPED) ? h.passes : h.pass;
+      ctx->launches += 11 * (int64_t)(last - first_pass + 1);
+    }
+    if (h.status == ST_RUN) continue;
+    if (h.status == ST_HOST) {
+      if (time_add && rs.ev.size() >= 2) {  // the stopped pass's k_add did no work
+        cudaEventDestroy(rs.ev.back());
+        rs.ev.pop_back();
+        cudaEventDestroy(rs.ev.back());
+        rs.ev.pop_back();
+        rs.add_launches--;
+      }
+      serve_host_request(ctx, h);
+      PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+      continue;
+    }
+    break;
+  }
+  rs.passes = h.passes;
+  rs.status = h.status == ST_DONE ? PH_OK : PH_NOT_CONVERGED;
+  if (ctx->opts.collect_stats) {
     rs.h_stats.assign((size_t)(rs.passes + 1) * PH_PS_N, 0);
     PH_CUDA(cudaMemcpyAsync(rs.h_stats.data(), rs.pass_stats,
                             rs.h_stats.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -929,21 +1172,21 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   }
   rs.ev.clear();
   rs.done = true;
-  (void)m;
   return rs.status;
 }
 
 void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
+  if (rs.graph_exec) cudaGraphExecDestroy(rs.graph_exec);
+  if (rs.graph) cudaGraphDestroy(rs.graph);
   for (void* p : {(void*)rs.act, (void*)rs.act2, (void*)rs.cptr, (void*)rs.clen,
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
-                  (void*)rs.flags, (void*)rs.cleared, (void*)rs.first_unp, rs.tiles,
-                  (void*)rs.totals, (void*)rs.pass_stats, (void*)rs.piv_bump})
+                  (void*)rs.flags, (void*)rs.cleared, (void*)rs.first_unp, rs.tiles, rs.dstate,
+                  (void*)rs.pass_stats})
     ctx->dfree(p);
-  for (auto& a : rs.arena)
-    if (a.p && a.p != ctx->rows0) ctx->dfree(a.p);
+  for (auto& a : rs.arena) ctx->dfree(a.p);
   for (auto& c : rs.pivots) ctx->dfree(c.p);
-  if (rs.h_totals) cudaFreeHost(rs.h_totals);
+  if (rs.hstate) cudaFreeHost(rs.hstate);
   for (auto e : rs.ev) cudaEventDestroy(e);
   rs = ReduceState{};
 }

@@ -115,7 +115,7 @@ class Context:
 
     def __init__(self, *, strict_phase2: bool = False, use_cor10: bool = True,
                  collect_stats: bool = False, staged_merge_max: int = 0, merge_items: int = 0,
-                 use_graph: bool = False, time_kernels: bool = False, stream=None):
+                 use_graph: bool = True, time_kernels: bool = False, stream=None):
         torch = _torch()
         self._torch = torch
         self.lib = load_library()

@@ -151,12 +151,13 @@ def test_merge_paths_agree(ph, orc, staged_max, items):
     assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
 
 
-def test_batched_clouds(ph, orc):
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_clouds(ph, orc, use_graph):
     sizes = [1, 2, 3, 17, 40, 5, 60, 33]
     clouds = [pc.random_cloud(n, 3, 100 + i) for i, n in enumerate(sizes)]
     x = np.concatenate(clouds)
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-    ctx = _gpu(ph, x, 2, offsets=off)
+    ctx = _gpu(ph, x, 2, offsets=off, use_graph=use_graph)
     assert ctx.n_clouds == len(sizes)
     st = ctx.reduce()
     agg = None
@@ -174,11 +175,12 @@ def test_batched_clouds(ph, orc):
     assert st["passes"] == len(agg) - 1
 
 
-def test_max_passes_partial_state(ph, orc):
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_max_passes_partial_state(ph, orc, use_graph):
     x = pc.circle40()
     K = orc.vr_build(x, 2)
     for k in (0, 1, 3, 7):
-        ctx = _gpu(ph, x, 2)
+        ctx = _gpu(ph, x, 2, use_graph=use_graph)
         st = ctx.reduce(max_passes=k)
         ref = orc.reduce_pms(K, max_passes=k)
         assert not st["converged"] and not ref.converged
@@ -242,13 +244,14 @@ def _golden(name):
     return json.loads(p.read_text())
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
 @pytest.mark.parametrize("name", ["circle40", "gauss8_120", "torus400"])
-def test_full_size_single(ph, name):
+def test_full_size_single(ph, name, use_graph):
     g = _golden(name)
     x = {"circle40": pc.circle40, "gauss8_120": pc.gauss8_120, "torus400": pc.torus400}[name]()
     assert _sha(x) == g["coords_sha"], "generator drift: coordinates differ from the golden's"
     max_dim = 3 if name == "gauss8_120" else 2
-    ctx = _gpu(ph, x, max_dim, g.get("max_diam2", -1))
+    ctx = _gpu(ph, x, max_dim, g.get("max_diam2", -1), use_graph=use_graph)
     assert ctx.m == g["m"]
     st = ctx.reduce()
     assert st["converged"] and st["passes"] == g["passes"]
@@ -260,11 +263,12 @@ def test_full_size_single(ph, name):
     assert np.bincount(es["dim"], minlength=max_dim + 1).tolist() == g["ess_per_dim"]
 
 
-def test_full_size_batch512(ph):
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_full_size_batch512(ph, use_graph):
     g = _golden("batch512")
     x, off = pc.batch512()
     assert _sha(x) == g["coords_sha"] and _sha(off) == g["offsets_sha"]
-    ctx = _gpu(ph, x, 2, offsets=off)
+    ctx = _gpu(ph, x, 2, offsets=off, use_graph=use_graph)
     assert ctx.m == g["m"]
     st = ctx.reduce()
     assert st["converged"] and st["passes"] == g["passes"]
@@ -288,3 +292,22 @@ def test_closed_form_complete_skeleton_large(ph):
     assert np.bincount(es["dim"].numpy(), minlength=3).tolist() == [1, 0, math.comb(159, 3)]
     pr = ctx.pairs(0, on_device=False)
     assert np.all(pr["birth_diam2"].numpy() <= pr["death_diam2"].numpy())
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_context_rebuilt_with_other_filtrations(ph, orc, use_graph):
+    # one context: a batched filtration first, then single clouds of other sizes (once, freed
+    # buffers of an earlier filtration were freed again after their addresses were reused)
+    x, off = pc.batch512(n_clouds=48)
+    ctx = _gpu(ph, x, 2, offsets=off, use_graph=use_graph)
+    ctx.reduce()
+    ctx.pairs(0)
+    import torch
+
+    for c in range(len(off) - 1):
+        xc = x[off[c]:off[c + 1]]
+        ctx.build_filtration(torch.from_numpy(np.ascontiguousarray(xc)).cuda(), None, 2)
+        st = ctx.reduce()
+        assert st["converged"]
+        K = orc.vr_build(xc, 2)
+        _check_reduced(orc, ctx, 0, K)
