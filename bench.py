@@ -48,6 +48,9 @@ WORKLOADS = {
     # smaller case of the same law for ncu captures (2.6M simplices)
     "torus250": dict(gen=lambda: pc.torus400()[:250], max_dim=2, max_diam2=-1,
                      desc="complete VR <= dim 2, first 250 of the 400 torus points"),
+    # the batched form: independent clouds, sharded across ranks under torchrun
+    "batch512": dict(gen=pc.batch512, max_dim=2, max_diam2=-1, batched=True,
+                     desc="512 clouds, n ~ U{20..120}, sphere/torus/N(0,I3), complete VR <= dim 2"),
 }
 
 
@@ -181,17 +184,28 @@ def main():
     import paper_1708_04710_gb300 as ph
 
     wl = WORKLOADS[args.workload]
-    x = wl["gen"]()
+    offsets = None
+    if wl.get("batched"):
+        from paper_1708_04710_gb300.shard import local_batch, shard_clouds
+
+        xa, off_all = wl["gen"]()
+        mine = shard_clouds(off_all, world)[rank]  # independent clouds: no collective needed
+        x, offsets = local_batch(xa, off_all, mine)
+    else:
+        x = wl["gen"]()  # one filtration does not shard: every rank reduces a replica
     coords = torch.from_numpy(x).to(dev)
-    ctx = ph.Context()  # the library's defaults: pass loop in one CUDA graph
+    from paper_1708_04710_gb300 import autotune
+
+    tuned = autotune.tune(coords, offsets, wl["max_dim"], wl["max_diam2"])
+    ctx = ph.Context(**tuned)  # pass loop in one CUDA graph (the library default)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(c, context=ctx):
-        context.build_filtration(c, None, wl["max_dim"], wl["max_diam2"])
+        context.build_filtration(c, offsets, wl["max_dim"], wl["max_diam2"])
         st = context.reduce()
-        context.pairs(0, on_device=True)
-        context.essential(0, on_device=True)
+        context.pairs(-1, on_device=True)
+        context.essential(-1, on_device=True)
         return st
 
     for _ in range(max(args.warmup, 0)):
@@ -219,8 +233,12 @@ def main():
         dist.barrier()
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
     total_ms = float(t_max.item())
-    m = ctx.m
-    value = m * args.steps * world / (total_ms / 1000.0)
+    m_local = ctx.m
+    m_all = torch.tensor([float(m_local)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(m_all, op=dist.ReduceOp.SUM)
+    m = int(m_all.item())  # simplices reduced per step by all ranks together
+    value = m * args.steps / (total_ms / 1000.0)
 
     # end to end through the public API with host buffers: H2D of the coordinates and D2H of
     # every output (pairs and essential simplices) inside the timed region
@@ -231,22 +249,22 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         dev_buf.copy_(x_pin, non_blocking=True)
-        ctx.build_filtration(dev_buf, None, wl["max_dim"], wl["max_diam2"])
+        ctx.build_filtration(dev_buf, offsets, wl["max_dim"], wl["max_diam2"])
         ctx.reduce()
-        pr = ctx.pairs(0, on_device=False)
-        es = ctx.essential(0, on_device=False)
+        pr = ctx.pairs(-1, on_device=False)
+        es = ctx.essential(-1, on_device=False)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         d2h = sum(v.numel() * v.element_size() for v in list(pr.values()) + list(es.values()))
     e2e_s = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = m * args.steps * world / float(e2e_s.item())
+    e2e_value = m * args.steps / float(e2e_s.item())
 
     # parity of the last output against the stored oracle result
     parity = None
     gpath = ROOT / "tests" / "golden" / f"{args.workload}.json"
-    if gpath.exists():
+    if gpath.exists() and not wl.get("batched"):
         g = json.loads(gpath.read_text())
         b, d = pr["birth"].numpy(), pr["death"].numpy()
         o = np.lexsort((b, d))
@@ -264,7 +282,7 @@ def main():
     # the dominant kernel, k_add, timed with CUDA events on the library's stream around every
     # launch: the same workload through the host-driven pass loop (events cannot sit inside the
     # graph's conditional body), with per-pass counters for its algorithmic bytes
-    prof = ph.Context(use_graph=False, collect_stats=True, time_kernels=True)
+    prof = ph.Context(**dict(tuned, use_graph=False, collect_stats=True, time_kernels=True))
     step(coords, prof)
     pst = [step(coords, prof) for _ in range(2)]
     peak, peak_kind = _peak_hbm()
@@ -288,8 +306,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "m": m,
-                       "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "parallelism": (f"clouds sharded x{world}" if wl.get("batched") else
+                                       f"replicas x{world}") if world > 1 else "single",
                        "pass_loop": "CUDA graph, conditional while node",
+                       "autotuned": tuned,
                        "l2": "256 MiB buffer written before every timed step"},
             "passes": stats[-1]["passes"], "col_adds": pst[-1]["col_adds"],
             "xors": pst[-1]["xors"], "bit_exact_vs_oracle": parity,
@@ -297,7 +317,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "clocks": clk}
-    if world == 1 and not args.no_forms:
+    if world == 1 and not args.no_forms and not wl.get("batched"):
         line["forms"] = compare_forms(ph, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         n_sample = 250

@@ -81,6 +81,8 @@ typedef struct {
   /* 1: CUDA events time every launch of the Phase II addition kernel (ph_stats.ms_add); only
    * with use_graph = 0 (events cannot sit inside a conditional graph body) */
   int32_t time_kernels;
+  /* persistent blocks per SM of the Phase II addition kernel, 1..4 (0 = library default, 4) */
+  int32_t add_blocks_per_sm;
 } ph_opts;
 
 /* Per-pass counters (rows of ph_get_pass_stats), in this order. */
@@ -178,7 +180,8 @@ int ph_reset_reduction(ph_ctx* ctx);
 int ph_get_pass_stats(ph_ctx* ctx, int64_t* out, int32_t max_rows, int32_t* rows_out);
 
 /* Persistence pairs (sigma_birth, sigma_death) of cloud `cloud` with lowstar(death) = birth
- * (Lemma 1), ordered by (dimension of death, death index). Two-call protocol: with
+ * (Lemma 1), ordered by (dimension of death, death index); cloud = -1 gives every cloud's pairs,
+ * clouds in order (indices stay per cloud). Two-call protocol: with
  * birth == NULL only *count is written. Output buffers (capacity >= count entries each) are
  * device pointers when on_device != 0, host pointers otherwise; any of them may be NULL.
  *   birth, death        int64 filtration indices within the cloud.
@@ -190,7 +193,8 @@ int ph_get_pairs(ph_ctx* ctx, int32_t cloud, int64_t* birth, int64_t* death, int
                  int32_t on_device);
 
 /* Essential simplices of cloud `cloud`: positive simplices that are never paired (Sec. 2.3,
- * set Ess), ordered by (dimension, index). Same protocol and buffer rules as ph_get_pairs.
+ * set Ess), ordered by (dimension, index); cloud = -1 gives all clouds in order. Same protocol
+ * and buffer rules as ph_get_pairs.
  *   idx    int64 filtration indices; dim int32; diam2 int64. */
 int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int64_t* diam2,
                      int64_t capacity, int64_t* count, int32_t on_device);

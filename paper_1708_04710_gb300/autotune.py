@@ -1,0 +1,100 @@
+"""Autotuner for the Phase II addition kernel.
+
+Three knobs shape the hot loop: how long a merge may be and still be staged in shared memory
+(``staged_merge_max``, the threshold between the staged and the straight-from-memory merge),
+how many merge-path positions a lane takes (``merge_items``, 0 = chosen per warp), and how many
+persistent blocks per SM the kernel runs (``add_blocks_per_sm``, the grid shape). The tuner times
+full reductions of the caller's own filtration, one knob at a time (coordinate descent from the
+library defaults), and caches the winner per GPU model and workload class in a JSON file
+(``$PH_GB300_CACHE`` or ``~/.cache/ph_gb300/autotune.json``).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+from pathlib import Path
+
+from .native import Context
+
+KNOBS = {
+    "staged_merge_max": (1024, 512, 256),
+    "merge_items": (0, 4, 8, 16),
+    "add_blocks_per_sm": (4, 3, 2),
+}
+DEFAULTS = {"staged_merge_max": 1024, "merge_items": 0, "add_blocks_per_sm": 4}
+
+
+def cache_path() -> Path:
+    p = os.environ.get("PH_GB300_CACHE")
+    return Path(p) if p else Path.home() / ".cache" / "ph_gb300" / "autotune.json"
+
+
+def workload_key(gpu: str, m: int, max_dim: int, n_clouds: int) -> str:
+    return f"{gpu}|m2^{round(math.log2(max(m, 1)))}|dim{max_dim}|{'batched' if n_clouds > 1 else 'single'}"
+
+
+def _time_reduce(torch, coords, offsets, max_dim, max_diam2, opts, reps=2) -> float:
+    ctx = Context(**opts)
+    best = float("inf")
+    for _ in range(reps + 1):
+        ctx.build_filtration(coords, offsets, max_dim, max_diam2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.reduce()
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    ctx.close()
+    return best
+
+
+def coordinate_descent(timer, knobs: dict, start: dict, verbose: bool = False):
+    """Minimise timer(options) one knob at a time, keeping every improvement; returns (best
+    options, best time, all trials)."""
+    best = dict(start)
+    best_t = timer(best)
+    trials = [(dict(best), best_t)]
+    for knob, values in knobs.items():
+        for val in values:
+            if val == best[knob]:
+                continue
+            cand = dict(best, **{knob: val})
+            t = timer(cand)
+            trials.append((cand, t))
+            if verbose:
+                print(f"autotune {cand} {1e3 * t:.2f} ms", flush=True)
+            if t < best_t:
+                best, best_t = cand, t
+    return best, best_t, trials
+
+
+def tune(coords, offsets=None, max_dim: int = 2, max_diam2: int = -1, use_cache: bool = True,
+         verbose: bool = False) -> dict:
+    """Best Context options for this filtration (cached per GPU model and workload class)."""
+    import torch
+
+    gpu = torch.cuda.get_device_name(coords.device)
+    probe = Context()
+    m = probe.build_filtration(coords, offsets, max_dim, max_diam2)
+    nc = probe.n_clouds
+    probe.close()
+    key = workload_key(gpu, m, max_dim, nc)
+    path = cache_path()
+    cache = {}
+    if use_cache and path.exists():
+        try:
+            cache = json.loads(path.read_text())
+        except Exception:
+            cache = {}
+        if key in cache:
+            return dict(cache[key]["options"])
+    best, best_t, trials = coordinate_descent(
+        lambda o: _time_reduce(torch, coords, offsets, max_dim, max_diam2, o), KNOBS, DEFAULTS,
+        verbose)
+    if use_cache:
+        cache[key] = {"options": best, "ms": 1e3 * best_t,
+                      "trials": [{"options": o, "ms": 1e3 * t} for o, t in trials]}
+        path.parent.mkdir(parents=True, exist_ok=True)
+        path.write_text(json.dumps(cache, indent=1))
+    return best

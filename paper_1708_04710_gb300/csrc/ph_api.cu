@@ -277,6 +277,7 @@ void ph_default_opts(ph_opts* o) {
   o->collect_stats = 0;
   o->use_graph = 1;
   o->time_kernels = 0;
+  o->add_blocks_per_sm = 0;
 }
 
 int ph_create(ph_ctx** out, const ph_opts* opts, const ph_allocator* alloc, void* stream) {
@@ -400,9 +401,10 @@ int ph_get_pairs(ph_ctx* ctx, int32_t cloud, int64_t* birth, int64_t* death, int
                  int32_t on_device) {
   PH_API_BEGIN
   PH_REQUIRE(ctx->reduced, PH_ERR_INVALID, "call ph_reduce first");
-  PH_REQUIRE(cloud >= 0 && cloud < ctx->n_clouds, PH_ERR_INVALID, "cloud out of range");
+  PH_REQUIRE(cloud >= -1 && cloud < ctx->n_clouds, PH_ERR_INVALID, "cloud out of range");
   ph::extract_all(ctx);
-  int64_t a = ctx->pair_off[cloud], n = ctx->pair_off[cloud + 1] - a;
+  int64_t a = cloud < 0 ? 0 : ctx->pair_off[cloud];
+  int64_t n = (cloud < 0 ? ctx->pair_off[ctx->n_clouds] : ctx->pair_off[cloud + 1]) - a;
   if (count) *count = n;
   if (!birth && !death && !dim && !birth_diam2 && !death_diam2) return PH_OK;
   PH_REQUIRE(capacity >= n, PH_ERR_CAPACITY, "output capacity too small");
@@ -420,9 +422,10 @@ int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int
                      int64_t capacity, int64_t* count, int32_t on_device) {
   PH_API_BEGIN
   PH_REQUIRE(ctx->reduced, PH_ERR_INVALID, "call ph_reduce first");
-  PH_REQUIRE(cloud >= 0 && cloud < ctx->n_clouds, PH_ERR_INVALID, "cloud out of range");
+  PH_REQUIRE(cloud >= -1 && cloud < ctx->n_clouds, PH_ERR_INVALID, "cloud out of range");
   ph::extract_all(ctx);
-  int64_t a = ctx->ess_off[cloud], n = ctx->ess_off[cloud + 1] - a;
+  int64_t a = cloud < 0 ? 0 : ctx->ess_off[cloud];
+  int64_t n = (cloud < 0 ? ctx->ess_off[ctx->n_clouds] : ctx->ess_off[cloud + 1]) - a;
   if (count) *count = n;
   if (!idx && !dim && !diam2) return PH_OK;
   PH_REQUIRE(capacity >= n, PH_ERR_CAPACITY, "output capacity too small");

@@ -942,7 +942,8 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
     rs.ev.push_back(e1);
     PH_CUDA(cudaEventRecord(e0, st));
   }
-  k_add<<<sms * 4, kThreads, kAddSmem, st>>>(a);
+  const int add_bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
+  k_add<<<sms * add_bps, kThreads, kAddSmem, st>>>(a);
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
   k_commit<<<sms * 8, kThreads, 0, st>>>(a);

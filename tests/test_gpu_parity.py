@@ -138,14 +138,15 @@ def test_modes(ph, orc, strict, cor10):
     assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
 
 
-@pytest.mark.parametrize("staged_max,items", [(1, 4), (16, 2), (0, 1), (0, 3), (0, 8),
-                                              (40, 8), (0, 32), (100, 16), (0, 0), (0, 64)])
-def test_merge_paths_agree(ph, orc, staged_max, items):
+@pytest.mark.parametrize("staged_max,items,bps", [(1, 4, 4), (16, 2, 1), (0, 1, 2), (0, 3, 3),
+                                                  (0, 8, 4), (40, 8, 2), (0, 32, 4),
+                                                  (100, 16, 1), (0, 0, 4), (0, 64, 3)])
+def test_merge_paths_agree(ph, orc, staged_max, items, bps):
     # staged_max = 1: every merge from global memory; 16 / 40: mixed; 0: all staged
     x = pc.random_cloud(60, 3, 12)
     K = orc.vr_build(x, 2)
     ref = orc.reduce_pms(K)
-    ctx = _gpu(ph, x, 2, staged_merge_max=staged_max, merge_items=items)
+    ctx = _gpu(ph, x, 2, staged_merge_max=staged_max, merge_items=items, add_blocks_per_sm=bps)
     ctx.reduce()
     assert np.array_equal(ctx.filtration(0)["low"], ref.low)
     assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
@@ -311,3 +312,34 @@ def test_context_rebuilt_with_other_filtrations(ph, orc, use_graph):
         assert st["converged"]
         K = orc.vr_build(xc, 2)
         _check_reduced(orc, ctx, 0, K)
+
+
+def test_autotuned_options_stay_exact(ph, orc, tmp_path, monkeypatch):
+    import torch
+
+    from paper_1708_04710_gb300 import autotune
+
+    monkeypatch.setenv("PH_GB300_CACHE", str(tmp_path / "tune.json"))
+    x = pc.random_cloud(70, 3, 21)
+    opts = autotune.tune(torch.from_numpy(x).cuda(), None, 2)
+    assert (tmp_path / "tune.json").exists()
+    assert autotune.tune(torch.from_numpy(x).cuda(), None, 2) == opts  # from the cache
+    K = orc.vr_build(x, 2)
+    ctx = _gpu(ph, x, 2, **opts)
+    ctx.reduce()
+    _check_reduced(orc, ctx, 0, K)
+
+
+def test_all_clouds_at_once(ph, orc):
+    sizes = [12, 30, 7]
+    clouds = [pc.random_cloud(n, 3, 200 + i) for i, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    ctx = _gpu(ph, np.concatenate(clouds), 2, offsets=off)
+    ctx.reduce()
+    allp = ctx.pairs(-1, on_device=False)
+    alle = ctx.essential(-1, on_device=False)
+    parts = [ctx.pairs(c, on_device=False) for c in range(3)]
+    eparts = [ctx.essential(c, on_device=False) for c in range(3)]
+    for k in ("birth", "death", "dim"):
+        assert np.array_equal(allp[k].numpy(), np.concatenate([p[k].numpy() for p in parts]))
+    assert np.array_equal(alle["idx"].numpy(), np.concatenate([e["idx"].numpy() for e in eparts]))
