@@ -179,6 +179,11 @@ int ph_reset_reduction(ph_ctx* ctx);
  * the number of rows available. Needs collect_stats. */
 int ph_get_pass_stats(ph_ctx* ctx, int64_t* out, int32_t max_rows, int32_t* rows_out);
 
+/* Durations (ms, CUDA events) of the Phase II addition kernel, one per pass of the last
+ * ph_reduce with time_kernels = 1 and use_graph = 0; host `out` with room for `max_n`,
+ * *n_out gets the number available. */
+int ph_get_add_times(ph_ctx* ctx, float* out, int32_t max_n, int32_t* n_out);
+
 /* Persistence pairs (sigma_birth, sigma_death) of cloud `cloud` with lowstar(death) = birth
  * (Lemma 1), ordered by (dimension of death, death index); cloud = -1 gives every cloud's pairs,
  * clouds in order (indices stay per cloud). Two-call protocol: with

@@ -389,6 +389,15 @@ int ph_get_pass_stats(ph_ctx* ctx, int64_t* out, int32_t max_rows, int32_t* rows
   PH_API_END
 }
 
+int ph_get_add_times(ph_ctx* ctx, float* out, int32_t max_n, int32_t* n_out) {
+  PH_API_BEGIN
+  const auto& v = ctx->rs.add_ms;
+  if (n_out) *n_out = (int32_t)v.size();
+  if (out) std::memcpy(out, v.data(), sizeof(float) * std::min<size_t>(v.size(), (size_t)max_n));
+  return PH_OK;
+  PH_API_END
+}
+
 static void copy_out(ph_ctx* ctx, void* dst, const void* src, size_t bytes, int on_device) {
   if (!dst || bytes == 0) return;
   PH_CUDA(cudaMemcpyAsync(dst, src, bytes,

@@ -47,6 +47,8 @@ struct ReduceState {
   uint8_t* flags = nullptr;
   uint8_t* cleared = nullptr;  // per id: zeroed by clearing
   void* tiles = nullptr;       // scan scratch
+  void* look = nullptr;        // look-back states of the survivor scan
+  void* dlist = nullptr;       // deferred column updates
   int64_t tiles_bytes = 0;
   void* dstate = nullptr;      // per-pass state in device memory
   void* hstate = nullptr;      // pinned host mirror of it
@@ -64,6 +66,7 @@ struct ReduceState {
   std::vector<cudaEvent_t> ev;   // start/stop pairs around the addition kernel
   int64_t add_launches = 0;
   double ms_add = 0;
+  std::vector<float> add_ms;     // per timed launch
 };
 
 }  // namespace ph

@@ -16,14 +16,13 @@
 //                low(j) > P_j (Thms 6-7). Empty columns become final; the zero case of
 //                Corollary 10 zeroes a column whose candidate rows are all paired. Each new
 //                pivot clears column low(j) (Lemma 1).
-//   k_s2_tiles / k_s2_top
-//                sizes of the surviving columns after this pass's additions (upper bounds).
 //   k_add        Phase II: every colliding column l gets column tab[low(l)] added (XOR of two
 //                sorted row lists). Sources are left-most, hence never targets, so additions
-//                are independent. Survivors are written compactly into the other arena, new
-//                pivots move to the pivot store (their columns never change again). Blocks
-//                take 256-column chunks from a device work queue.
-//   k_commit     publishes the new column locations and the next active list.
+//                are independent. Survivors take their place in the next active list by a
+//                decoupled look-back and their slot in the other arena by atomics; new pivots
+//                move to the pivot store (their columns never change again). Blocks take
+//                256-column chunks from a device work queue.
+//   k_commit     publishes the new locations of the columns other jobs may have been reading.
 //   k_end        advances the pass, decides convergence (no collision left, Thm 8) and, inside a
 //                CUDA graph, sets the conditional that repeats the pass.
 // All per-pass state lives in device memory (DevState), so the same kernel sequence runs either
@@ -37,7 +36,8 @@ namespace ph {
 constexpr int kRItems = 8;
 constexpr int kRTile = kThreads * kRItems;
 
-enum : int32_t { ST_RUN = 0, ST_DONE = 1, ST_CAPPED = 2, ST_HOST = 3 };
+enum : int32_t { ST_RUN = 0, ST_DONE = 1, ST_CAPPED = 2, ST_HOST = 3, ST_FAULT = 4 };
+constexpr int kSpinLimit = 1 << 22;  // iterations of a look-back wait before it gives up
 
 struct DevState {
   int32_t* act;   // active ids, ascending
@@ -55,9 +55,12 @@ struct DevState {
   int32_t status;
   int32_t passes;
   int32_t host_reason;  // 1 arena, 2 pivot store, 4 counter rows
-  int64_t totals[4];    // survivors, words, pivot words, targets of the current pass
+  unsigned long long totals[2];  // survivors and targets of the current pass
   unsigned long long bound_words, bound_piv;
-  unsigned int queue;  // next chunk for k_add
+  unsigned long long arena_used;  // words taken in the arena of the current pass
+  unsigned int queue;             // next chunk for k_add
+  int32_t n_deferred;             // entries of dlist
+  int32_t fault;                  // a bounded wait ran out
 };
 
 struct RArgs {
@@ -80,9 +83,8 @@ struct RArgs {
   int cor10;
   SegMax* tile_sm;    // [ntiles] Phase I tile aggregates (scanned in place to prefixes)
   SegMax* chunk_sm;   // [ntiles][kRItems] aggregate of each 256-entry chunk alone
-  int64_t* tile_cnt;  // [ntiles][2] survivors, words (scanned in place to prefixes)
-  int64_t* tile_aux;  // [ntiles][2] pivot words, targets
-  int64_t* chunk_cnt; // [ntiles][kRItems][2] survivors, words of each chunk alone
+  unsigned long long* look;  // per 256-entry chunk: look-back state of the survivor count
+  int32_t* dlist;     // active slots whose column update waits for k_commit
   int staged_max;     // merges of more rows than this run from global memory
   int force_km;       // > 0: merge-path positions per lane for every warp
 };
@@ -131,6 +133,9 @@ __global__ void k_tab_init(RArgs a) {
     ds->bound_words = 0;
     ds->bound_piv = 0;
     ds->queue = 0;
+    ds->arena_used = 0;
+    ds->n_deferred = 0;
+    ds->totals[0] = ds->totals[1] = 0;
   }
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < a.rows_end;
        x += (int64_t)gridDim.x * blockDim.x) {
@@ -348,74 +353,6 @@ __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
   return jb;
 }
 
-__global__ void k_s2_tiles(RArgs a) {
-  __shared__ int64_t sh[kWarps + 1];
-  if (a.ds->status != ST_RUN) return;
-  const PV v = pass_view(a.ds);
-  for (int64_t t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
-    const int64_t tile0 = t * kRTile;
-    int64_t t0 = 0, t1 = 0, pivw = 0, targ = 0;
-    for (int it = 0; it < kRItems; it++) {
-      Job jb = job_of(a, v, tile0 + it * kThreads + threadIdx.x);
-      int64_t cs, cw;
-      block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, cs);
-      block_excl_sum<int64_t>(jb.words, sh, cw);
-      if (threadIdx.x == 0) {
-        a.chunk_cnt[2 * (t * kRItems + it)] = cs;
-        a.chunk_cnt[2 * (t * kRItems + it) + 1] = cw;
-      }
-      t0 += cs;
-      t1 += cw;
-      targ += jb.target;
-      if (jb.newpiv) pivw += a.clen[jb.j];
-    }
-    int64_t t2, t3;
-    block_excl_sum<int64_t>(pivw, sh, t2);
-    block_excl_sum<int64_t>(targ, sh, t3);
-    if (threadIdx.x == 0) {
-      a.tile_cnt[2 * t] = t0;
-      a.tile_cnt[2 * t + 1] = t1;
-      a.tile_aux[2 * t] = t2;
-      a.tile_aux[2 * t + 1] = t3;
-    }
-  }
-}
-
-__global__ void k_s2_top(RArgs a) {
-  __shared__ int64_t sh[kWarps + 1];
-  DevState* ds = a.ds;
-  if (ds->status != ST_RUN) return;
-  const PV v = pass_view(ds);
-  int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-  for (int64_t base = 0; base < v.ntiles; base += kThreads) {
-    int64_t i = base + threadIdx.x;
-    int64_t v0 = i < v.ntiles ? a.tile_cnt[2 * i] : 0;
-    int64_t v1 = i < v.ntiles ? a.tile_cnt[2 * i + 1] : 0;
-    int64_t v2 = i < v.ntiles ? a.tile_aux[2 * i] : 0;
-    int64_t v3 = i < v.ntiles ? a.tile_aux[2 * i + 1] : 0;
-    int64_t t0, t1, t2, t3;
-    int64_t e0 = block_excl_sum<int64_t>(v0, sh, t0);
-    int64_t e1 = block_excl_sum<int64_t>(v1, sh, t1);
-    block_excl_sum<int64_t>(v2, sh, t2);
-    block_excl_sum<int64_t>(v3, sh, t3);
-    if (i < v.ntiles) {
-      a.tile_cnt[2 * i] = c0 + e0;
-      a.tile_cnt[2 * i + 1] = c1 + e1;
-    }
-    c0 += t0;
-    c1 += t1;
-    c2 += t2;
-    c3 += t3;
-  }
-  if (threadIdx.x == 0) {
-    ds->totals[0] = c0;
-    ds->totals[1] = c1;
-    ds->totals[2] = c2;
-    ds->totals[3] = c3;
-    if (v.stats) v.stats[PH_PS_TARGETS] = c3;
-  }
-}
-
 // ------------------------------------------------------------------------------------------
 // column arithmetic over F2: symmetric difference of two ascending row lists
 // ------------------------------------------------------------------------------------------
@@ -495,12 +432,12 @@ __device__ __forceinline__ int warp_symdiff(const int32_t* __restrict__ A, int n
 constexpr int kStage = 1024;
 struct WarpStage {
   int32_t in[kStage];
+  int32_t* jout[32];    // output slot of the job (its reserved words in the next arena)
   int32_t na[32];
   int32_t nin[32];      // rows staged for the job (na + nb), 0 if not staged
   int32_t in_off[33];   // exclusive prefix of nin over the warp's lanes
   int32_t pad_off[33];  // exclusive prefix of nin rounded up to km
-  int32_t jstart[32];   // first output row of the job, relative to the warp's output base
-  int32_t jcnt[32];     // output rows of the job
+  int32_t jcnt[32];     // output rows of the job so far
   int32_t jlow[32];     // largest output row (new low), -1 if none
 };
 constexpr size_t kAddSmem = sizeof(WarpStage) * kWarps;
@@ -540,28 +477,144 @@ __device__ __forceinline__ int lane_symdiff(const int32_t* __restrict__ sA, int 
   return cnt;
 }
 
-// Phase II for one 256-entry chunk of the active list. After one block scan for the output
-// offsets, every warp works on its own 32 jobs: new pivots are copied to the pivot store;
-// survivors (with or without an addition) are staged in shared memory and merged by a merge
-// path over the concatenation of all of the batch's jobs, each job padded to a multiple of km
-// positions so that a lane's km positions never span two jobs (km is chosen per warp from the
-// mean merge length); outputs are written compactly and in order into the warp's region of the
-// next arena. Merges longer than the staging bound run from global memory.
-__device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
-                                          WarpStage& S, int64_t* sh, int64_t& n_add,
-                                          int64_t& n_xor, int64_t& n_copy) {
-  const int lane = lane_id();
-  const int64_t tile = chunk / kRItems;
-  int64_t cs = a.tile_cnt[2 * tile], cw = a.tile_cnt[2 * tile + 1];
-  for (int64_t c = tile * kRItems; c < chunk; c++) {
-    cs += a.chunk_cnt[2 * c];
-    cw += a.chunk_cnt[2 * c + 1];
+// Symmetric difference of two short sorted columns (na, nb <= S) by one thread: both are loaded
+// into registers, padded with INT32_MAX, B reversed so that the 2S values form a bitonic
+// sequence, sorted by a bitonic merge network (static indices: no divergence, no local memory);
+// equal rows -- one from each column -- end up adjacent and cancel. Returns the output length
+// and the last (largest) row written, -1 if none.
+template <int S>
+__device__ __forceinline__ int reg_symdiff(const int32_t* __restrict__ A, int na,
+                                           const int32_t* __restrict__ B, int nb,
+                                           int32_t* __restrict__ dst, int32_t& last) {
+  int32_t c[2 * S];
+#pragma unroll
+  for (int i = 0; i < S; i++) c[i] = i < na ? __ldg(A + i) : INT32_MAX;
+#pragma unroll
+  for (int i = 0; i < S; i++) c[2 * S - 1 - i] = i < nb ? __ldg(B + i) : INT32_MAX;
+#pragma unroll
+  for (int st = S; st >= 1; st >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 2 * S; i++) {
+      if ((i & st) == 0) {
+        const int32_t x = c[i], y = c[i + st];
+        c[i] = min(x, y);
+        c[i + st] = max(x, y);
+      }
+    }
   }
+  int k = 0;
+  last = -1;
+#pragma unroll
+  for (int i = 0; i < 2 * S; i++) {
+    const int32_t v = c[i];
+    const bool drop = v == INT32_MAX || (i > 0 && c[i - 1] == v) || (i + 1 < 2 * S && c[i + 1] == v);
+    if (!drop) {
+      dst[k++] = v;
+      last = v;
+    }
+  }
+  return k;
+}
+
+constexpr unsigned long long kLookAgg = 1ull << 38, kLookIncl = 2ull << 38;
+constexpr unsigned long long kLookFlags = 3ull << 38, kLookVal = (1ull << 38) - 1;
+
+// Decoupled look-back over the chunks before `chunk`: the number of survivors in all earlier
+// chunks. A chunk publishes its own count (an aggregate state) as soon as its block scan is
+// done and looks back only after its merges, when its predecessors have mostly finished and
+// published inclusive prefixes. Each state word holds its value, so no fence is needed; states
+// carry the pass number and never need resetting within one reduction. Chunks are claimed in
+// order from the work queue, so every predecessor belongs to a running or finished block. A
+// wait that runs past its bound records a fault (reported as an error) and counts as zero.
+__device__ __forceinline__ unsigned long long look_tag(int32_t pass) {
+  return (unsigned long long)(pass & 0xffffff) << 40;
+}
+
+__device__ __forceinline__ void look_publish(const RArgs& a, int32_t pass, int64_t chunk,
+                                             int64_t agg) {
+  atomicExch(a.look + chunk,
+             look_tag(pass) | (chunk == 0 ? kLookIncl : kLookAgg) | (unsigned long long)agg);
+}
+
+// by one full warp; returns the exclusive prefix of `chunk` and publishes its inclusive one
+__device__ __forceinline__ int64_t look_back(const RArgs& a, int32_t pass, int64_t chunk,
+                                             int64_t agg) {
+  if (chunk == 0) return 0;
+  const int lane = lane_id();
+  const unsigned long long tag = look_tag(pass);
+  const unsigned long long* st = a.look;
+  int64_t prefix = 0;
+  bool fault = false;
+  for (int64_t p = chunk - 1;; p -= 32) {
+    const int64_t q = p - lane;
+    unsigned long long w = tag | kLookIncl;  // before chunk 0: nothing
+    if (q >= 0) {
+      for (int it = 0;; it++) {
+        w = *(const volatile unsigned long long*)(st + q);
+        if ((w >> 40) == (tag >> 40) && (w & kLookFlags)) break;
+        if (it > kSpinLimit) {
+          fault = true;
+          w = tag | kLookIncl;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    const bool incl = (w & kLookFlags) == kLookIncl;
+    const unsigned im = __ballot_sync(0xffffffffu, incl);
+    const int stop = im ? __ffs(im) - 1 : 32;  // nearest inclusive state
+    const int64_t val = lane <= stop ? (int64_t)(w & kLookVal) : 0;
+    prefix += __shfl_sync(0xffffffffu, warp_incl_sum(val), 31);
+    if (im || p < 32) break;
+  }
+  if (lane == 0) atomicExch(a.look + chunk, tag | kLookIncl | (unsigned long long)(prefix + agg));
+  if (__any_sync(0xffffffffu, fault) && lane == 0) a.ds->fault = 1;
+  return prefix;
+}
+
+// Phase II for one 256-entry chunk of the active list. Survivors get their place in the next
+// active list from a block scan plus the look-back, and their rows a slot of the next arena
+// from a warp-aggregated atomic. New pivots are copied to the pivot store; survivors (with or
+// without an addition) are merged in registers (short columns, one thread per job) or staged
+// in shared memory and merged by a merge path over the concatenation of the batch's jobs, each
+// padded to a multiple of km positions (km chosen per warp from the mean merge length); merges
+// longer than the staging bound run from global memory. Targets and zeroed columns are updated
+// in place (no other job reads them this pass); new pivots and left-most survivors, which other
+// jobs may be reading as sources, are updated by k_commit.
+struct AddCounts {  // per thread: counts are bounded by the chunks one thread visits
+  int32_t active = 0, cleared = 0, targets = 0, adds = 0;
+  int64_t xors = 0, copied = 0;
+};
+
+__device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
+                                          WarpStage& S, int64_t* sh, int64_t* s_prefix,
+                                          AddCounts& cnt) {
+  const int lane = lane_id();
   const int64_t e = chunk * kThreads + threadIdx.x;
   Job jb = job_of(a, v, e);
-  int64_t ts, tw;
-  const int64_t pos = cs + block_excl_sum<int64_t>(jb.surv ? 1 : 0, sh, ts);
-  const int64_t off = cw + block_excl_sum<int64_t>(jb.words, sh, tw);
+  // one block scan gives both the survivor rank (high 16 bits) and the arena words (low 48)
+  constexpr int kRankShift = 48;
+  constexpr int64_t kWordMask = (int64_t(1) << kRankShift) - 1;
+  const int64_t packed = jb.surv ? ((int64_t(1) << kRankShift) | jb.words) : 0;
+  int64_t tot;
+  const int64_t excl = block_excl_sum<int64_t>(packed, sh, tot);
+  const int64_t n_surv = tot >> kRankShift;
+  const int32_t pass = a.ds->pass;
+  if (threadIdx.x == 0) {
+    look_publish(a, pass, chunk, n_surv);
+    // the chunk's survivors take one contiguous run of the next arena
+    s_prefix[1] = (tot & kWordMask)
+                      ? (int64_t)atomicAdd(&a.ds->arena_used, (unsigned long long)(tot & kWordMask))
+                      : 0;
+    if (n_surv) atomicAdd(&a.ds->totals[0], (unsigned long long)n_surv);
+  }
+  __syncthreads();
+  const int64_t off = s_prefix[1] + (excl & kWordMask);
+  if (jb.j >= 0) {
+    cnt.active++;
+    cnt.cleared += a.cleared[jb.j];
+    cnt.targets += jb.target;
+  }
 
   const int32_t* A = nullptr;
   const int32_t* B = nullptr;
@@ -574,11 +627,8 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       nb = a.clen[jb.src];
     }
   }
-  if (jb.j >= 0 && !jb.newpiv && !jb.surv) {
-    a.nxt_ptr[e] = nullptr;
-    a.nxt_len[e] = 0;
-  }
-  if (jb.surv) v.act2[pos] = jb.j;
+  int32_t* o_ptr = nullptr;  // the column's new place and length
+  int o_len = 0;
 
   // ---- new pivots: their columns never change again; move them to the pivot store
   unsigned pmask = __ballot_sync(0xffffffffu, jb.newpiv);
@@ -593,36 +643,52 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     int32_t* dst = v.piv_base + w0;
     for (int q = lane; q < wna; q += 32) dst[q] = wA[q];
     if (lane == src) {
-      a.nxt_ptr[e] = dst;
-      a.nxt_len[e] = wna;
-      n_copy += wna;
+      o_ptr = dst;
+      o_len = wna;
+      cnt.copied += wna;
     }
   }
 
-  // ---- survivors
-  const unsigned smask = __ballot_sync(0xffffffffu, jb.surv);
+  // ---- survivors: every job writes into its own reserved slot of the next arena
+  int32_t* slot = jb.surv ? v.arena_next + off : nullptr;
+  const int N = jb.surv ? na + nb : 0;
+  // short merges: one thread per job, in registers
+  int cls = !jb.surv ? 0 : (na <= 8 && nb <= 8 ? 1 : (na <= 16 && nb <= 16 ? 2 : 3));
+  // the register path pays off when most of the warp takes it; a few short jobs among long
+  // ones would keep the rest of the warp waiting, so they join the staged path instead
+  if (__popc(__ballot_sync(0xffffffffu, cls == 1 || cls == 2)) < 12 && cls != 0) cls = 3;
+  if (cls == 1 || cls == 2) {
+    int32_t last;
+    const int len = cls == 1 ? reg_symdiff<8>(A, na, B, nb, slot, last)
+                             : reg_symdiff<16>(A, na, B, nb, slot, last);
+    o_ptr = slot;
+    o_len = len;
+    if (B) {
+      a.low[jb.j] = last;
+      cnt.adds++;
+      cnt.xors += (na + nb + len) / 2;
+    } else {
+      cnt.copied += na;
+    }
+  }
+  const unsigned smask = __ballot_sync(0xffffffffu, cls == 3);
   if (smask) {
-    const int first = __ffs(smask) - 1;
-    const int64_t wbase = __shfl_sync(0xffffffffu, off, first);  // warp's output region
-    const int N = jb.surv ? na + nb : 0;
-    const bool big = N > a.staged_max;
-    const int nin = big ? 0 : N;
+    // longer merges: staged in shared memory, merge path over the concatenated jobs
+    const bool big = cls == 3 && N > a.staged_max;
+    const int nin = (cls == 3 && !big) ? N : 0;
     const int in_ex = warp_incl_sum(nin) - nin;
     const int small_total = __shfl_sync(0xffffffffu, in_ex + nin, 31);
     const int n_staged = __popc(__ballot_sync(0xffffffffu, nin > 0));
     const int mean = n_staged ? small_total / n_staged : 0;
-    // longer chunks amortise the two merge-path splits, shorter ones keep lanes balanced
     const int km = a.force_km > 0 ? a.force_km
                                   : (mean >= 160 ? 32 : (mean >= 80 ? 16 : (mean >= 32 ? 8 : 4)));
     const int npad = (nin + km - 1) / km * km;
     const int pad_ex = warp_incl_sum(npad) - npad;
-    const int bigN = big ? N : 0;
-    const int big_ex = warp_incl_sum(bigN) - bigN;
+    S.jout[lane] = slot;
     S.na[lane] = na;
     S.nin[lane] = nin;
     S.in_off[lane] = in_ex;
     S.pad_off[lane] = pad_ex;
-    S.jstart[lane] = 0;
     S.jcnt[lane] = 0;
     S.jlow[lane] = -1;
     if (lane == 31) {
@@ -630,8 +696,6 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       S.pad_off[32] = pad_ex + npad;
     }
     __syncwarp();
-    int32_t* out = v.arena_next + wbase;  // compact outputs of the staged jobs
-    int ocur = 0;
     int c = 0;
     while (c < 32) {
       // batch: jobs c.. whose staged rows fit together
@@ -662,29 +726,12 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
         }
         if (mine && nin < 32) {
           int32_t* d = S.in + (in_ex - in_c);
-          int q = 0;
-          for (; q + 4 <= na; q += 4) {
-            const int32_t v0 = __ldg(A + q), v1 = __ldg(A + q + 1), v2 = __ldg(A + q + 2),
-                          v3 = __ldg(A + q + 3);
-            d[q] = v0;
-            d[q + 1] = v1;
-            d[q + 2] = v2;
-            d[q + 3] = v3;
-          }
-          for (; q < na; q++) d[q] = __ldg(A + q);
-          int r = 0;
-          for (; r + 4 <= nb; r += 4) {
-            const int32_t v0 = __ldg(B + r), v1 = __ldg(B + r + 1), v2 = __ldg(B + r + 2),
-                          v3 = __ldg(B + r + 3);
-            d[na + r] = v0;
-            d[na + r + 1] = v1;
-            d[na + r + 2] = v2;
-            d[na + r + 3] = v3;
-          }
-          for (; r < nb; r++) d[na + r] = __ldg(B + r);
+          for (int q = 0; q < na; q++) d[q] = __ldg(A + q);
+          for (int r = 0; r < nb; r++) d[na + r] = __ldg(B + r);
         }
         __syncwarp();
-        // merge: lane takes one km-position chunk per round
+        // merge: lane takes one km-position chunk per round; outputs go to the job's slot at
+        // the job's running count plus the count of the job's earlier lanes in this round
         const int p0 = S.pad_off[c];
         for (int h0 = 0; h0 < nch; h0 += 32) {
           const int h = h0 + lane;
@@ -710,37 +757,42 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
               cnt = lane_symdiff<false>(sA, x0, x1, sB, y0, y1, nullptr, nullptr);
             }
           }
+          const unsigned peers = __match_any_sync(0xffffffffu, k);
+          const int first_peer = __ffs(peers) - 1, last_peer = 31 - __clz(peers);
           const int incl = warp_incl_sum(cnt);
-          const int o = ocur + incl - cnt;
+          const int seg_ex = (incl - cnt) - __shfl_sync(0xffffffffu, incl - cnt, first_peer);
+          const int seg_tot = __shfl_sync(0xffffffffu, incl, last_peer) -
+                              __shfl_sync(0xffffffffu, incl - cnt, first_peer);
+          const int base = k >= 0 ? S.jcnt[k] : 0;
+          __syncwarp();
           if (k >= 0) {
-            if (h * km == S.pad_off[k] - p0) S.jstart[k] = o;
             if (cnt) {
-              int32_t last;
-              lane_symdiff<true>(sA, x0, x1, sB, y0, y1, out + o, &last);
-              atomicAdd(&S.jcnt[k], cnt);
-              atomicMax(&S.jlow[k], last);
+              int32_t lastv;
+              lane_symdiff<true>(sA, x0, x1, sB, y0, y1, S.jout[k] + base + seg_ex, &lastv);
+              atomicMax(&S.jlow[k], lastv);
             }
+            if (lane == last_peer) S.jcnt[k] = base + seg_tot;
           }
-          ocur += __shfl_sync(0xffffffffu, incl, 31);
+          __syncwarp();
         }
       }
       __syncwarp();
       c = c_end;
     }
     __syncwarp();
-    if (jb.surv && !big) {
+    if (cls == 3 && !big) {
       const int len = S.jcnt[lane];
-      a.nxt_ptr[e] = out + S.jstart[lane];
-      a.nxt_len[e] = len;
+      o_ptr = slot;
+      o_len = len;
       if (B) {
         a.low[jb.j] = S.jlow[lane];
-        n_add++;
-        n_xor += (na + nb + len) / 2;
+        cnt.adds++;
+        cnt.xors += (na + nb + len) / 2;
       } else {
-        n_copy += na;
+        cnt.copied += na;
       }
     }
-    // merges too long to stage: straight from global memory, after the staged outputs
+    // merges too long to stage: straight from global memory into their slot
     unsigned bmask = __ballot_sync(0xffffffffu, big);
     while (bmask) {
       const int src = __ffs(bmask) - 1;
@@ -749,7 +801,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       const int32_t* wB = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)B, src);
       const int wna = __shfl_sync(0xffffffffu, na, src);
       const int wnb = __shfl_sync(0xffffffffu, nb, src);
-      int32_t* wd = v.arena_next + wbase + small_total + __shfl_sync(0xffffffffu, big_ex, src);
+      int32_t* wd = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)slot, src);
       int len;
       int32_t last = -1;
       if (wB) {
@@ -761,69 +813,95 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       if (lane == src) {
         if (B) {
           a.low[jb.j] = last;
-          n_add++;
-          n_xor += (na + nb + len) / 2;
+          cnt.adds++;
+          cnt.xors += (na + nb + len) / 2;
         } else {
-          n_copy += na;
+          cnt.copied += na;
         }
-        a.nxt_ptr[e] = wd;
-        a.nxt_len[e] = len;
+        o_ptr = wd;
+        o_len = len;
       }
     }
   }
+  // ---- the survivors' places in the next active list
+  if (threadIdx.x < 32) {
+    const int64_t pre = look_back(a, pass, chunk, n_surv);
+    if (threadIdx.x == 0) s_prefix[0] = pre;
+  }
+  __syncthreads();
+  if (jb.surv) v.act2[s_prefix[0] + (excl >> kRankShift)] = jb.j;
+  // ---- publish: in place for targets and zeroed columns, through k_commit for the others
+  if (jb.j >= 0) {
+    if (jb.surv && jb.target) {
+      a.cptr[jb.j] = o_ptr;
+      a.clen[jb.j] = o_len;
+    } else if (!jb.surv && !jb.newpiv) {
+      a.flags[jb.j] |= F_FINAL;
+      a.low[jb.j] = -1;
+      a.clen[jb.j] = 0;
+    }
+  }
+  const bool defer = jb.newpiv || (jb.surv && !jb.target);
+  if (defer) {
+    a.nxt_ptr[e] = o_ptr;
+    a.nxt_len[e] = o_len;
+  }
+  const unsigned dmask = __ballot_sync(0xffffffffu, defer);
+  if (dmask) {
+    int d0 = 0;
+    if (lane == __ffs(dmask) - 1) d0 = atomicAdd(&a.ds->n_deferred, __popc(dmask));
+    d0 = __shfl_sync(0xffffffffu, d0, __ffs(dmask) - 1);
+    if (defer) a.dlist[d0 + __popc(dmask & ((1u << lane) - 1))] = (int32_t)e;
+  }
+}
+
+__device__ __forceinline__ void total_add(unsigned long long* t, int64_t v) {
+  int64_t s = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane_id() == 0 && s != 0) atomicAdd(t, (unsigned long long)s);
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
   __shared__ int64_t sh[kWarps + 1];
   __shared__ int64_t s_chunk;
+  __shared__ int64_t s_prefix[2];
   extern __shared__ __align__(16) unsigned char add_smem[];
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
   WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[threadIdx.x >> 5];
-  int64_t n_add = 0, n_xor = 0, n_copy = 0;
-  for (;;) {  // device work queue of chunks
+  AddCounts cnt;
+  for (;;) {  // device work queue of chunks, claimed in order
     if (threadIdx.x == 0) s_chunk = atomicAdd(&a.ds->queue, 1u);
     __syncthreads();
     const int64_t chunk = s_chunk;
     __syncthreads();
     if (chunk >= v.nchunks) break;
-    add_chunk(a, v, chunk, S, sh, n_add, n_xor, n_copy);
+    add_chunk(a, v, chunk, S, sh, s_prefix, cnt);
   }
+  total_add(&a.ds->totals[1], cnt.targets);
   if (v.stats) {
-    stat_add(v.stats, PH_PS_ADDS, n_add);
-    stat_add(v.stats, PH_PS_XORS, n_xor);
-    stat_add(v.stats, PH_PS_COPIED, n_copy);
+    stat_add(v.stats, PH_PS_ADDS, cnt.adds);
+    stat_add(v.stats, PH_PS_XORS, cnt.xors);
+    stat_add(v.stats, PH_PS_COPIED, cnt.copied);
+    stat_add(v.stats, PH_PS_ACTIVE, cnt.active);
+    stat_add(v.stats, PH_PS_CLEARED, cnt.cleared);
+    stat_add(v.stats, PH_PS_TARGETS, cnt.targets);
   }
 }
 
+// the deferred column updates: new pivots (now in the pivot store) and left-most survivors
 __global__ void k_commit(RArgs a) {
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
-  int64_t n_clear = 0, n_act = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < v.n_act;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t j = v.act[e];
-    uint8_t f = a.flags[j];
-    uint8_t c = a.cleared[j];
-    n_act++;
-    n_clear += c;
-    bool surv = !(f & (F_PROVEN | F_FINAL)) && !c;
-    if (f & F_NEWPIV) {
-      a.cptr[j] = a.nxt_ptr[e];
-      a.clen[j] = a.nxt_len[e];
-      a.flags[j] = f & (uint8_t)~F_NEWPIV;
-    } else if (surv) {
-      a.cptr[j] = a.nxt_ptr[e];
-      a.clen[j] = a.nxt_len[e];
-    } else {
-      a.flags[j] = f | F_FINAL;
-      a.low[j] = -1;
-      a.clen[j] = 0;
-    }
-  }
-  if (v.stats) {
-    stat_add(v.stats, PH_PS_ACTIVE, n_act);
-    stat_add(v.stats, PH_PS_CLEARED, n_clear);
+  const int64_t n = a.ds->n_deferred;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = a.dlist[i];
+    const int32_t j = v.act[e];
+    a.cptr[j] = a.nxt_ptr[e];
+    a.clen[j] = a.nxt_len[e];
+    a.flags[j] &= (uint8_t)~F_NEWPIV;
   }
 }
 
@@ -831,13 +909,14 @@ __global__ void k_commit(RArgs a) {
 __global__ void k_end(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DevState* ds = a.ds;
+  if (ds->status == ST_RUN && ds->fault) ds->status = ST_FAULT;
   if (ds->status == ST_RUN) {
     const int32_t p = ds->pass;
-    ds->n_act = ds->totals[0];
+    ds->n_act = (int64_t)ds->totals[0];
     int32_t* t = ds->act;
     ds->act = ds->act2;
     ds->act2 = t;
-    if (ds->totals[3] == 0) {
+    if (ds->totals[1] == 0) {
       ds->status = ST_DONE;
       ds->passes = p;
     } else if (p >= ds->max_passes) {
@@ -902,9 +981,8 @@ static RArgs make_args(ph_ctx* ctx) {
   a.cor10 = ctx->opts.use_cor10;
   a.tile_sm = (SegMax*)rs.tiles;
   a.chunk_sm = a.tile_sm + ntiles;
-  a.tile_cnt = (int64_t*)(a.chunk_sm + ntiles * kRItems);
-  a.tile_aux = a.tile_cnt + 2 * ntiles;
-  a.chunk_cnt = a.tile_aux + 2 * ntiles;
+  a.look = static_cast<unsigned long long*>(rs.look);
+  a.dlist = static_cast<int32_t*>(rs.dlist);
   a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
                                                  : kStage;
   a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
@@ -930,10 +1008,6 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   PH_CHECK_LAUNCH();
   k_mark<<<sms * 8, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_s2_tiles<<<sms * 4, kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
-  k_s2_top<<<1, kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
   if (time_add) {
     cudaEvent_t e0, e1;
     PH_CUDA(cudaEventCreate(&e0));
@@ -946,7 +1020,7 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   k_add<<<sms * add_bps, kThreads, kAddSmem, st>>>(a);
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
-  k_commit<<<sms * 8, kThreads, 0, st>>>(a);
+  k_commit<<<sms * 2, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
   k_end<<<1, 32, 0, st>>>(a, cond, in_graph ? 1 : 0);
   PH_CHECK_LAUNCH();
@@ -978,8 +1052,12 @@ void reduce_init(ph_ctx* ctx) {
   int nseg = (int)ctx->seg_start.size() - 1;
   rs.first_unp = alloc_n<int32_t>(ctx, nseg);
   int64_t ntiles = (m + kRTile - 1) / kRTile;
-  rs.tiles_bytes = ntiles * ((1 + kRItems) * sizeof(SegMax) + (4 + 2 * kRItems) * sizeof(int64_t));
+  rs.tiles_bytes = ntiles * (1 + kRItems) * sizeof(SegMax);
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
+  const int64_t nchunks = (m + kThreads - 1) / kThreads + 1;
+  rs.look = alloc_n<unsigned long long>(ctx, nchunks);
+  PH_CUDA(cudaMemsetAsync(rs.look, 0, nchunks * sizeof(unsigned long long), st));
+  rs.dlist = alloc_n<int32_t>(ctx, m);
   rs.dstate = ctx->dalloc(sizeof(DevState));
   PH_CUDA(cudaMallocHost(&rs.hstate, sizeof(DevState)));
   rs.h_stats.clear();
@@ -1137,9 +1215,9 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     }
     PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     PH_CUDA(cudaStreamSynchronize(st));
-    if (use_graph) {  // 11 kernels per executed pass of the graph's loop
+    if (use_graph) {  // 9 kernels per executed pass of the graph's loop
       const int32_t last = (h.status == ST_DONE || h.status == ST_CAPPED) ? h.passes : h.pass;
-      ctx->launches += 11 * (int64_t)(last - first_pass + 1);
+      ctx->launches += 9 * (int64_t)(last - first_pass + 1);
     }
     if (h.status == ST_RUN) continue;
     if (h.status == ST_HOST) {
@@ -1156,6 +1234,8 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     }
     break;
   }
+  PH_REQUIRE(h.status != ST_FAULT, PH_ERR_CUDA,
+             "a bounded wait in the addition kernel ran out (look-back did not complete)");
   rs.passes = h.passes;
   rs.status = h.status == ST_DONE ? PH_OK : PH_NOT_CONVERGED;
   if (ctx->opts.collect_stats) {
@@ -1168,6 +1248,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     float ms = 0;
     PH_CUDA(cudaEventElapsedTime(&ms, rs.ev[i], rs.ev[i + 1]));
     rs.ms_add += ms;
+    rs.add_ms.push_back(ms);
     cudaEventDestroy(rs.ev[i]);
     cudaEventDestroy(rs.ev[i + 1]);
   }
@@ -1183,6 +1264,7 @@ void free_reduce_state(ph_ctx* ctx) {
   for (void* p : {(void*)rs.act, (void*)rs.act2, (void*)rs.cptr, (void*)rs.clen,
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
                   (void*)rs.flags, (void*)rs.cleared, (void*)rs.first_unp, rs.tiles, rs.dstate,
+                  rs.look, rs.dlist,
                   (void*)rs.pass_stats})
     ctx->dfree(p);
   for (auto& a : rs.arena) ctx->dfree(a.p);

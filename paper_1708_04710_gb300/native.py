@@ -70,6 +70,7 @@ SIGNATURES = {
     "ph_get_filtration": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, POINTER(c_int64)]),
     "ph_beta_static": (c_int, [c_void_p, c_int64, c_int32, c_int64, c_void_p, c_void_p]),
+    "ph_get_add_times": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "ph_kernel_launches": (c_int64, [c_void_p]),
     "ph_last_error": (c_char_p, [c_void_p]),
 }
@@ -247,6 +248,13 @@ class Context:
         return dict(passes=st.passes, status=st.status, converged=(rc == PH_OK), m=st.m,
                     col_adds=st.col_adds, xors=st.xors, alg_bytes=st.alg_bytes,
                     add_bytes=st.add_bytes, add_launches=st.add_launches, ms_add=st.ms_add)
+
+    def add_times(self) -> np.ndarray:
+        n = c_int32(0)
+        self._check(self.lib.ph_get_add_times(self._h, None, 0, byref(n)))
+        out = np.zeros(n.value, np.float32)
+        self._check(self.lib.ph_get_add_times(self._h, _ptr(out), n.value, byref(n)))
+        return out
 
     def kernel_launches(self) -> int:
         return int(self.lib.ph_kernel_launches(self._h))
