@@ -158,6 +158,10 @@ def main():
     ap.add_argument("--workload", default="torus400", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="library default options (short profiler captures)")
+    ap.add_argument("--pass-loop", default="graph", choices=["graph", "host"],
+                    help="pass loop of the timed steps: one CUDA graph, or host-driven")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -196,8 +200,10 @@ def main():
     coords = torch.from_numpy(x).to(dev)
     from paper_1708_04710_gb300 import autotune
 
-    tuned = autotune.tune(coords, offsets, wl["max_dim"], wl["max_diam2"])
-    ctx = ph.Context(**tuned)  # pass loop in one CUDA graph (the library default)
+    tuned = ({} if args.no_autotune
+             else autotune.tune(coords, offsets, wl["max_dim"], wl["max_diam2"]))
+    # the pass loop runs in one CUDA graph by default
+    ctx = ph.Context(**dict(tuned, use_graph=args.pass_loop == "graph"))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -308,7 +314,8 @@ def main():
             "config": {"workload": args.workload, "desc": wl["desc"], "m": m,
                        "parallelism": (f"clouds sharded x{world}" if wl.get("batched") else
                                        f"replicas x{world}") if world > 1 else "single",
-                       "pass_loop": "CUDA graph, conditional while node",
+                       "pass_loop": ("CUDA graph, conditional while node"
+                                     if args.pass_loop == "graph" else "host-driven"),
                        "autotuned": tuned,
                        "l2": "256 MiB buffer written before every timed step"},
             "passes": stats[-1]["passes"], "col_adds": pst[-1]["col_adds"],

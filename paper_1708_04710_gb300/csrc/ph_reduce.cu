@@ -572,6 +572,110 @@ __device__ __forceinline__ int64_t look_back(const RArgs& a, int32_t pass, int64
   return prefix;
 }
 
+// Branch-free merge of one lane's merge-path range A[x0..x1), B[y0..y1) (at most KM + 1 rows,
+// since a split moves an equal pair to one side) into registers: step t takes the smaller head,
+// ties from A first, so the two copies of a row common to both columns come out adjacent.
+template <int KM>
+__device__ __forceinline__ void lane_merge_regs(const int32_t* __restrict__ sA, int x0, int x1,
+                                                const int32_t* __restrict__ sB, int y0, int y1,
+                                                int32_t (&m)[KM + 1]) {
+  int i = x0, j = y0;
+  int32_t va = i < x1 ? sA[i] : INT32_MAX;
+  int32_t vb = j < y1 ? sB[j] : INT32_MAX;
+#pragma unroll
+  for (int t = 0; t <= KM; t++) {
+    const bool ta = va <= vb;
+    m[t] = ta ? va : vb;
+    if (t < KM) {
+      const int nx = ta ? i + 1 : j + 1;
+      const bool ok = ta ? nx < x1 : nx < y1;
+      const int32_t nv = ok ? (ta ? sA : sB)[nx] : INT32_MAX;
+      i = ta ? nx : i;
+      j = ta ? j : nx;
+      va = ta ? nv : va;
+      vb = ta ? vb : nv;
+    }
+  }
+}
+
+// One batch of staged jobs (c..c_end) of a warp, merged by rounds: a lane takes one
+// km-position piece of the padded concatenation per round. Outputs go to the job's slot at the
+// job's running count plus the count of the job's earlier lanes in the round. KM > 0: the piece
+// is merged once into registers and the rows that are not one of an equal pair are written;
+// KM = 0 (a forced piece size without a register form): counted first, then merged again.
+template <int KM>
+__device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p0, int nch,
+                                              int km) {
+  const int lane = lane_id();
+  const int in_c = S.in_off[c];
+  for (int h0 = 0; h0 < nch; h0 += 32) {
+    const int h = h0 + lane;
+    int cnt = 0, k = -1, x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    const int32_t* sA = S.in;
+    const int32_t* sB = S.in;
+    int32_t m[KM + 1];
+    uint32_t keep = 0;
+    if (h < nch) {
+      const int gp = p0 + h * km;
+      int lo = c, hi = c_end - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.pad_off[mid] <= gp) lo = mid; else hi = mid - 1;
+      }
+      k = lo;
+      const int d = gp - S.pad_off[k];
+      const int nk = S.nin[k];
+      if (d < nk) {
+        sA = S.in + (S.in_off[k] - in_c);
+        const int ka = S.na[k], kb = nk - ka;
+        sB = sA + ka;
+        merge_split(sA, ka, sB, kb, d, x0, y0);
+        merge_split(sA, ka, sB, kb, min(d + km, nk), x1, y1);
+        if constexpr (KM > 0) {
+          lane_merge_regs<KM>(sA, x0, x1, sB, y0, y1, m);
+#pragma unroll
+          for (int t = 0; t <= KM; t++) {
+            const bool dup = (t > 0 && m[t - 1] == m[t]) || (t < KM && m[t + 1] == m[t]);
+            if (m[t] != INT32_MAX && !dup) keep |= 1u << t;
+          }
+          cnt = __popc(keep);
+        } else {
+          cnt = lane_symdiff<false>(sA, x0, x1, sB, y0, y1, nullptr, nullptr);
+        }
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    const int first_peer = __ffs(peers) - 1, last_peer = 31 - __clz(peers);
+    const int incl = warp_incl_sum(cnt);
+    const int seg_ex = (incl - cnt) - __shfl_sync(0xffffffffu, incl - cnt, first_peer);
+    const int seg_tot = __shfl_sync(0xffffffffu, incl, last_peer) -
+                        __shfl_sync(0xffffffffu, incl - cnt, first_peer);
+    const int base = k >= 0 ? S.jcnt[k] : 0;
+    __syncwarp();
+    if (k >= 0) {
+      if (cnt) {
+        int32_t* dst = S.jout[k] + base + seg_ex;
+        int32_t lastv = -1;
+        if constexpr (KM > 0) {
+          int q = 0;
+#pragma unroll
+          for (int t = 0; t <= KM; t++) {
+            if (keep & (1u << t)) {
+              dst[q++] = m[t];
+              lastv = m[t];
+            }
+          }
+        } else {
+          lane_symdiff<true>(sA, x0, x1, sB, y0, y1, dst, &lastv);
+        }
+        atomicMax(&S.jlow[k], lastv);
+      }
+      if (lane == last_peer) S.jcnt[k] = base + seg_tot;
+    }
+    __syncwarp();
+  }
+}
+
 // Phase II for one 256-entry chunk of the active list. Survivors get their place in the next
 // active list from a block scan plus the look-back, and their rows a slot of the next arena
 // from a warp-aggregated atomic. New pivots are copied to the pivot store; survivors (with or
@@ -581,14 +685,17 @@ __device__ __forceinline__ int64_t look_back(const RArgs& a, int32_t pass, int64
 // longer than the staging bound run from global memory. Targets and zeroed columns are updated
 // in place (no other job reads them this pass); new pivots and left-most survivors, which other
 // jobs may be reading as sources, are updated by k_commit.
-struct AddCounts {  // per thread: counts are bounded by the chunks one thread visits
-  int32_t active = 0, cleared = 0, targets = 0, adds = 0;
-  int64_t xors = 0, copied = 0;
-};
+enum : int { kCntTargets, kCntActive, kCntCleared, kCntAdds, kCntXors, kCntCopied, kNumCnt };
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
                                           WarpStage& S, int64_t* sh, int64_t* s_prefix,
-                                          AddCounts& cnt) {
+                                          unsigned long long* s_cnt) {
   const int lane = lane_id();
   const int64_t e = chunk * kThreads + threadIdx.x;
   Job jb = job_of(a, v, e);
@@ -610,11 +717,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   }
   __syncthreads();
   const int64_t off = s_prefix[1] + (excl & kWordMask);
-  if (jb.j >= 0) {
-    cnt.active++;
-    cnt.cleared += a.cleared[jb.j];
-    cnt.targets += jb.target;
-  }
+  const int rank = (int)(excl >> kRankShift);
 
   const int32_t* A = nullptr;
   const int32_t* B = nullptr;
@@ -645,7 +748,6 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     if (lane == src) {
       o_ptr = dst;
       o_len = wna;
-      cnt.copied += wna;
     }
   }
 
@@ -663,13 +765,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
                              : reg_symdiff<16>(A, na, B, nb, slot, last);
     o_ptr = slot;
     o_len = len;
-    if (B) {
-      a.low[jb.j] = last;
-      cnt.adds++;
-      cnt.xors += (na + nb + len) / 2;
-    } else {
-      cnt.copied += na;
-    }
+    if (B) a.low[jb.j] = last;
   }
   const unsigned smask = __ballot_sync(0xffffffffu, cls == 3);
   if (smask) {
@@ -681,7 +777,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     const int n_staged = __popc(__ballot_sync(0xffffffffu, nin > 0));
     const int mean = n_staged ? small_total / n_staged : 0;
     const int km = a.force_km > 0 ? a.force_km
-                                  : (mean >= 160 ? 32 : (mean >= 80 ? 16 : (mean >= 32 ? 8 : 4)));
+                                  : (mean >= 80 ? 16 : (mean >= 32 ? 8 : 4));
     const int npad = (nin + km - 1) / km * km;
     const int pad_ex = warp_incl_sum(npad) - npad;
     S.jout[lane] = slot;
@@ -730,50 +826,12 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
           for (int r = 0; r < nb; r++) d[na + r] = __ldg(B + r);
         }
         __syncwarp();
-        // merge: lane takes one km-position chunk per round; outputs go to the job's slot at
-        // the job's running count plus the count of the job's earlier lanes in this round
         const int p0 = S.pad_off[c];
-        for (int h0 = 0; h0 < nch; h0 += 32) {
-          const int h = h0 + lane;
-          int cnt = 0, k = -1, x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-          const int32_t* sA = S.in;
-          const int32_t* sB = S.in;
-          if (h < nch) {
-            const int gp = p0 + h * km;
-            int lo = c, hi = c_end - 1;
-            while (lo < hi) {
-              const int mid = (lo + hi + 1) >> 1;
-              if (S.pad_off[mid] <= gp) lo = mid; else hi = mid - 1;
-            }
-            k = lo;
-            const int d = gp - S.pad_off[k];
-            const int nk = S.nin[k];
-            if (d < nk) {
-              sA = S.in + (S.in_off[k] - in_c);
-              const int ka = S.na[k], kb = nk - ka;
-              sB = sA + ka;
-              merge_split(sA, ka, sB, kb, d, x0, y0);
-              merge_split(sA, ka, sB, kb, min(d + km, nk), x1, y1);
-              cnt = lane_symdiff<false>(sA, x0, x1, sB, y0, y1, nullptr, nullptr);
-            }
-          }
-          const unsigned peers = __match_any_sync(0xffffffffu, k);
-          const int first_peer = __ffs(peers) - 1, last_peer = 31 - __clz(peers);
-          const int incl = warp_incl_sum(cnt);
-          const int seg_ex = (incl - cnt) - __shfl_sync(0xffffffffu, incl - cnt, first_peer);
-          const int seg_tot = __shfl_sync(0xffffffffu, incl, last_peer) -
-                              __shfl_sync(0xffffffffu, incl - cnt, first_peer);
-          const int base = k >= 0 ? S.jcnt[k] : 0;
-          __syncwarp();
-          if (k >= 0) {
-            if (cnt) {
-              int32_t lastv;
-              lane_symdiff<true>(sA, x0, x1, sB, y0, y1, S.jout[k] + base + seg_ex, &lastv);
-              atomicMax(&S.jlow[k], lastv);
-            }
-            if (lane == last_peer) S.jcnt[k] = base + seg_tot;
-          }
-          __syncwarp();
+        switch (km) {
+          case 4: staged_rounds<4>(S, c, c_end, p0, nch, km); break;
+          case 8: staged_rounds<8>(S, c, c_end, p0, nch, km); break;
+          case 16: staged_rounds<16>(S, c, c_end, p0, nch, km); break;
+          default: staged_rounds<0>(S, c, c_end, p0, nch, km); break;
         }
       }
       __syncwarp();
@@ -784,13 +842,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       const int len = S.jcnt[lane];
       o_ptr = slot;
       o_len = len;
-      if (B) {
-        a.low[jb.j] = S.jlow[lane];
-        cnt.adds++;
-        cnt.xors += (na + nb + len) / 2;
-      } else {
-        cnt.copied += na;
-      }
+      if (B) a.low[jb.j] = S.jlow[lane];
     }
     // merges too long to stage: straight from global memory into their slot
     unsigned bmask = __ballot_sync(0xffffffffu, big);
@@ -811,13 +863,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
         len = wna;
       }
       if (lane == src) {
-        if (B) {
-          a.low[jb.j] = last;
-          cnt.adds++;
-          cnt.xors += (na + nb + len) / 2;
-        } else {
-          cnt.copied += na;
-        }
+        if (B) a.low[jb.j] = last;
         o_ptr = wd;
         o_len = len;
       }
@@ -829,7 +875,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     if (threadIdx.x == 0) s_prefix[0] = pre;
   }
   __syncthreads();
-  if (jb.surv) v.act2[s_prefix[0] + (excl >> kRankShift)] = jb.j;
+  if (jb.surv) v.act2[s_prefix[0] + rank] = jb.j;
   // ---- publish: in place for targets and zeroed columns, through k_commit for the others
   if (jb.j >= 0) {
     if (jb.surv && jb.target) {
@@ -853,40 +899,53 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     d0 = __shfl_sync(0xffffffffu, d0, __ffs(dmask) - 1);
     if (defer) a.dlist[d0 + __popc(dmask & ((1u << lane) - 1))] = (int32_t)e;
   }
-}
-
-__device__ __forceinline__ void total_add(unsigned long long* t, int64_t v) {
-  int64_t s = v;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane_id() == 0 && s != 0) atomicAdd(t, (unsigned long long)s);
+  // ---- counters, per warp into the block's shared totals
+  const int n_tgt = __popc(__ballot_sync(0xffffffffu, jb.target));
+  if (lane == 0 && n_tgt) atomicAdd(&s_cnt[kCntTargets], (unsigned long long)n_tgt);
+  if (v.stats) {
+    const bool add = jb.surv && B != nullptr;
+    const bool copy = jb.newpiv || (jb.surv && B == nullptr);
+    const int n_act = __popc(__ballot_sync(0xffffffffu, jb.j >= 0));
+    const int n_clr = __popc(__ballot_sync(0xffffffffu, jb.j >= 0 && a.cleared[jb.j]));
+    const int n_add = __popc(__ballot_sync(0xffffffffu, add));
+    const int64_t xr = warp_sum64(add ? (na + nb + o_len) / 2 : 0);
+    const int64_t cp = warp_sum64(copy ? na : 0);
+    if (lane == 0) {
+      atomicAdd(&s_cnt[kCntActive], (unsigned long long)n_act);
+      atomicAdd(&s_cnt[kCntCleared], (unsigned long long)n_clr);
+      atomicAdd(&s_cnt[kCntAdds], (unsigned long long)n_add);
+      atomicAdd(&s_cnt[kCntXors], (unsigned long long)xr);
+      atomicAdd(&s_cnt[kCntCopied], (unsigned long long)cp);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
   __shared__ int64_t sh[kWarps + 1];
   __shared__ int64_t s_chunk;
   __shared__ int64_t s_prefix[2];
+  __shared__ unsigned long long s_cnt[kNumCnt];
+  __shared__ PV s_v;  // per-pass values from shared memory rather than held in registers
   extern __shared__ __align__(16) unsigned char add_smem[];
   if (a.ds->status != ST_RUN) return;
-  const PV v = pass_view(a.ds);
+  if (threadIdx.x == 0) s_v = pass_view(a.ds);
+  const PV& v = s_v;
   WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[threadIdx.x >> 5];
-  AddCounts cnt;
+  if (threadIdx.x < kNumCnt) s_cnt[threadIdx.x] = 0;
   for (;;) {  // device work queue of chunks, claimed in order
     if (threadIdx.x == 0) s_chunk = atomicAdd(&a.ds->queue, 1u);
     __syncthreads();
     const int64_t chunk = s_chunk;
     __syncthreads();
     if (chunk >= v.nchunks) break;
-    add_chunk(a, v, chunk, S, sh, s_prefix, cnt);
+    add_chunk(a, v, chunk, S, sh, s_prefix, s_cnt);
   }
-  total_add(&a.ds->totals[1], cnt.targets);
-  if (v.stats) {
-    stat_add(v.stats, PH_PS_ADDS, cnt.adds);
-    stat_add(v.stats, PH_PS_XORS, cnt.xors);
-    stat_add(v.stats, PH_PS_COPIED, cnt.copied);
-    stat_add(v.stats, PH_PS_ACTIVE, cnt.active);
-    stat_add(v.stats, PH_PS_CLEARED, cnt.cleared);
-    stat_add(v.stats, PH_PS_TARGETS, cnt.targets);
+  if (threadIdx.x == 0 && s_cnt[kCntTargets]) atomicAdd(&a.ds->totals[1], s_cnt[kCntTargets]);
+  if (v.stats && threadIdx.x == 0) {
+    const int idx[kNumCnt] = {PH_PS_TARGETS, PH_PS_ACTIVE, PH_PS_CLEARED,
+                              PH_PS_ADDS,    PH_PS_XORS,   PH_PS_COPIED};
+    for (int i = 0; i < kNumCnt; i++)
+      if (s_cnt[i]) atomicAdd((unsigned long long*)&v.stats[idx[i]], s_cnt[i]);
   }
 }
 
