@@ -572,6 +572,16 @@ __device__ __forceinline__ int64_t look_back(const RArgs& a, int32_t pass, int64
   return prefix;
 }
 
+// 4-byte asynchronous copy global -> shared (no register staging); completed by
+// cp_async_wait_all, which waits for all of this thread's copies.
+__device__ __forceinline__ void cp_async4(int32_t* smem_dst, const int32_t* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Branch-free merge of one lane's merge-path range A[x0..x1), B[y0..y1) (at most KM + 1 rows,
 // since a split moves an equal pair to one side) into registers: step t takes the smaller head,
 // ties from A first, so the two copies of a row common to both columns come out adjacent.
@@ -615,7 +625,8 @@ __device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p
     const int32_t* sB = S.in;
     int32_t m[KM + 1];
     uint32_t keep = 0;
-    if (h < nch) {
+    int d = 0, nk = 0, ka = 0;
+    if (h < nch) {  // every piece starts inside its job: d < nk
       const int gp = p0 + h * km;
       int lo = c, hi = c_end - 1;
       while (lo < hi) {
@@ -623,25 +634,36 @@ __device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p
         if (S.pad_off[mid] <= gp) lo = mid; else hi = mid - 1;
       }
       k = lo;
-      const int d = gp - S.pad_off[k];
-      const int nk = S.nin[k];
-      if (d < nk) {
-        sA = S.in + (S.in_off[k] - in_c);
-        const int ka = S.na[k], kb = nk - ka;
-        sB = sA + ka;
-        merge_split(sA, ka, sB, kb, d, x0, y0);
-        merge_split(sA, ka, sB, kb, min(d + km, nk), x1, y1);
-        if constexpr (KM > 0) {
-          lane_merge_regs<KM>(sA, x0, x1, sB, y0, y1, m);
+      d = gp - S.pad_off[k];
+      nk = S.nin[k];
+      ka = S.na[k];
+      sA = S.in + (S.in_off[k] - in_c);
+      sB = sA + ka;
+      merge_split(sA, ka, sB, nk - ka, d, x0, y0);
+    }
+    // a piece ends where the next one (the next lane's, same job) starts
+    const int nx0 = __shfl_down_sync(0xffffffffu, x0, 1);
+    const int ny0 = __shfl_down_sync(0xffffffffu, y0, 1);
+    if (k >= 0) {
+      if (d + km >= nk) {
+        x1 = ka;
+        y1 = nk - ka;
+      } else if (lane < 31) {
+        x1 = nx0;
+        y1 = ny0;
+      } else {
+        merge_split(sA, ka, sB, nk - ka, d + km, x1, y1);
+      }
+      if constexpr (KM > 0) {
+        lane_merge_regs<KM>(sA, x0, x1, sB, y0, y1, m);
 #pragma unroll
-          for (int t = 0; t <= KM; t++) {
-            const bool dup = (t > 0 && m[t - 1] == m[t]) || (t < KM && m[t + 1] == m[t]);
-            if (m[t] != INT32_MAX && !dup) keep |= 1u << t;
-          }
-          cnt = __popc(keep);
-        } else {
-          cnt = lane_symdiff<false>(sA, x0, x1, sB, y0, y1, nullptr, nullptr);
+        for (int t = 0; t <= KM; t++) {
+          const bool dup = (t > 0 && m[t - 1] == m[t]) || (t < KM && m[t + 1] == m[t]);
+          if (m[t] != INT32_MAX && !dup) keep |= 1u << t;
         }
+        cnt = __popc(keep);
+      } else {
+        cnt = lane_symdiff<false>(sA, x0, x1, sB, y0, y1, nullptr, nullptr);
       }
     }
     const unsigned peers = __match_any_sync(0xffffffffu, k);
@@ -801,7 +823,8 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       const int nch = (S.pad_off[c_end] - S.pad_off[c]) / km;
       const bool mine = lane >= c && lane < c_end && nin > 0;
       if (__ballot_sync(0xffffffffu, mine)) {
-        // stage: columns of 32+ rows by the whole warp (coalesced), shorter ones by their lane
+        // stage: columns of 32+ rows by the whole warp (coalesced), shorter ones by their lane;
+        // asynchronous copies, so the loads of all of the batch's jobs are in flight together
         unsigned lmask = __ballot_sync(0xffffffffu, mine && nin >= 32);
         while (lmask) {
           const int src = __ffs(lmask) - 1;
@@ -811,20 +834,14 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
           const int wna = __shfl_sync(0xffffffffu, na, src);
           const int wn = __shfl_sync(0xffffffffu, nin, src);
           int32_t* d = S.in + (__shfl_sync(0xffffffffu, in_ex, src) - in_c);
-          for (int q = lane; q < wn; q += 64) {
-            const int q2 = q + 32;
-            const int32_t v0 = q < wna ? __ldg(wA + q) : __ldg(wB + (q - wna));
-            int32_t v1 = 0;
-            if (q2 < wn) v1 = q2 < wna ? __ldg(wA + q2) : __ldg(wB + (q2 - wna));
-            d[q] = v0;
-            if (q2 < wn) d[q2] = v1;
-          }
+          for (int q = lane; q < wn; q += 32) cp_async4(d + q, q < wna ? wA + q : wB + (q - wna));
         }
         if (mine && nin < 32) {
           int32_t* d = S.in + (in_ex - in_c);
-          for (int q = 0; q < na; q++) d[q] = __ldg(A + q);
-          for (int r = 0; r < nb; r++) d[na + r] = __ldg(B + r);
+          for (int q = 0; q < na; q++) cp_async4(d + q, A + q);
+          for (int r = 0; r < nb; r++) cp_async4(d + na + r, B + r);
         }
+        cp_async_wait_all();
         __syncwarp();
         const int p0 = S.pad_off[c];
         switch (km) {
