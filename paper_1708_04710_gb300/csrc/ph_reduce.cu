@@ -777,14 +777,18 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   int32_t* slot = jb.surv ? v.arena_next + off : nullptr;
   const int N = jb.surv ? na + nb : 0;
   // short merges: one thread per job, in registers
-  int cls = !jb.surv ? 0 : (na <= 8 && nb <= 8 ? 1 : (na <= 16 && nb <= 16 ? 2 : 3));
-  // the register path pays off when most of the warp takes it; a few short jobs among long
-  // ones would keep the rest of the warp waiting, so they join the staged path instead
-  if (__popc(__ballot_sync(0xffffffffu, cls == 1 || cls == 2)) < 12 && cls != 0) cls = 3;
-  if (cls == 1 || cls == 2) {
+  // (cls 1: register merge, 3: staged or from global memory). The register path pays off when
+  // most of the warp takes it; a few short jobs among long ones would keep the rest of the warp
+  // waiting, so they join the staged path instead. One network size serves the whole warp.
+  const int need = max(na, nb);
+  int cls = !jb.surv ? 0 : (need <= 16 ? 1 : 3);
+  if (__popc(__ballot_sync(0xffffffffu, cls == 1)) < 12 && cls != 0) cls = 3;
+  const unsigned wneed = __reduce_max_sync(0xffffffffu, cls == 1 ? (unsigned)need : 0u);
+  if (cls == 1) {
     int32_t last;
-    const int len = cls == 1 ? reg_symdiff<8>(A, na, B, nb, slot, last)
-                             : reg_symdiff<16>(A, na, B, nb, slot, last);
+    const int len = wneed <= 4   ? reg_symdiff<4>(A, na, B, nb, slot, last)
+                    : wneed <= 8 ? reg_symdiff<8>(A, na, B, nb, slot, last)
+                                 : reg_symdiff<16>(A, na, B, nb, slot, last);
     o_ptr = slot;
     o_len = len;
     if (B) a.low[jb.j] = last;
