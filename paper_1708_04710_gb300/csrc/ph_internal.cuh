@@ -49,6 +49,7 @@ struct ReduceState {
   void* tiles = nullptr;       // scan scratch
   void* look = nullptr;        // look-back states of the survivor scan
   void* dlist = nullptr;       // deferred column updates
+  void* src_e = nullptr;       // per active slot: source candidate of Phase II
   int64_t tiles_bytes = 0;
   void* dstate = nullptr;      // per-pass state in device memory
   void* hstate = nullptr;      // pinned host mirror of it

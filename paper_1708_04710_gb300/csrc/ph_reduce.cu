@@ -85,6 +85,7 @@ struct RArgs {
   SegMax* chunk_sm;   // [ntiles][kRItems] aggregate of each 256-entry chunk alone
   unsigned long long* look;  // per 256-entry chunk: look-back state of the survivor count
   int32_t* dlist;     // active slots whose column update waits for k_commit
+  int32_t* src_e;     // per active slot: the colliding column's left-most column, -1 if none
   int staged_max;     // merges of more rows than this run from global memory
   int force_km;       // > 0: merge-path positions per lane for every warp
 };
@@ -288,12 +289,14 @@ __global__ void k_mark(RArgs a) {
       int32_t j = v.act[e];
       int32_t l = a.low[j];
       uint8_t f = a.flags[j];
+      const int32_t s = l >= 0 ? a.tab[l] : -1;
+      a.src_e[e] = s != j ? s : -1;  // Phase II reads it in list order
       if (l < 0) {
         a.flags[j] = f | F_FINAL;
         n_zero++;
       } else {
         int32_t P = (pre.seg == val.seg) ? pre.val : -1;
-        bool leftmost = a.tab[l] == j;
+        bool leftmost = s == j;
         int32_t b = a.beta[j];
         if (leftmost && (l == b || l > P)) {
           a.flags[j] = f | F_PROVEN | F_NEWPIV;
@@ -324,31 +327,49 @@ struct Job {
   bool newpiv;    // proven this pass: moves to the pivot store
   bool target;    // collides with an earlier column
   int64_t words;  // arena words reserved (survivors only)
+  const int32_t* A;  // the column's rows (new pivots and survivors)
+  const int32_t* B;  // the source's rows (additions)
+  int na, nb;
 };
 
 __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
-  Job jb{-1, -1, false, false, false, 0};
+  Job jb{-1, -1, false, false, false, 0, nullptr, nullptr, 0, 0};
   if (e >= v.n_act) return jb;
-  int32_t j = v.act[e];
+  // every load is issued up front: the column and its source candidate are known from the
+  // active list and k_mark's per-slot source, so no load waits on another's result
+  const int32_t j = v.act[e];
+  const int32_t s = a.src_e[e];
+  const uint8_t f = a.flags[j];
+  const uint8_t cj = a.cleared[j];
+  const int32_t nj = a.clen[j];
+  const int32_t* pj = a.cptr[j];
+  uint8_t fs = 0, cs = 0;
+  int32_t ns = 0;
+  const int32_t* ps = nullptr;
+  if (s >= 0) {
+    fs = a.flags[s];
+    cs = a.cleared[s];
+    ns = a.clen[s];
+    ps = a.cptr[s];
+  }
   jb.j = j;
-  uint8_t f = a.flags[j];
   jb.newpiv = (f & F_NEWPIV) != 0;
-  jb.surv = !(f & (F_PROVEN | F_FINAL)) && !a.cleared[j];
+  jb.surv = !(f & (F_PROVEN | F_FINAL)) && !cj;
   if (jb.surv) {
-    int32_t l = a.low[j];
-    int32_t s = a.tab[l];
-    jb.words = a.clen[j];
-    if (s != j) {
+    jb.words = nj;
+    if (s >= 0) {
       jb.target = true;
-      if (v.do_adds) {
-        uint8_t fs = a.flags[s];
-        bool ok = !(fs & F_FINAL) && !a.cleared[s] && (!a.strict || (fs & F_PROVEN));
-        if (ok) {
-          jb.src = s;
-          jb.words += a.clen[s];
-        }
+      if (v.do_adds && !(fs & F_FINAL) && !cs && (!a.strict || (fs & F_PROVEN))) {
+        jb.src = s;
+        jb.words += ns;
+        jb.B = ps;
+        jb.nb = ns;
       }
     }
+  }
+  if (jb.newpiv || jb.surv) {
+    jb.A = pj;
+    jb.na = nj;
   }
   return jb;
 }
@@ -741,17 +762,9 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   const int64_t off = s_prefix[1] + (excl & kWordMask);
   const int rank = (int)(excl >> kRankShift);
 
-  const int32_t* A = nullptr;
-  const int32_t* B = nullptr;
-  int na = 0, nb = 0;
-  if (jb.j >= 0 && (jb.newpiv || jb.surv)) {
-    A = a.cptr[jb.j];
-    na = a.clen[jb.j];
-    if (jb.surv && jb.src >= 0) {
-      B = a.cptr[jb.src];
-      nb = a.clen[jb.src];
-    }
-  }
+  const int32_t* A = jb.A;
+  const int32_t* B = jb.B;
+  const int na = jb.na, nb = jb.nb;
   int32_t* o_ptr = nullptr;  // the column's new place and length
   int o_len = 0;
 
@@ -1063,6 +1076,7 @@ static RArgs make_args(ph_ctx* ctx) {
   a.chunk_sm = a.tile_sm + ntiles;
   a.look = static_cast<unsigned long long*>(rs.look);
   a.dlist = static_cast<int32_t*>(rs.dlist);
+  a.src_e = static_cast<int32_t*>(rs.src_e);
   a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
                                                  : kStage;
   a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
@@ -1138,6 +1152,7 @@ void reduce_init(ph_ctx* ctx) {
   rs.look = alloc_n<unsigned long long>(ctx, nchunks);
   PH_CUDA(cudaMemsetAsync(rs.look, 0, nchunks * sizeof(unsigned long long), st));
   rs.dlist = alloc_n<int32_t>(ctx, m);
+  rs.src_e = alloc_n<int32_t>(ctx, m);
   rs.dstate = ctx->dalloc(sizeof(DevState));
   PH_CUDA(cudaMallocHost(&rs.hstate, sizeof(DevState)));
   rs.h_stats.clear();
@@ -1344,7 +1359,7 @@ void free_reduce_state(ph_ctx* ctx) {
   for (void* p : {(void*)rs.act, (void*)rs.act2, (void*)rs.cptr, (void*)rs.clen,
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
                   (void*)rs.flags, (void*)rs.cleared, (void*)rs.first_unp, rs.tiles, rs.dstate,
-                  rs.look, rs.dlist,
+                  rs.look, rs.dlist, rs.src_e,
                   (void*)rs.pass_stats})
     ctx->dfree(p);
   for (auto& a : rs.arena) ctx->dfree(a.p);
