@@ -207,9 +207,13 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(c, context=ctx):
+    def step(c, context=ctx, marks=None):
         context.build_filtration(c, offsets, wl["max_dim"], wl["max_diam2"])
+        if marks:
+            marks[0].record(stream)
         st = context.reduce()
+        if marks:
+            marks[1].record(stream)
         context.pairs(-1, on_device=True)
         context.essential(-1, on_device=True)
         return st
@@ -222,15 +226,20 @@ def main():
     clocks = Clocks(dev.index) if rank == 0 else None
     launches0 = ctx.kernel_launches()
     total_ms, stats = 0.0, []
+    phase_ms = [0.0, 0.0, 0.0]  # filtration build, reduction, extraction
     for _ in range(args.steps):
         flush.fill_(1)  # write 256 MiB (> 129 MB L2) so no step starts from a warm L2
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         e0.record(stream)
-        stats.append(step(coords))
+        stats.append(step(coords, marks=marks))
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+        phase_ms[0] += e0.elapsed_time(marks[0])
+        phase_ms[1] += marks[0].elapsed_time(marks[1])
+        phase_ms[2] += marks[1].elapsed_time(e1)
     torch.cuda.synchronize()
     launches = ctx.kernel_launches() - launches0
     clk = clocks.stop() if clocks else None
@@ -323,7 +332,11 @@ def main():
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": int(launches), "clocks": clk}
+            "gpu_launches": int(launches), "clocks": clk,
+            # the step's three parts, same timed steps (rank 0's clock)
+            "phases": {name: {"ms": t / args.steps,
+                              "simplices_per_s": m_local * args.steps / (t / 1e3) if t else None}
+                       for name, t in zip(("build_filtration", "reduce", "extract"), phase_ms)}}
     if world == 1 and not args.no_forms and not wl.get("batched"):
         line["forms"] = compare_forms(ph, torch, dev)
     if world == 1 and not args.no_cpu_baseline:

@@ -40,7 +40,9 @@ enum {
   PH_ERR_INVALID = -1,  /* bad argument or call order */
   PH_ERR_ALLOC = -2,    /* device allocation failed */
   PH_ERR_CUDA = -3,     /* a CUDA call failed (message in ph_last_error) */
-  PH_ERR_CAPACITY = -4  /* a size limit of the library was exceeded */
+  PH_ERR_CAPACITY = -4, /* a size limit of the library was exceeded */
+  PH_ERR_TIMEOUT = -5   /* the pass loop ran past ph_opts.timeout_ms; the reduction state is
+                         * left as it was after the last complete pass */
 };
 
 typedef struct ph_ctx ph_ctx;
@@ -81,8 +83,12 @@ typedef struct {
   /* 1: CUDA events time every launch of the Phase II addition kernel (ph_stats.ms_add); only
    * with use_graph = 0 (events cannot sit inside a conditional graph body) */
   int32_t time_kernels;
-  /* persistent blocks per SM of the Phase II addition kernel, 1..4 (0 = library default, 4) */
+  /* occupancy of the persistent Phase II addition kernel: 1..4 units of 256 threads per SM
+   * (two 128-thread blocks each; 0 = library default, 4) */
   int32_t add_blocks_per_sm;
+  /* wall-clock bound of one ph_reduce's pass loop in ms, checked on the device at the end of
+   * every pass (0 = library default, 60000); past it the call returns PH_ERR_TIMEOUT */
+  int32_t timeout_ms;
 } ph_opts;
 
 /* Per-pass counters (rows of ph_get_pass_stats), in this order. */
@@ -164,7 +170,8 @@ int ph_load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t*
  * Algorithm 5 with Thms 6-7), zero columns and the zero case of Corollary 10, clears the
  * partners of new pivots (Lemma 1), then adds every colliding column's left-most column into
  * it, until no low collides (Thm 8). All clouds are reduced together.
- *   max_passes    cap on passes with additions (< 0: no cap). When it is hit the call
+ *   max_passes    cap on passes with additions (< 0: m + 1, which a reduction never needs:
+ *                 every pass proves or zeroes at least one column). When it is hit the call
  *                 returns PH_NOT_CONVERGED and the state stays a valid partial reduction.
  *   out           host, optional: summary counters.
  * Synchronises the stream. May be called once per filtration. */

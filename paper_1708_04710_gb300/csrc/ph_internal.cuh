@@ -190,22 +190,22 @@ __device__ __forceinline__ T warp_incl_sum(T v) {
 }
 
 // exclusive block scan (sum) of one value per thread; returns the exclusive prefix and the
-// block total. `sh` must hold kWarps + 1 elements.
-template <class T>
+// block total, for blocks of W warps. `sh` must hold W + 1 elements.
+template <class T, int W = kWarps>
 __device__ __forceinline__ T block_excl_sum(T v, T* sh, T& total) {
   T inc = warp_incl_sum(v);
   int w = threadIdx.x >> 5;
   if (lane_id() == 31) sh[w] = inc;
   __syncthreads();
   if (w == 0) {
-    T x = (lane_id() < kWarps) ? sh[lane_id()] : T(0);
+    T x = (lane_id() < W) ? sh[lane_id()] : T(0);
     T xi = warp_incl_sum(x);
-    if (lane_id() < kWarps) sh[lane_id()] = xi - x;
-    if (lane_id() == kWarps - 1) sh[kWarps] = xi;
+    if (lane_id() < W) sh[lane_id()] = xi - x;
+    if (lane_id() == W - 1) sh[W] = xi;
   }
   __syncthreads();
   T res = inc - v + sh[w];
-  total = sh[kWarps];
+  total = sh[W];
   __syncthreads();
   return res;
 }

@@ -36,7 +36,8 @@ namespace ph {
 constexpr int kRItems = 8;
 constexpr int kRTile = kThreads * kRItems;
 
-enum : int32_t { ST_RUN = 0, ST_DONE = 1, ST_CAPPED = 2, ST_HOST = 3, ST_FAULT = 4 };
+enum : int32_t { ST_RUN = 0, ST_DONE = 1, ST_CAPPED = 2, ST_HOST = 3, ST_FAULT = 4,
+                 ST_TIMEOUT = 5 };
 constexpr int kSpinLimit = 1 << 22;  // iterations of a look-back wait before it gives up
 
 struct DevState {
@@ -55,6 +56,8 @@ struct DevState {
   int32_t status;
   int32_t passes;
   int32_t host_reason;  // 1 arena, 2 pivot store, 4 counter rows
+  unsigned long long t_start;     // global timer (ns) when this ph_reduce's loop began
+  unsigned long long t_limit;     // ns the loop may run before it stops with ST_TIMEOUT
   unsigned long long totals[2];  // survivors and targets of the current pass
   unsigned long long bound_words, bound_piv;
   unsigned long long arena_used;  // words taken in the arena of the current pass
@@ -461,7 +464,10 @@ struct WarpStage {
   int32_t jcnt[32];     // output rows of the job so far
   int32_t jlow[32];     // largest output row (new low), -1 if none
 };
-constexpr size_t kAddSmem = sizeof(WarpStage) * kWarps;
+// Phase II blocks: 128 threads, so a block's barriers wait on 4 warps rather than 8
+constexpr int kAddThreads = 128;
+constexpr int kAddWarps = kAddThreads / 32;
+constexpr size_t kAddSmem = sizeof(WarpStage) * kAddWarps;
 
 // merge the staged rows A[x0..x1), B[y0..y1) of one lane's range; equal rows cancel.
 // With WRITE, the surviving rows go to dst; returns their count and the last one in *last.
@@ -740,14 +746,14 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
                                           WarpStage& S, int64_t* sh, int64_t* s_prefix,
                                           unsigned long long* s_cnt) {
   const int lane = lane_id();
-  const int64_t e = chunk * kThreads + threadIdx.x;
+  const int64_t e = chunk * kAddThreads + threadIdx.x;
   Job jb = job_of(a, v, e);
   // one block scan gives both the survivor rank (high 16 bits) and the arena words (low 48)
   constexpr int kRankShift = 48;
   constexpr int64_t kWordMask = (int64_t(1) << kRankShift) - 1;
   const int64_t packed = jb.surv ? ((int64_t(1) << kRankShift) | jb.words) : 0;
   int64_t tot;
-  const int64_t excl = block_excl_sum<int64_t>(packed, sh, tot);
+  const int64_t excl = block_excl_sum<int64_t, kAddWarps>(packed, sh, tot);
   const int64_t n_surv = tot >> kRankShift;
   const int32_t pass = a.ds->pass;
   if (threadIdx.x == 0) {
@@ -954,8 +960,8 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
-  __shared__ int64_t sh[kWarps + 1];
+__global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
+  __shared__ int64_t sh[kAddWarps + 1];
   __shared__ int64_t s_chunk;
   __shared__ int64_t s_prefix[2];
   __shared__ unsigned long long s_cnt[kNumCnt];
@@ -968,10 +974,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_add(RArgs a) {
   if (threadIdx.x < kNumCnt) s_cnt[threadIdx.x] = 0;
   for (;;) {  // device work queue of chunks, claimed in order
     if (threadIdx.x == 0) s_chunk = atomicAdd(&a.ds->queue, 1u);
-    __syncthreads();
+    __syncthreads();  // also publishes s_v, written by thread 0 before the loop
     const int64_t chunk = s_chunk;
+    const int64_t nchunks = (v.n_act + kAddThreads - 1) / kAddThreads;
     __syncthreads();
-    if (chunk >= v.nchunks) break;
+    if (chunk >= nchunks) break;
     add_chunk(a, v, chunk, S, sh, s_prefix, s_cnt);
   }
   if (threadIdx.x == 0 && s_cnt[kCntTargets]) atomicAdd(&a.ds->totals[1], s_cnt[kCntTargets]);
@@ -998,7 +1005,17 @@ __global__ void k_commit(RArgs a) {
   }
 }
 
-// end of a pass: the next active list, convergence (no collision left) or the pass cap
+// the device's global timer, in ns
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void k_clock_start(DevState* ds) { ds->t_start = global_ns(); }
+
+// end of a pass: the next active list, convergence (no target left), the pass cap, the time
+// bound, and the graph's loop condition
 __global__ void k_end(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DevState* ds = a.ds;
@@ -1017,6 +1034,8 @@ __global__ void k_end(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
       ds->passes = p;
     } else {
       ds->pass = p + 1;
+      // the pass is complete, so a later call can resume from the next one
+      if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
     }
   }
   if (in_graph) cudaGraphSetConditional(cond, ds->status == ST_RUN ? 1u : 0u);
@@ -1111,7 +1130,7 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
     PH_CUDA(cudaEventRecord(e0, st));
   }
   const int add_bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
-  k_add<<<sms * add_bps, kThreads, kAddSmem, st>>>(a);
+  k_add<<<sms * add_bps * (kThreads / kAddThreads), kAddThreads, kAddSmem, st>>>(a);
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
   k_commit<<<sms * 2, kThreads, 0, st>>>(a);
@@ -1148,7 +1167,7 @@ void reduce_init(ph_ctx* ctx) {
   int64_t ntiles = (m + kRTile - 1) / kRTile;
   rs.tiles_bytes = ntiles * (1 + kRItems) * sizeof(SegMax);
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
-  const int64_t nchunks = (m + kThreads - 1) / kThreads + 1;
+  const int64_t nchunks = (m + kAddThreads - 1) / kAddThreads + 1;
   rs.look = alloc_n<unsigned long long>(ctx, nchunks);
   PH_CUDA(cudaMemsetAsync(rs.look, 0, nchunks * sizeof(unsigned long long), st));
   rs.dlist = alloc_n<int32_t>(ctx, m);
@@ -1295,9 +1314,16 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   if (h.status == ST_CAPPED) {
     h.pass = h.passes + 1;
     h.status = ST_RUN;
+  } else if (h.status == ST_TIMEOUT) {  // stopped between two passes
+    h.status = ST_RUN;
   }
-  h.max_passes = max_passes < 0 ? INT32_MAX : max_passes;
+  // every pass proves or zeroes at least one column, so m + 1 passes always suffice
+  h.max_passes = max_passes < 0 ? (int32_t)std::min<int64_t>(ctx->m + 1, INT32_MAX) : max_passes;
+  const int64_t limit_ms = ctx->opts.timeout_ms > 0 ? ctx->opts.timeout_ms : 60000;
+  h.t_limit = (unsigned long long)limit_ms * 1000000ull;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  k_clock_start<<<1, 1, 0, st>>>(static_cast<DevState*>(rs.dstate));
+  PH_CHECK_LAUNCH();
   const RArgs a = make_args(ctx);
   if (use_graph && !rs.graph_exec) build_graph(ctx, a);
   for (;;) {
@@ -1331,6 +1357,8 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   }
   PH_REQUIRE(h.status != ST_FAULT, PH_ERR_CUDA,
              "a bounded wait in the addition kernel ran out (look-back did not complete)");
+  PH_REQUIRE(h.status != ST_TIMEOUT, PH_ERR_TIMEOUT,
+             "the pass loop ran past the time bound (ph_opts.timeout_ms)");
   rs.passes = h.passes;
   rs.status = h.status == ST_DONE ? PH_OK : PH_NOT_CONVERGED;
   if (ctx->opts.collect_stats) {

@@ -30,7 +30,7 @@ class PhOpts(Structure):
     _fields_ = [("strict_phase2", c_int32), ("use_cor10", c_int32), ("block_threads", c_int32),
                 ("staged_merge_max", c_int32), ("merge_items", c_int32),
                 ("collect_stats", c_int32), ("use_graph", c_int32), ("time_kernels", c_int32),
-                ("add_blocks_per_sm", c_int32)]
+                ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32)]
 
 
 class PhStats(Structure):
@@ -118,6 +118,7 @@ class Context:
     def __init__(self, *, strict_phase2: bool = False, use_cor10: bool = True,
                  collect_stats: bool = False, staged_merge_max: int = 0, merge_items: int = 0,
                  use_graph: bool = True, time_kernels: bool = False, add_blocks_per_sm: int = 0,
+                 timeout_ms: int = 0,
                  stream=None):
         torch = _torch()
         self._torch = torch
@@ -133,6 +134,7 @@ class Context:
         opts.use_graph = int(use_graph)
         opts.time_kernels = int(time_kernels)
         opts.add_blocks_per_sm = int(add_blocks_per_sm)
+        opts.timeout_ms = int(timeout_ms)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
         dev_index = self.device.index if self.device.index is not None else 0

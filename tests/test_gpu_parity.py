@@ -193,6 +193,30 @@ def test_max_passes_partial_state(ph, orc, use_graph):
         _check_reduced(orc, ctx, 0, K)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_time_bound_stops_between_passes_and_resumes(ph, orc, use_graph):
+    # a 1 ms bound stops the pass loop after some complete pass; every further call runs at
+    # least one more pass and the result, pass count and counters are those of one call
+    x = pc.torus400()[:160]
+    K = orc.vr_build(x, 2)
+    ref = orc.reduce_pms(K)
+    ctx = _gpu(ph, x, 2, use_graph=use_graph, timeout_ms=1)
+    timeouts = 0
+    for _ in range(ref.passes + 2):
+        try:
+            st = ctx.reduce()
+            break
+        except ph.PHError as err:
+            assert err.code == -5 and "time bound" in str(err)
+            timeouts += 1
+    else:
+        pytest.fail("the reduction did not finish")
+    assert timeouts >= 1
+    assert st["converged"] and st["passes"] == ref.passes
+    assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+
+
 def test_triangulations(ph, orc):
     from helpers import closure, random_compatible_order
 
