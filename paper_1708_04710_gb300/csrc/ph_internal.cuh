@@ -28,6 +28,29 @@ constexpr uint8_t F_PROVEN = 1;  // pivot: low(j) = lowstar(j) > 0 is known
 constexpr uint8_t F_FINAL = 2;   // column is zero and positive for good
 constexpr uint8_t F_NEWPIV = 4;  // proven in the current pass
 
+// Per-column metadata of the reduction, one 16-byte record per id, so that reading a column
+// (its own or a source's) costs one sector rather than one per field.
+struct __align__(16) ColMeta {
+  int32_t* ptr;     // its rows (ascending): boundary matrix, arena or pivot store
+  int32_t len;      // number of rows
+  uint8_t flags;    // F_PROVEN | F_FINAL | F_NEWPIV
+  uint8_t cleared;  // zeroed by clearing (Lemma 1)
+  uint16_t pad;
+};
+static_assert(sizeof(ColMeta) == 16, "one 16-byte record per column");
+
+__device__ __forceinline__ ColMeta load_meta(const ColMeta* p) {
+  const int4 v = *reinterpret_cast<const int4*>(p);
+  ColMeta m;
+  m.ptr = reinterpret_cast<int32_t*>((unsigned long long)(unsigned)v.x |
+                                     ((unsigned long long)(unsigned)v.y << 32));
+  m.len = v.z;
+  m.flags = (uint8_t)(v.w & 0xff);
+  m.cleared = (uint8_t)((v.w >> 8) & 0xff);
+  m.pad = 0;
+  return m;
+}
+
 struct ColStore {  // a device buffer that holds column storage (int32 rows)
   int32_t* p = nullptr;
   int64_t cap = 0;  // words
@@ -37,15 +60,12 @@ struct ReduceState {
   int32_t* act = nullptr;      // active list buffers (which one is current: device state)
   int32_t* act2 = nullptr;
   int64_t act_cap = 0;
-  int32_t** cptr = nullptr;    // per id: pointer to its rows
-  int32_t* clen = nullptr;     // per id: number of rows
+  void* meta = nullptr;        // per id: ColMeta (rows, length, flags, clearing mark)
   int32_t** nxt_ptr = nullptr; // per active slot: new location
   int32_t* nxt_len = nullptr;
   int32_t* owner = nullptr;    // per row id: proven pivot with that low, -1
   int32_t* tab = nullptr;      // per row id: left-most column with that low (this pass)
   int32_t* first_unp = nullptr;// per segment: first row id not known to be paired
-  uint8_t* flags = nullptr;
-  uint8_t* cleared = nullptr;  // per id: zeroed by clearing
   void* tiles = nullptr;       // scan scratch
   void* look = nullptr;        // look-back states of the survivor scan
   void* dlist = nullptr;       // deferred column updates

@@ -70,10 +70,7 @@ struct RArgs {
   DevState* ds;
   int32_t* low;
   const int32_t* beta;
-  uint8_t* flags;
-  uint8_t* cleared;
-  int32_t** cptr;
-  int32_t* clen;
+  ColMeta* meta;      // per id: the column's rows, length, flags and clearing mark
   int32_t** nxt_ptr;
   int32_t* nxt_len;
   int32_t* owner;
@@ -145,7 +142,7 @@ __global__ void k_tab_init(RArgs a) {
        x += (int64_t)gridDim.x * blockDim.x) {
     int32_t o = a.owner[x];
     a.tab[x] = o < 0 ? INT32_MAX : o;
-    bool paired = (a.flags[x] & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
+    bool paired = (a.meta[x].flags & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
     if (!paired) atomicMin(&a.first_unp[a.seg[x]], (int32_t)x);
   }
 }
@@ -222,12 +219,12 @@ __global__ void k_p1_tiles(RArgs a) {
       carry = segmax_combine(carry, tot);
       if (e < v.n_act) {
         const int32_t j = v.act[e];
-        const int32_t n = a.clen[j];
+        const int32_t n = a.meta[j].len;
         bw += n;
         const int32_t l = a.low[j];
         if (l >= 0) {
           const int32_t s = a.tab[l];
-          if (s != j) bw += a.clen[s];  // a target: its source may be added
+          if (s != j) bw += a.meta[s].len;  // a target: its source may be added
           else bp += n;                 // left-most: it may be proven and move
         }
       }
@@ -291,23 +288,23 @@ __global__ void k_mark(RArgs a) {
     if (e < v.n_act) {
       int32_t j = v.act[e];
       int32_t l = a.low[j];
-      uint8_t f = a.flags[j];
+      uint8_t f = a.meta[j].flags;
       const int32_t s = l >= 0 ? a.tab[l] : -1;
       a.src_e[e] = s != j ? s : -1;  // Phase II reads it in list order
       if (l < 0) {
-        a.flags[j] = f | F_FINAL;
+        a.meta[j].flags = f | F_FINAL;
         n_zero++;
       } else {
         int32_t P = (pre.seg == val.seg) ? pre.val : -1;
         bool leftmost = s == j;
         int32_t b = a.beta[j];
         if (leftmost && (l == b || l > P)) {
-          a.flags[j] = f | F_PROVEN | F_NEWPIV;
+          a.meta[j].flags = f | F_PROVEN | F_NEWPIV;
           a.owner[l] = j;
-          a.cleared[l] = 1;  // clearing (Lemma 1): column l is positive and paired with j
+          a.meta[l].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
           n_piv++;
         } else if (a.cor10 && b < 0 && l < a.first_unp[val.seg - a.nc]) {
-          a.flags[j] = f | F_FINAL;  // Corollary 10, zero case
+          a.meta[j].flags = f | F_FINAL;  // Corollary 10, zero case
           n_c10++;
         }
       }
@@ -342,18 +339,20 @@ __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
   // active list and k_mark's per-slot source, so no load waits on another's result
   const int32_t j = v.act[e];
   const int32_t s = a.src_e[e];
-  const uint8_t f = a.flags[j];
-  const uint8_t cj = a.cleared[j];
-  const int32_t nj = a.clen[j];
-  const int32_t* pj = a.cptr[j];
+  const ColMeta mj = load_meta(a.meta + j);  // one 16-byte load per column
+  const uint8_t f = mj.flags;
+  const uint8_t cj = mj.cleared;
+  const int32_t nj = mj.len;
+  const int32_t* pj = mj.ptr;
   uint8_t fs = 0, cs = 0;
   int32_t ns = 0;
   const int32_t* ps = nullptr;
   if (s >= 0) {
-    fs = a.flags[s];
-    cs = a.cleared[s];
-    ns = a.clen[s];
-    ps = a.cptr[s];
+    const ColMeta ms = load_meta(a.meta + s);
+    fs = ms.flags;
+    cs = ms.cleared;
+    ns = ms.len;
+    ps = ms.ptr;
   }
   jb.j = j;
   jb.newpiv = (f & F_NEWPIV) != 0;
@@ -919,12 +918,12 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   // ---- publish: in place for targets and zeroed columns, through k_commit for the others
   if (jb.j >= 0) {
     if (jb.surv && jb.target) {
-      a.cptr[jb.j] = o_ptr;
-      a.clen[jb.j] = o_len;
+      a.meta[jb.j].ptr = o_ptr;
+      a.meta[jb.j].len = o_len;
     } else if (!jb.surv && !jb.newpiv) {
-      a.flags[jb.j] |= F_FINAL;
+      a.meta[jb.j].flags |= F_FINAL;
       a.low[jb.j] = -1;
-      a.clen[jb.j] = 0;
+      a.meta[jb.j].len = 0;
     }
   }
   const bool defer = jb.newpiv || (jb.surv && !jb.target);
@@ -946,7 +945,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     const bool add = jb.surv && B != nullptr;
     const bool copy = jb.newpiv || (jb.surv && B == nullptr);
     const int n_act = __popc(__ballot_sync(0xffffffffu, jb.j >= 0));
-    const int n_clr = __popc(__ballot_sync(0xffffffffu, jb.j >= 0 && a.cleared[jb.j]));
+    const int n_clr = __popc(__ballot_sync(0xffffffffu, jb.j >= 0 && a.meta[jb.j].cleared));
     const int n_add = __popc(__ballot_sync(0xffffffffu, add));
     const int64_t xr = warp_sum64(add ? (na + nb + o_len) / 2 : 0);
     const int64_t cp = warp_sum64(copy ? na : 0);
@@ -999,9 +998,9 @@ __global__ void k_commit(RArgs a) {
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t e = a.dlist[i];
     const int32_t j = v.act[e];
-    a.cptr[j] = a.nxt_ptr[e];
-    a.clen[j] = a.nxt_len[e];
-    a.flags[j] &= (uint8_t)~F_NEWPIV;
+    a.meta[j].ptr = a.nxt_ptr[e];
+    a.meta[j].len = a.nxt_len[e];
+    a.meta[j].flags &= (uint8_t)~F_NEWPIV;
   }
 }
 
@@ -1052,21 +1051,23 @@ struct InitLayout {
 
 // the boundary matrix of a simplicial complex: a column of dimension d > 0 has d + 1 rows,
 // stored in id order from rowbase[d]
-__global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0, int32_t** cptr,
-                              int32_t* clen, int32_t* low, int32_t* act, int32_t* owner,
-                              uint8_t* flags, uint8_t* cleared) {
+__global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0, ColMeta* meta,
+                              int32_t* low, int32_t* act, int32_t* owner) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < m;
        x += (int64_t)gridDim.x * blockDim.x) {
     int d = 0;
     while (d < L.maxd && x >= L.dimoff[d + 1]) d++;
     int32_t* c = rows0 + L.rowbase[d] + (int64_t)(d > 0 ? d + 1 : 0) * (x - L.dimoff[d]);
-    cptr[x] = c;
-    clen[x] = d > 0 ? d + 1 : 0;
+    ColMeta mx;
+    mx.ptr = c;
+    mx.len = d > 0 ? d + 1 : 0;
+    mx.flags = 0;
+    mx.cleared = 0;
+    mx.pad = 0;
+    meta[x] = mx;
     low[x] = d > 0 ? c[d] : -1;  // largest row of the unreduced column
     act[x] = (int32_t)x;
     owner[x] = -1;
-    flags[x] = 0;
-    cleared[x] = 0;
   }
 }
 
@@ -1077,10 +1078,7 @@ static RArgs make_args(ph_ctx* ctx) {
   a.ds = static_cast<DevState*>(rs.dstate);
   a.low = ctx->low;
   a.beta = ctx->beta;
-  a.flags = rs.flags;
-  a.cleared = rs.cleared;
-  a.cptr = rs.cptr;
-  a.clen = rs.clen;
+  a.meta = static_cast<ColMeta*>(rs.meta);
   a.nxt_ptr = rs.nxt_ptr;
   a.nxt_len = rs.nxt_len;
   a.owner = rs.owner;
@@ -1154,14 +1152,11 @@ void reduce_init(ph_ctx* ctx) {
   rs.act = alloc_n<int32_t>(ctx, m);
   rs.act2 = alloc_n<int32_t>(ctx, m);
   rs.act_cap = m;
-  rs.cptr = alloc_n<int32_t*>(ctx, m);
-  rs.clen = alloc_n<int32_t>(ctx, m);
+  rs.meta = alloc_n<ColMeta>(ctx, m);
   rs.nxt_ptr = alloc_n<int32_t*>(ctx, m);
   rs.nxt_len = alloc_n<int32_t>(ctx, m);
   rs.owner = alloc_n<int32_t>(ctx, m);
   rs.tab = alloc_n<int32_t>(ctx, m);
-  rs.flags = alloc_n<uint8_t>(ctx, m);
-  rs.cleared = alloc_n<uint8_t>(ctx, m);
   int nseg = (int)ctx->seg_start.size() - 1;
   rs.first_unp = alloc_n<int32_t>(ctx, nseg);
   int64_t ntiles = (m + kRTile - 1) / kRTile;
@@ -1184,7 +1179,7 @@ void reduce_init(ph_ctx* ctx) {
     rb += (d > 0 ? d + 1 : 0) * (ctx->dimoff[d + 1] - ctx->dimoff[d]);
   }
   k_reduce_init<<<grid_for(ctx, m, kThreads), kThreads, 0, st>>>(
-      m, L, ctx->rows0, rs.cptr, rs.clen, ctx->low, rs.act, rs.owner, rs.flags, rs.cleared);
+      m, L, ctx->rows0, static_cast<ColMeta*>(rs.meta), ctx->low, rs.act, rs.owner);
   PH_CHECK_LAUNCH();
   // first arenas: pass 0 needs at most the boundary matrix twice over
   grow_store(ctx, rs.arena[0], 2 * ctx->nnz + 1);
@@ -1384,9 +1379,9 @@ void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
   if (rs.graph_exec) cudaGraphExecDestroy(rs.graph_exec);
   if (rs.graph) cudaGraphDestroy(rs.graph);
-  for (void* p : {(void*)rs.act, (void*)rs.act2, (void*)rs.cptr, (void*)rs.clen,
+  for (void* p : {(void*)rs.act, (void*)rs.act2, rs.meta,
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
-                  (void*)rs.flags, (void*)rs.cleared, (void*)rs.first_unp, rs.tiles, rs.dstate,
+                  (void*)rs.first_unp, rs.tiles, rs.dstate,
                   rs.look, rs.dlist, rs.src_e,
                   (void*)rs.pass_stats})
     ctx->dfree(p);
