@@ -102,6 +102,8 @@ enum {
   PH_PS_ADDS,          /* column additions done */
   PH_PS_XORS,          /* nontrivial scalar XORs, |target union source| (Sec. 4.1) */
   PH_PS_COPIED,        /* rows moved without an addition (survivors and new pivots) */
+  PH_PS_ESS_EST,       /* |E^l| after the pass's marks: the essential estimate of
+                        * Eq. (essential_iteration), which contains Ess (Lemma 11) */
   PH_PS_N
 };
 
@@ -210,6 +212,14 @@ int ph_get_pairs(ph_ctx* ctx, int32_t cloud, int64_t* birth, int64_t* death, int
  *   idx    int64 filtration indices; dim int32; diam2 int64. */
 int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int64_t* diam2,
                      int64_t capacity, int64_t* count, int32_t on_device);
+
+/* Essential estimate E^l of cloud `cloud` after the passes run so far (Sec. 3.3): E^0 = [m],
+ * E^{l+1} = (E^l minus Paired^l) minus {low(j)} (Eq. essential_iteration), so every essential
+ * simplex is in E^l (Lemma 11) and, after a partial reduction (ph_reduce with max_passes), E^l
+ * is the early-stopping estimate of Ess. Host buffer `in_e` of `count` bytes, one per simplex
+ * of the cloud in filtration order: 1 if in E^l. With in_e == NULL only *count is written.
+ * Needs ph_reduce first. Synchronises the stream. */
+int ph_get_essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* in_e, int64_t* count);
 
 /* Inspection of the filtration of cloud `cloud` in filtration order, for testing the build
  * against an independent implementation. Host buffers of `count` entries (any may be NULL):

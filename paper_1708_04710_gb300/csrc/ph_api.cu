@@ -447,6 +447,21 @@ int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int
   PH_API_END
 }
 
+int ph_get_essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* in_e, int64_t* count) {
+  PH_API_BEGIN
+  PH_REQUIRE(ctx->reduced && ctx->rs.init, PH_ERR_INVALID, "call ph_reduce first");
+  PH_REQUIRE(cloud >= 0 && cloud < ctx->n_clouds, PH_ERR_INVALID, "cloud out of range");
+  const int nc = ctx->n_clouds;
+  int64_t n = 0;
+  for (int d = 0; d <= ctx->max_dim; d++)
+    n += ctx->seg_start[d * nc + cloud + 1] - ctx->seg_start[d * nc + cloud];
+  if (count) *count = n;
+  if (!in_e) return PH_OK;
+  ph::essential_estimate(ctx, cloud, in_e, n);
+  return PH_OK;
+  PH_API_END
+}
+
 int ph_get_filtration(ph_ctx* ctx, int32_t cloud, int32_t* dim, int64_t* diam2, int32_t* verts,
                       int32_t* beta, int32_t* low, int64_t* count) {
   PH_API_BEGIN

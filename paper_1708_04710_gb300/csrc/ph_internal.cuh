@@ -35,7 +35,8 @@ struct __align__(16) ColMeta {
   int32_t len;      // number of rows
   uint8_t flags;    // F_PROVEN | F_FINAL | F_NEWPIV
   uint8_t cleared;  // zeroed by clearing (Lemma 1)
-  uint16_t pad;
+  uint8_t low_seen; // the id was the low of some column at the start of some pass
+  uint8_t spare;
 };
 static_assert(sizeof(ColMeta) == 16, "one 16-byte record per column");
 
@@ -47,8 +48,18 @@ __device__ __forceinline__ ColMeta load_meta(const ColMeta* p) {
   m.len = v.z;
   m.flags = (uint8_t)(v.w & 0xff);
   m.cleared = (uint8_t)((v.w >> 8) & 0xff);
-  m.pad = 0;
+  m.low_seen = (uint8_t)((v.w >> 16) & 0xff);
+  m.spare = 0;
   return m;
+}
+
+// Membership of id x in the essential estimate E^l of Eq. (essential_iteration): E^0 = [m] and
+// E^{l+1} = (E^l \ Paired^l) \ low^l([m]). Paired only grows, so x is in E^l iff it is not
+// paired now (proven pivot, beta_x >= 0 by Thm 5, or the low of a proven pivot) and was never
+// the low of a column at the start of a pass.
+__device__ __forceinline__ bool in_essential_estimate(const ColMeta& mx, int32_t beta_x,
+                                                      int32_t owner_x) {
+  return !(mx.flags & F_PROVEN) && beta_x < 0 && owner_x < 0 && !mx.low_seen;
 }
 
 struct ColStore {  // a device buffer that holds column storage (int32 rows)
@@ -268,6 +279,8 @@ void reduce_init(ph_ctx* ctx);
 int reduce_run(ph_ctx* ctx, int32_t max_passes);
 void extract_all(ph_ctx* ctx);
 void free_reduce_state(ph_ctx* ctx);
+// E^l of one cloud, one byte per simplex in filtration order, into host memory (n bytes)
+void essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* host_out, int64_t n);
 // generic device helpers (ph_scan.cu)
 void excl_scan_i64(ph_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev);
 void radix_sort_u64(ph_ctx* ctx, uint64_t* keys, uint64_t* vals, int64_t n, int lo_bit,

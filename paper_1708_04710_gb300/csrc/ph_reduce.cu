@@ -154,7 +154,10 @@ __global__ void k_tab(RArgs a) {
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t j = v.act[i];
     int32_t l = a.low[j];
-    if (l >= 0 && a.tab[l] > j) atomicMin(&a.tab[l], j);
+    if (l >= 0) {
+      if (a.tab[l] > j) atomicMin(&a.tab[l], j);
+      if (!a.meta[l].low_seen) a.meta[l].low_seen = 1;  // for the essential estimate
+    }
   }
 }
 
@@ -989,6 +992,37 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   }
 }
 
+// |E^l| after this pass's marks (per-pass counter; only with collect_stats)
+__global__ void k_ess_count(RArgs a, int64_t m) {
+  __shared__ int64_t sh[kWarps + 1];
+  if (a.ds->status != ST_RUN) return;
+  int64_t n = 0;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < m;
+       x += (int64_t)gridDim.x * blockDim.x)
+    n += in_essential_estimate(load_meta(a.meta + x), a.beta[x], a.owner[x]);
+  int64_t tot;
+  block_excl_sum<int64_t>(n, sh, tot);
+  if (threadIdx.x == 0 && tot)
+    atomicAdd((unsigned long long*)&a.ds->stats[(int64_t)a.ds->pass * PH_PS_N + PH_PS_ESS_EST],
+              (unsigned long long)tot);
+}
+
+// E^l of the ids [lo, hi) (one dimension of one cloud), as bytes at their filtration index
+__global__ void k_ess_flags(int64_t lo, int64_t hi, const ColMeta* __restrict__ meta,
+                            const int32_t* __restrict__ beta, const int32_t* __restrict__ owner,
+                            const int64_t* __restrict__ gidx, int64_t n, uint8_t* out,
+                            int32_t* bad) {
+  for (int64_t x = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < hi;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = gidx[x];
+    if (g < 0 || g >= n) {
+      *bad = 1;
+      continue;
+    }
+    out[g] = in_essential_estimate(load_meta(meta + x), beta[x], owner[x]) ? 1 : 0;
+  }
+}
+
 // the deferred column updates: new pivots (now in the pivot store) and left-most survivors
 __global__ void k_commit(RArgs a) {
   if (a.ds->status != ST_RUN) return;
@@ -1063,7 +1097,8 @@ __global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0, ColMeta* 
     mx.len = d > 0 ? d + 1 : 0;
     mx.flags = 0;
     mx.cleared = 0;
-    mx.pad = 0;
+    mx.low_seen = 0;
+    mx.spare = 0;
     meta[x] = mx;
     low[x] = d > 0 ? c[d] : -1;  // largest row of the unreduced column
     act[x] = (int32_t)x;
@@ -1119,6 +1154,10 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   PH_CHECK_LAUNCH();
   k_mark<<<sms * 8, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
+  if (ctx->opts.collect_stats) {
+    k_ess_count<<<sms * 4, kThreads, 0, st>>>(a, ctx->m);
+    PH_CHECK_LAUNCH();
+  }
   if (time_add) {
     cudaEvent_t e0, e1;
     PH_CUDA(cudaEventCreate(&e0));
@@ -1331,9 +1370,10 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     }
     PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     PH_CUDA(cudaStreamSynchronize(st));
-    if (use_graph) {  // 9 kernels per executed pass of the graph's loop
+    if (use_graph) {  // kernels per executed pass of the graph's loop
       const int32_t last = (h.status == ST_DONE || h.status == ST_CAPPED) ? h.passes : h.pass;
-      ctx->launches += 9 * (int64_t)(last - first_pass + 1);
+      const int per_pass = 9 + (ctx->opts.collect_stats ? 1 : 0);
+      ctx->launches += per_pass * (int64_t)(last - first_pass + 1);
     }
     if (h.status == ST_RUN) continue;
     if (h.status == ST_HOST) {
@@ -1373,6 +1413,29 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   rs.ev.clear();
   rs.done = true;
   return rs.status;
+}
+
+void essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* host_out, int64_t n) {
+  ReduceState& rs = ctx->rs;
+  const int nc = ctx->n_clouds;
+  uint8_t* d_out = alloc_n<uint8_t>(ctx, n);
+  int32_t* d_bad = alloc_n<int32_t>(ctx, 1);
+  PH_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int32_t), ctx->stream));
+  for (int d = 0; d <= ctx->max_dim; d++) {
+    const int64_t lo = ctx->seg_start[d * nc + cloud], hi = ctx->seg_start[d * nc + cloud + 1];
+    if (hi <= lo) continue;
+    k_ess_flags<<<grid_for(ctx, hi - lo, kThreads), kThreads, 0, ctx->stream>>>(
+        lo, hi, static_cast<const ColMeta*>(rs.meta), ctx->beta, rs.owner, ctx->gidx, n, d_out,
+        d_bad);
+    PH_CHECK_LAUNCH();
+  }
+  int32_t bad = 0;
+  PH_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  PH_CUDA(cudaMemcpyAsync(host_out, d_out, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+  PH_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->dfree(d_out);
+  ctx->dfree(d_bad);
+  PH_REQUIRE(bad == 0, PH_ERR_INVALID, "internal error: filtration index out of range");
 }
 
 void free_reduce_state(ph_ctx* ctx) {

@@ -17,7 +17,7 @@ LIB_PATH = Path(__file__).resolve().parent / "libph_gb300.so"
 
 PH_OK, PH_NOT_CONVERGED = 0, 1
 PS_FIELDS = ("active", "new_pivots", "zero_final", "cor10", "cleared", "targets", "adds",
-             "xors", "copied")
+             "xors", "copied", "ess_est")
 
 
 class PHError(RuntimeError):
@@ -71,6 +71,7 @@ SIGNATURES = {
                                   c_void_p, POINTER(c_int64)]),
     "ph_beta_static": (c_int, [c_void_p, c_int64, c_int32, c_int64, c_void_p, c_void_p]),
     "ph_get_add_times": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
+    "ph_get_essential_estimate": (c_int, [c_void_p, c_int32, c_void_p, POINTER(c_int64)]),
     "ph_kernel_launches": (c_int64, [c_void_p]),
     "ph_last_error": (c_char_p, [c_void_p]),
 }
@@ -257,6 +258,15 @@ class Context:
         out = np.zeros(n.value, np.float32)
         self._check(self.lib.ph_get_add_times(self._h, _ptr(out), n.value, byref(n)))
         return out
+
+    def essential_estimate(self, cloud: int = 0) -> np.ndarray:
+        """E^l after the passes run so far (Eq. essential_iteration), as a boolean mask over the
+        cloud's simplices in filtration order; it contains every essential simplex."""
+        n = c_int64(0)
+        self._check(self.lib.ph_get_essential_estimate(self._h, int(cloud), None, byref(n)))
+        out = np.zeros(n.value, np.uint8)
+        self._check(self.lib.ph_get_essential_estimate(self._h, int(cloud), _ptr(out), byref(n)))
+        return out.astype(bool)
 
     def kernel_launches(self) -> int:
         return int(self.lib.ph_kernel_launches(self._h))

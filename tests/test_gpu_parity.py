@@ -49,6 +49,14 @@ def _gpu(ph, coords, max_dim, max_diam2=-1, offsets=None, **kw):
     return ctx
 
 
+def _check_counters(ctx, ref, cloud=0):
+    """Per-pass counters and the essential estimate E^l against the oracle's pass loop."""
+    ps = ctx.pass_stats()
+    assert np.array_equal(ps[:, :8], ref.stats[:, :8])
+    assert np.array_equal(ps[:, 9], ref.stats[:, 8])  # |E^l| after each pass's marks
+    assert np.array_equal(ctx.essential_estimate(cloud), ref.ess_est)
+
+
 def _canon(pairs_b, pairs_d, ess):
     p = np.stack([pairs_b, pairs_d], 1) if len(pairs_b) else np.zeros((0, 2), np.int64)
     o = np.lexsort((p[:, 0], p[:, 1])) if len(p) else np.zeros(0, int)
@@ -124,7 +132,7 @@ def test_filtration_and_reduction(ph, orc, name, gen, max_dim, cut):
     assert st["converged"]
     ref = _check_reduced(orc, ctx, 0, K)
     assert st["passes"] == ref.passes
-    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+    _check_counters(ctx, ref)
 
 
 @pytest.mark.parametrize("strict,cor10", [(True, True), (False, False), (True, False)])
@@ -135,7 +143,7 @@ def test_modes(ph, orc, strict, cor10):
     st = ctx.reduce()
     ref = _check_reduced(orc, ctx, 0, K, strict=strict, cor10=cor10)
     assert st["passes"] == ref.passes
-    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+    _check_counters(ctx, ref)
 
 
 @pytest.mark.parametrize("staged_max,items,bps", [(1, 4, 4), (16, 2, 1), (0, 1, 2), (0, 3, 3),
@@ -161,18 +169,23 @@ def test_batched_clouds(ph, orc, use_graph):
     ctx = _gpu(ph, x, 2, offsets=off, use_graph=use_graph)
     assert ctx.n_clouds == len(sizes)
     st = ctx.reduce()
-    agg = None
+    agg, ess = None, None
     for c, xc in enumerate(clouds):
         K = orc.vr_build(xc, 2)
         _check_filtration(orc, ctx, c, K)
         ref = _check_reduced(orc, ctx, c, K)
-        s = ref.stats[:, :8]
+        assert np.array_equal(ctx.essential_estimate(c), ref.ess_est)
+        s, e = ref.stats[:, :8], ref.stats[:, 8]
         if agg is None:
-            agg = s
+            agg, ess = s, e
         else:
             n = max(len(agg), len(s))
             agg = np.pad(agg, ((0, n - len(agg)), (0, 0))) + np.pad(s, ((0, n - len(s)), (0, 0)))
+            # a converged cloud's estimate no longer changes
+            ess = np.pad(ess, (0, n - len(ess)), mode="edge") + np.pad(e, (0, n - len(e)),
+                                                                        mode="edge")
     assert np.array_equal(ctx.pass_stats()[:, :8], agg)
+    assert np.array_equal(ctx.pass_stats()[:, 9], ess)
     assert st["passes"] == len(agg) - 1
 
 
@@ -186,7 +199,7 @@ def test_max_passes_partial_state(ph, orc, use_graph):
         ref = orc.reduce_pms(K, max_passes=k)
         assert not st["converged"] and not ref.converged
         assert np.array_equal(ctx.filtration(0)["low"], ref.low)
-        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+        _check_counters(ctx, ref)  # E^l of the early-stopped reduction
         ctx.reset_reduction()
         st = ctx.reduce()
         assert st["converged"]

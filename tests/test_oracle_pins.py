@@ -158,12 +158,28 @@ def test_pms_per_pass_invariants(orc):
         assert np.array_equal(low[r.proven], lowstar[r.proven])  # pivots are reduced
         assert np.all(r.ess_est[ess])  # Lemma 11: Ess is contained in E^l
         if prev is not None:
+            assert np.all(r.ess_est <= prev_e)  # E^l only shrinks (Eq. essential_iteration)
+            assert r.stats[k, 8] == r.ess_est.sum()
             assert np.all(low <= prev)  # low never increases
             # Thm 8: a pass that found collisions changed something
             st = dict(zip(orc.PS_FIELDS, r.stats[k - 1]))
             assert st["targets"] == 0 or (st["new_pivots"] + st["adds"] + st["cor10"]
                                           + st["zero_final"] + st["cleared"]) > 0
-        prev = low
+        prev, prev_e = low, r.ess_est
+    # at convergence every negative column is proven and every paired positive one is the low of
+    # a pivot, so the estimate is exact: E equals Ess of the standard reduction
+    assert np.array_equal(np.flatnonzero(full.ess_est), np.sort(ess))
+
+
+def test_essential_estimate_exact_at_convergence(orc):
+    for x, k, cut in [(pc.random_cloud(30, 3, 21), 2, -1), (pc.random_cloud(14, 4, 22), 3, -1),
+                      (pc.random_cloud(20, 2, 23), 3, int(1.5 * 65536 ** 2))]:
+        K = orc.vr_build(x, k, cut)
+        lowstar = orc.reduce_std(K)[0]
+        _, ess = orc.pairs_and_essential(lowstar, K["dim"])
+        for strict in (False, True):
+            r = orc.reduce_pms(K, strict=strict)
+            assert r.converged and np.array_equal(np.flatnonzero(r.ess_est), np.sort(ess))
 
 
 def test_vr_filtration_properties(orc):
