@@ -6,25 +6,27 @@
 //                that is not known to be paired (for Corollary 10).
 //   k_tab        tab[low(j)] <- min j over the active columns (atomicMin): the left-most column
 //                with each low, which defines the neighbour sets N(j) (Eq. neighbours).
-//   k_p1_tiles / k_p1_top
-//                Phase I (Algorithm 5) as a segmented exclusive prefix-max over the active
+//   k_p1_tiles   Phase I (Algorithm 5) as a segmented exclusive prefix-max over the active
 //                columns of each (cloud, dim): P_j = largest low of an earlier colliding column;
-//                also upper bounds of the space this pass can need.
-//   k_check      stops the pass before anything changes if the bounds exceed the space the host
-//                provided (the host then grows it and the pass runs again).
+//                also upper bounds of the space this pass can need. The block that finishes
+//                last scans the tile aggregates and stops the pass before anything changes if
+//                the bounds exceed the space the host provided (the host then grows it and the
+//                pass runs again).
 //   k_mark       j is proven if it is left-most for its low and low(j) = beta_j (Thm 5) or
 //                low(j) > P_j (Thms 6-7). Empty columns become final; the zero case of
 //                Corollary 10 zeroes a column whose candidate rows are all paired. Each new
-//                pivot clears column low(j) (Lemma 1).
+//                pivot clears column low(j) (Lemma 1). Each active slot's source candidate is
+//                stored for Phase II.
 //   k_add        Phase II: every colliding column l gets column tab[low(l)] added (XOR of two
 //                sorted row lists). Sources are left-most, hence never targets, so additions
 //                are independent. Survivors take their place in the next active list by a
-//                decoupled look-back and their slot in the other arena by atomics; new pivots
-//                move to the pivot store (their columns never change again). Blocks take
-//                256-column chunks from a device work queue.
-//   k_commit     publishes the new locations of the columns other jobs may have been reading.
-//   k_end        advances the pass, decides convergence (no collision left, Thm 8) and, inside a
-//                CUDA graph, sets the conditional that repeats the pass.
+//                decoupled look-back and their slot in the other arena by one atomic per chunk;
+//                new pivots move to the pivot store (their columns never change again). Blocks
+//                of 128 threads take 128-slot chunks from a device work queue.
+//   k_commit     publishes the new locations of the columns other jobs may have been reading;
+//                its last block ends the pass: the next active list, convergence (no collision
+//                left, Thm 8), the pass cap and time bound, and inside a CUDA graph the
+//                conditional that repeats the pass.
 // All per-pass state lives in device memory (DevState), so the same kernel sequence runs either
 // from a host loop or as the body of a graph's conditional while node.
 #include <algorithm>
@@ -56,6 +58,7 @@ struct DevState {
   int32_t status;
   int32_t passes;
   int32_t host_reason;  // 1 arena, 2 pivot store, 4 counter rows
+  unsigned int blocks_done;       // blocks of the current grid that have finished (last-block)
   unsigned long long t_start;     // global timer (ns) when this ph_reduce's loop began
   unsigned long long t_limit;     // ns the loop may run before it stops with ST_TIMEOUT
   unsigned long long totals[2];  // survivors and targets of the current pass
@@ -202,6 +205,47 @@ __device__ __forceinline__ SegMax block_scan_segmax(SegMax v, SegMax carry, SegM
   return ex;
 }
 
+// True in the one block that finishes the grid last; it then sees every other block's writes.
+__device__ __forceinline__ bool last_block(unsigned int* done) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return s_last;
+}
+
+// scan of the tile aggregates to tile prefixes, by one block
+__device__ __forceinline__ void p1_top(const RArgs& a, const PV& v, SegMax* sh) {
+  SegMax carry{-1, -1};
+  for (int64_t base = 0; base < v.ntiles; base += kThreads) {
+    int64_t i = base + threadIdx.x;
+    SegMax val{INT32_MAX, -1};
+    if (i < v.ntiles) {  // written by other blocks of this grid: read from L2
+      const int2 t = __ldcg(reinterpret_cast<const int2*>(a.tile_sm + i));
+      val = SegMax{t.x, t.y};
+    }
+    SegMax tot;
+    SegMax ex = block_scan_segmax(val, carry, sh, tot);
+    if (i < v.ntiles) a.tile_sm[i] = ex;
+    carry = tot;
+  }
+}
+
+// the space this pass can need (arena, pivot store, counter rows) against what the host
+// provided; nothing has changed yet, so a pass stopped here runs again unchanged once the host
+// has grown the buffers
+__device__ __forceinline__ void check_capacity(DevState* ds) {
+  int reason = 0;
+  if (ds->bound_words > (unsigned long long)ds->arena_cap[ds->pass & 1]) reason |= 1;
+  if (ds->bound_piv + ds->piv_used > (unsigned long long)ds->piv_cap) reason |= 2;
+  if (ds->stats && ds->pass >= ds->stats_rows) reason |= 4;
+  if (reason) {
+    ds->host_reason = reason;
+    ds->status = ST_HOST;
+  }
+}
+
 // per tile: Phase I aggregates of each chunk and of the tile, and upper bounds of the arena
 // words (target + source) and pivot-store words (only a left-most column can become a pivot)
 __global__ void k_p1_tiles(RArgs a) {
@@ -241,37 +285,18 @@ __global__ void k_p1_tiles(RArgs a) {
     atomicAdd(&a.ds->bound_words, (unsigned long long)tw);
     atomicAdd(&a.ds->bound_piv, (unsigned long long)tp);
   }
-}
-
-__global__ void k_p1_top(RArgs a) {
-  __shared__ SegMax sh[kWarps + 1];
-  if (a.ds->status != ST_RUN) return;
-  const PV v = pass_view(a.ds);
-  SegMax carry{-1, -1};
-  for (int64_t base = 0; base < v.ntiles; base += kThreads) {
-    int64_t i = base + threadIdx.x;
-    SegMax val = i < v.ntiles ? a.tile_sm[i] : SegMax{INT32_MAX, -1};
-    SegMax tot;
-    SegMax ex = block_scan_segmax(val, carry, sh, tot);
-    if (i < v.ntiles) a.tile_sm[i] = ex;
-    carry = tot;
+  // the last block scans the tile aggregates and checks capacity (no extra launches)
+  if (last_block(&a.ds->blocks_done)) {
+    p1_top(a, v, sh);
+    if (threadIdx.x == 0) {
+      a.ds->blocks_done = 0;
+      check_capacity(a.ds);
+    }
   }
 }
 
-// the space this pass can need, against what the host provided; nothing has changed yet, so a
-// pass stopped here runs again unchanged once the host has grown the buffers
-__global__ void k_check(RArgs a) {
-  DevState* ds = a.ds;
-  if (ds->status != ST_RUN || threadIdx.x != 0 || blockIdx.x != 0) return;
-  int reason = 0;
-  if (ds->bound_words > (unsigned long long)ds->arena_cap[ds->pass & 1]) reason |= 1;
-  if (ds->bound_piv + ds->piv_used > (unsigned long long)ds->piv_cap) reason |= 2;
-  if (ds->stats && ds->pass >= ds->stats_rows) reason |= 4;
-  if (reason) {
-    ds->host_reason = reason;
-    ds->status = ST_HOST;
-  }
-}
+
+
 
 // one 256-entry chunk per block iteration; its prefix is the tile's prefix combined with the
 // aggregates of the earlier chunks of the same tile
@@ -1024,17 +1049,25 @@ __global__ void k_ess_flags(int64_t lo, int64_t hi, const ColMeta* __restrict__ 
 }
 
 // the deferred column updates: new pivots (now in the pivot store) and left-most survivors
-__global__ void k_commit(RArgs a) {
-  if (a.ds->status != ST_RUN) return;
-  const PV v = pass_view(a.ds);
-  const int64_t n = a.ds->n_deferred;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t e = a.dlist[i];
-    const int32_t j = v.act[e];
-    a.meta[j].ptr = a.nxt_ptr[e];
-    a.meta[j].len = a.nxt_len[e];
-    a.meta[j].flags &= (uint8_t)~F_NEWPIV;
+__device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int in_graph);
+
+// the deferred column updates, then (last block) the end of the pass
+__global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
+  if (a.ds->status == ST_RUN) {
+    const PV v = pass_view(a.ds);
+    const int64_t n = a.ds->n_deferred;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t e = a.dlist[i];
+      const int32_t j = v.act[e];
+      a.meta[j].ptr = a.nxt_ptr[e];
+      a.meta[j].len = a.nxt_len[e];
+      a.meta[j].flags &= (uint8_t)~F_NEWPIV;
+    }
+  }
+  if (last_block(&a.ds->blocks_done) && threadIdx.x == 0) {
+    a.ds->blocks_done = 0;
+    end_of_pass(a, cond, in_graph);
   }
 }
 
@@ -1049,8 +1082,7 @@ __global__ void k_clock_start(DevState* ds) { ds->t_start = global_ns(); }
 
 // end of a pass: the next active list, convergence (no target left), the pass cap, the time
 // bound, and the graph's loop condition
-__global__ void k_end(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int in_graph) {
   DevState* ds = a.ds;
   if (ds->status == ST_RUN && ds->fault) ds->status = ST_FAULT;
   if (ds->status == ST_RUN) {
@@ -1148,10 +1180,6 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   PH_CHECK_LAUNCH();
   k_p1_tiles<<<sms * 4, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_p1_top<<<1, kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
-  k_check<<<1, 32, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
   k_mark<<<sms * 8, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
   if (ctx->opts.collect_stats) {
@@ -1170,9 +1198,7 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   k_add<<<sms * add_bps * (kThreads / kAddThreads), kAddThreads, kAddSmem, st>>>(a);
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
-  k_commit<<<sms * 2, kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
-  k_end<<<1, 32, 0, st>>>(a, cond, in_graph ? 1 : 0);
+  k_commit<<<sms * 2, kThreads, 0, st>>>(a, cond, in_graph ? 1 : 0);
   PH_CHECK_LAUNCH();
 }
 
@@ -1353,6 +1379,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   }
   // every pass proves or zeroes at least one column, so m + 1 passes always suffice
   h.max_passes = max_passes < 0 ? (int32_t)std::min<int64_t>(ctx->m + 1, INT32_MAX) : max_passes;
+  h.blocks_done = 0;
   const int64_t limit_ms = ctx->opts.timeout_ms > 0 ? ctx->opts.timeout_ms : 60000;
   h.t_limit = (unsigned long long)limit_ms * 1000000ull;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
@@ -1372,7 +1399,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     PH_CUDA(cudaStreamSynchronize(st));
     if (use_graph) {  // kernels per executed pass of the graph's loop
       const int32_t last = (h.status == ST_DONE || h.status == ST_CAPPED) ? h.passes : h.pass;
-      const int per_pass = 9 + (ctx->opts.collect_stats ? 1 : 0);
+      const int per_pass = 6 + (ctx->opts.collect_stats ? 1 : 0);
       ctx->launches += per_pass * (int64_t)(last - first_pass + 1);
     }
     if (h.status == ST_RUN) continue;
