@@ -83,6 +83,9 @@ class Complex(dict):
         return int(self["dim"].shape[0])
 
 
+VR_NV = 6  # vertex slots per simplex of a VR build (dimension <= 5), -1 padded
+
+
 def vr_build(coords: np.ndarray, max_dim: int, max_diam2: int = -1) -> Complex:
     """Vietoris-Rips filtration of int32 grid points (Sec. 2.2) with its boundary matrix."""
     L = _load()
@@ -96,7 +99,7 @@ def vr_build(coords: np.ndarray, max_dim: int, max_diam2: int = -1) -> Complex:
         m = L.orc_complex_size(h)
         nnz = L.orc_complex_nnz(h)
         K = Complex(dim=np.empty(m, np.int32), diam2=np.empty(m, np.int64),
-                    verts=np.empty((m, 4), np.int32), colptr=np.empty(m + 1, np.int64),
+                    verts=np.empty((m, VR_NV), np.int32), colptr=np.empty(m + 1, np.int64),
                     rows=np.empty(max(nnz, 1), np.int32))
         L.orc_complex_export(h, _ptr(K["dim"]), _ptr(K["diam2"]), _ptr(K["verts"]),
                              _ptr(K["colptr"]), _ptr(K["rows"]))

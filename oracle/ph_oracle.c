@@ -100,10 +100,13 @@ static void cols_free(col_t* c, int64_t m) {
 /*   faces before cofaces) is realised by sorting on (diam^2, dim, vertex tuple in lexicographic */
 /*   order); a face never has a larger diameter nor a larger dimension than its coface.        */
 /* ------------------------------------------------------------------------------------------ */
+#define ORC_VR_MAX_DIM 5 /* largest simplex dimension of a VR build (6 vertices) */
+#define ORC_VR_NV (ORC_VR_MAX_DIM + 1)
+
 typedef struct {
   int64_t diam2;
   int32_t dim;
-  int32_t v[4];
+  int32_t v[ORC_VR_NV];
 } simplex_t;
 
 static int cmp_filtration(const void* a, const void* b) {
@@ -120,7 +123,7 @@ typedef struct {
   int64_t m, nnz;
   int32_t* dim;
   int64_t* diam2;
-  int32_t* verts; /* m x 4, -1 beyond the simplex's dim */
+  int32_t* verts; /* m x ORC_VR_NV, -1 beyond the simplex's dim */
   int64_t* colptr;
   int32_t* rows;
 } orc_complex;
@@ -154,12 +157,13 @@ static int64_t sqdist(const int32_t* coords, int D, int a, int b) {
 }
 
 /* Build the VR filtration of the n points `coords` (int32 grid units, row-major n x D) up to
- * dimension max_dim (<= 3). Simplices with squared diameter above max_diam2 are dropped when
+ * dimension max_dim (<= 5). Simplices with squared diameter above max_diam2 are dropped when
  * max_diam2 >= 0. Returns a heap object released by orc_complex_free. */
 int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, int64_t max_diam2,
                  orc_complex** out) {
-  if (!coords || n <= 0 || D <= 0 || max_dim < 0 || max_dim > 3 || !out) return ORC_ERR_INVALID;
-  /* count candidates */
+  if (!coords || n <= 0 || D <= 0 || max_dim < 0 || max_dim > ORC_VR_MAX_DIM || !out)
+    return ORC_ERR_INVALID;
+  /* count candidates: C(n, d + 1) for d = 0..max_dim */
   int64_t cap = 0, binom = 1;
   for (int d = 0; d <= max_dim; d++) {
     binom = binom * (n - d) / (d + 1);
@@ -169,48 +173,32 @@ int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, i
   simplex_t* S = (simplex_t*)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(simplex_t));
   if (!S) return ORC_ERR_ALLOC;
   int64_t m = 0;
-  /* nested-loop enumeration of all k-subsets, each with its maximum pairwise squared distance */
-  for (int a = 0; a < n; a++) {
-    simplex_t s = {0, 0, {a, -1, -1, -1}};
-    S[m++] = s;
-  }
-  if (max_dim >= 1)
-    for (int a = 0; a < n; a++)
-      for (int b = a + 1; b < n; b++) {
-        int64_t d2 = sqdist(coords, D, a, b);
-        if (max_diam2 >= 0 && d2 > max_diam2) continue;
-        simplex_t s = {d2, 1, {a, b, -1, -1}};
+  /* every k-subset of the points in lexicographic order (an odometer over ascending tuples),
+   * each with its largest pairwise squared distance (the VR diameter, Sec. 2.2) */
+  for (int k = 1; k <= max_dim + 1 && k <= n; k++) {
+    int v[ORC_VR_NV];
+    for (int i = 0; i < k; i++) v[i] = i;
+    for (;;) {
+      int64_t d2 = 0;
+      for (int p = 0; p < k; p++)
+        for (int q = p + 1; q < k; q++) {
+          int64_t t = sqdist(coords, D, v[p], v[q]);
+          if (t > d2) d2 = t;
+        }
+      if (k == 1 || max_diam2 < 0 || d2 <= max_diam2) {
+        simplex_t s;
+        s.diam2 = d2;
+        s.dim = k - 1;
+        for (int i = 0; i < ORC_VR_NV; i++) s.v[i] = i < k ? v[i] : -1;
         S[m++] = s;
       }
-  if (max_dim >= 2)
-    for (int a = 0; a < n; a++)
-      for (int b = a + 1; b < n; b++)
-        for (int c = b + 1; c < n; c++) {
-          int64_t d2 = sqdist(coords, D, a, b);
-          int64_t t = sqdist(coords, D, a, c);
-          if (t > d2) d2 = t;
-          t = sqdist(coords, D, b, c);
-          if (t > d2) d2 = t;
-          if (max_diam2 >= 0 && d2 > max_diam2) continue;
-          simplex_t s = {d2, 2, {a, b, c, -1}};
-          S[m++] = s;
-        }
-  if (max_dim >= 3)
-    for (int a = 0; a < n; a++)
-      for (int b = a + 1; b < n; b++)
-        for (int c = b + 1; c < n; c++)
-          for (int e = c + 1; e < n; e++) {
-            int v[4] = {a, b, c, e};
-            int64_t d2 = 0;
-            for (int p = 0; p < 4; p++)
-              for (int q = p + 1; q < 4; q++) {
-                int64_t t = sqdist(coords, D, v[p], v[q]);
-                if (t > d2) d2 = t;
-              }
-            if (max_diam2 >= 0 && d2 > max_diam2) continue;
-            simplex_t s = {d2, 3, {a, b, c, e}};
-            S[m++] = s;
-          }
+      int i = k - 1; /* advance: last position that can still grow */
+      while (i >= 0 && v[i] == n - k + i) i--;
+      if (i < 0) break;
+      v[i]++;
+      for (int j = i + 1; j < k; j++) v[j] = v[j - 1] + 1;
+    }
+  }
   qsort(S, (size_t)m, sizeof(simplex_t), cmp_filtration);
 
   orc_complex* K = (orc_complex*)calloc(1, sizeof(orc_complex));
@@ -218,7 +206,7 @@ int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, i
   K->m = m;
   K->dim = (int32_t*)malloc((size_t)m * sizeof(int32_t));
   K->diam2 = (int64_t*)malloc((size_t)m * sizeof(int64_t));
-  K->verts = (int32_t*)malloc((size_t)m * 4 * sizeof(int32_t));
+  K->verts = (int32_t*)malloc((size_t)m * ORC_VR_NV * sizeof(int32_t));
   K->colptr = (int64_t*)malloc((size_t)(m + 1) * sizeof(int64_t));
   int64_t nnz = 0;
   for (int64_t j = 0; j < m; j++) nnz += S[j].dim > 0 ? S[j].dim + 1 : 0;
@@ -228,12 +216,12 @@ int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, i
   for (int64_t j = 0; j < m; j++) {
     K->dim[j] = S[j].dim;
     K->diam2[j] = S[j].diam2;
-    for (int k = 0; k < 4; k++) K->verts[j * 4 + k] = S[j].v[k];
+    for (int k = 0; k < ORC_VR_NV; k++) K->verts[j * ORC_VR_NV + k] = S[j].v[k];
   }
 
   /* per dimension: global indices sorted by vertex tuple, for face lookup */
-  int64_t* bydim[4] = {0, 0, 0, 0};
-  int64_t cnt[4] = {0, 0, 0, 0};
+  int64_t* bydim[ORC_VR_NV] = {0};
+  int64_t cnt[ORC_VR_NV] = {0};
   for (int64_t j = 0; j < m; j++) cnt[S[j].dim]++;
   for (int d = 0; d <= max_dim; d++) {
     bydim[d] = (int64_t*)malloc((size_t)(cnt[d] > 0 ? cnt[d] : 1) * sizeof(int64_t));
@@ -253,7 +241,7 @@ int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, i
     K->colptr[j] = pos;
     int d = S[j].dim;
     if (d == 0) continue;
-    int32_t face[4];
+    int32_t face[ORC_VR_NV];
     int64_t start = pos;
     for (int drop = 0; drop <= d; drop++) {
       int k = 0;
@@ -267,7 +255,7 @@ int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, i
       if (!hit) return ORC_ERR_INVALID; /* a face is missing: cannot happen for VR */
       K->rows[pos++] = (int32_t)*hit;
     }
-    /* ascending row order (insertion sort of d+1 <= 4 entries) */
+    /* ascending row order (insertion sort of d+1 <= 6 entries) */
     for (int64_t a = start + 1; a < pos; a++) {
       int32_t x = K->rows[a];
       int64_t b = a - 1;
@@ -292,7 +280,7 @@ void orc_complex_export(const orc_complex* K, int32_t* dim, int64_t* diam2, int3
                         int64_t* colptr, int32_t* rows) {
   if (dim) memcpy(dim, K->dim, (size_t)K->m * sizeof(int32_t));
   if (diam2) memcpy(diam2, K->diam2, (size_t)K->m * sizeof(int64_t));
-  if (verts) memcpy(verts, K->verts, (size_t)K->m * 4 * sizeof(int32_t));
+  if (verts) memcpy(verts, K->verts, (size_t)K->m * ORC_VR_NV * sizeof(int32_t));
   if (colptr) memcpy(colptr, K->colptr, (size_t)(K->m + 1) * sizeof(int64_t));
   if (rows) memcpy(rows, K->rows, (size_t)K->nnz * sizeof(int32_t));
 }

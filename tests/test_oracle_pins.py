@@ -63,7 +63,8 @@ def test_betti_of_triangulations(orc, name, order_seed):
         assert _essential_per_dim(orc, K, low) == expect
 
 
-@pytest.mark.parametrize("n,k", [(6, 1), (7, 2), (9, 2), (8, 3), (40, 2)])
+@pytest.mark.parametrize("n,k", [(6, 1), (7, 2), (9, 2), (8, 3), (40, 2), (9, 4), (10, 5),
+                                 (15, 5)])
 def test_complete_skeleton_closed_form(orc, n, k):
     # k-skeleton of the (n-1)-simplex: b_0 = 1, b_k = C(n-1, k+1), all others 0
     x = pc.random_cloud(n, 3, seed=n + k)
@@ -183,7 +184,8 @@ def test_essential_estimate_exact_at_convergence(orc):
 
 
 def test_vr_filtration_properties(orc):
-    for (n, D, k, cut) in [(9, 2, 2, -1), (8, 5, 3, -1), (12, 3, 3, None), (10, 2, 2, None)]:
+    for (n, D, k, cut) in [(9, 2, 2, -1), (8, 5, 3, -1), (12, 3, 3, None), (10, 2, 2, None),
+                           (9, 3, 5, -1), (10, 4, 4, None), (11, 3, 5, None)]:
         x = pc.random_cloud(n, D, seed=n * 10 + D)
         if cut is None:
             d2 = ((x[:, None, :].astype(np.int64) - x[None, :, :]) ** 2).sum(-1)
