@@ -140,10 +140,11 @@ void ph_destroy(ph_ctx* ctx);
  *                 n_points.
  *   n_points      total number of points N (rows of coords).
  *   D             coordinate dimension, 1..16.
- *   max_dim       largest simplex dimension, 1..3.
+ *   max_dim       largest simplex dimension, 1..5 (above 3, at most 254 points per cloud).
  *   max_diam2     simplices with squared diameter above this are left out; < 0 keeps all.
  *   m_out         host, optional: total number of simplices over all clouds.
- * Limits: 1..65535 points per cloud; at most 2^31 - 1 simplices in total.
+ * Limits: 1..4094 points per cloud up to dimension 3 (1..254 above); at most 65535 clouds and
+ * 2^31 - 1 candidate simplices in total.
  * Replaces any filtration the context held. Synchronises the stream. */
 int ph_build_filtration(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets,
                         int32_t n_clouds, int64_t n_points, int32_t D, int32_t max_dim,
@@ -223,7 +224,7 @@ int ph_get_essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* in_e, int64_t
 
 /* Inspection of the filtration of cloud `cloud` in filtration order, for testing the build
  * against an independent implementation. Host buffers of `count` entries (any may be NULL):
- *   dim int32; diam2 int64; verts int32 [count][4] (-1 padded); beta int32 (Definition 4, as
+ *   dim int32; diam2 int64; verts int32 [count][6] (-1 padded); beta int32 (Definition 4, as
  *   a filtration index, -1 = none); low int32 (current low, filtration index, -1 = zero).
  * *count receives the number of simplices of the cloud; with dim == NULL nothing else is
  * copied. Synchronises the stream. */

@@ -220,7 +220,7 @@ __global__ void k_inspect(int64_t lo, int64_t hi, const int32_t* __restrict__ se
                           const int64_t* __restrict__ d2tab, const uint64_t* __restrict__ verts,
                           const int32_t* __restrict__ beta, const int32_t* __restrict__ low,
                           int32_t* o_dim, int64_t* o_d2, int32_t* o_v, int32_t* o_beta,
-                          int32_t* o_low, int64_t n, int32_t* bad) {
+                          int32_t* o_low, int64_t n, int vbits, int32_t* bad) {
   for (int64_t x = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < hi;
        x += (int64_t)gridDim.x * blockDim.x) {
     int64_t g = gidx[x];
@@ -232,10 +232,8 @@ __global__ void k_inspect(int64_t lo, int64_t hi, const int32_t* __restrict__ se
     o_dim[g] = d;
     o_d2[g] = diam2_of(key, d2tab, (int32_t)x);
     uint64_t p = verts[x];
-    for (int q = 0; q < 4; q++) {
-      int v = (int)((p >> (36 - 12 * q)) & 0xfffu);
-      o_v[4 * g + q] = (p == ~0ull || q > d) ? -1 : v;
-    }
+    for (int q = 0; q < kVrSlots; q++)
+      o_v[kVrSlots * g + q] = (p == ~0ull || q > d) ? -1 : packed_vert_at(p, q, vbits);
     o_beta[g] = beta[x] >= 0 ? (int32_t)gidx[beta[x]] : -1;
     o_low[g] = low[x] >= 0 ? (int32_t)gidx[low[x]] : -1;
   }
@@ -475,7 +473,7 @@ int ph_get_filtration(ph_ctx* ctx, int32_t cloud, int32_t* dim, int64_t* diam2, 
   if (!dim) return PH_OK;
   int32_t* o_dim = ph::alloc_n<int32_t>(ctx, n);
   int64_t* o_d2 = ph::alloc_n<int64_t>(ctx, n);
-  int32_t* o_v = ph::alloc_n<int32_t>(ctx, 4 * n);
+  int32_t* o_v = ph::alloc_n<int32_t>(ctx, ph::kVrSlots * n);
   int32_t* o_beta = ph::alloc_n<int32_t>(ctx, n);
   int32_t* o_low = ph::alloc_n<int32_t>(ctx, n);
   int32_t* d_bad = ph::alloc_n<int32_t>(ctx, 1);
@@ -485,14 +483,14 @@ int ph_get_filtration(ph_ctx* ctx, int32_t cloud, int32_t* dim, int64_t* diam2, 
     if (hi <= lo) continue;
     ph::k_inspect<<<ph::grid_for(ctx, hi - lo, ph::kThreads), ph::kThreads, 0, ctx->stream>>>(
         lo, hi, ctx->seg, nc, ctx->gidx, ctx->key, ctx->d2tab, ctx->verts, ctx->beta, ctx->low,
-        o_dim, o_d2, o_v, o_beta, o_low, n, d_bad);
+        o_dim, o_d2, o_v, o_beta, o_low, n, ctx->vbits, d_bad);
     PH_CHECK_LAUNCH();
   }
   int32_t bad = 0;
   PH_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   copy_out(ctx, dim, o_dim, n * 4, 0);
   copy_out(ctx, diam2, o_d2, n * 8, 0);
-  copy_out(ctx, verts, o_v, n * 16, 0);
+  copy_out(ctx, verts, o_v, n * 4 * ph::kVrSlots, 0);
   copy_out(ctx, beta, o_beta, n * 4, 0);
   copy_out(ctx, low, o_low, n * 4, 0);
   PH_CUDA(cudaStreamSynchronize(ctx->stream));

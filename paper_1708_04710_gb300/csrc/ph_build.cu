@@ -14,30 +14,26 @@
 
 namespace ph {
 
-constexpr unsigned kNoVert = (1u << kVertBits) - 1u;  // padding of unused vertex slots
-
-__host__ __device__ __forceinline__ uint64_t pack_simplex(uint32_t cloud, int k, const int* v) {
+// cloud in the top 16 bits, then 48 / vbits vertex slots of vbits bits (unused: all ones)
+__host__ __device__ __forceinline__ uint64_t pack_simplex(uint32_t cloud, int k, const int* v,
+                                                          int vbits) {
   uint64_t p = (uint64_t)cloud << 48;
-  for (int i = 0; i < 4; i++) {
-    uint64_t x = i < k ? (uint64_t)v[i] : (uint64_t)kNoVert;
-    p |= x << (36 - 12 * i);
+  const int slots = 48 / vbits;
+  const uint64_t none = (1ull << vbits) - 1ull;
+  for (int i = 0; i < slots; i++) {
+    uint64_t x = i < k ? (uint64_t)v[i] : none;
+    p |= x << (48 - vbits * (i + 1));
   }
   return p;
 }
 __device__ __forceinline__ uint32_t packed_cloud(uint64_t p) { return (uint32_t)(p >> 48); }
-__device__ __forceinline__ int packed_vert(uint64_t p, int i) {
-  return (int)((p >> (36 - 12 * i)) & kNoVert);
-}
 
+// C(n, k) for the small k of a VR build (k <= 6); exact in int64 for n < 2^12
 __host__ __device__ __forceinline__ int64_t binom_small(int64_t n, int k) {
-  if (n < k || n < 0) return 0;
-  switch (k) {
-    case 0: return 1;
-    case 1: return n;
-    case 2: return n * (n - 1) / 2;
-    case 3: return n * (n - 1) / 2 * (n - 2) / 3;
-    default: return n * (n - 1) / 2 * (n - 2) / 3 * (n - 3) / 4;
-  }
+  if (n < k || n < 0 || k < 0) return 0;
+  int64_t r = 1;
+  for (int i = 0; i < k; i++) r = r * (n - i) / (i + 1);  // each prefix is a binomial
+  return r;
 }
 
 // k-subset of [n] with lexicographic rank r (0-based). Uses the complement map
@@ -45,7 +41,7 @@ __host__ __device__ __forceinline__ int64_t binom_small(int64_t n, int k) {
 // subset's rank is sum_i C(u_i, i+1) and can be peeled off greedily.
 __device__ __forceinline__ void lex_unrank(int64_t r, int n, int k, int* v) {
   int64_t R = binom_small(n, k) - 1 - r;
-  int u[4];
+  int u[kVrSlots];
   int hi = n - 1;
   for (int i = k - 1; i >= 0; i--) {
     int lo = i, h = hi;
@@ -79,7 +75,12 @@ struct CloudTabs {
   const int64_t* pt_off;  // [nc+1] point offsets
   const int64_t* mo;      // [nc+1] offsets of the n_c x n_c tables
   int nc;
+  int vbits;              // bits per packed vertex
 };
+
+__device__ __forceinline__ int packed_vert(const CloudTabs& ct, uint64_t p, int i) {
+  return packed_vert_at(p, i, ct.vbits);
+}
 
 // ------------------------------------------------------------------------------------------
 __global__ void k_check_coords(const int32_t* __restrict__ x, int64_t n, int32_t* bad) {
@@ -138,7 +139,7 @@ __global__ void k_edge_cand(CloudTabs ct, const int64_t* __restrict__ cand, int6
     int64_t e = d2[ct.mo[c] + (int64_t)v[0] * n + v[1]];
     bool keep = max_d2 < 0 || e <= max_d2;
     keys[t] = keep ? (uint64_t)e : sent;
-    vals[t] = pack_simplex((uint32_t)c, 2, v);
+    vals[t] = pack_simplex((uint32_t)c, 2, v, ct.vbits);
     count_kept(count_per_cloud, c, keep);
   }
 }
@@ -158,14 +159,14 @@ __global__ void k_edge_newflag(const uint64_t* __restrict__ vals, int64_t E, Clo
     uint64_t p = vals[i];
     int c = (int)packed_cloud(p);
     int n = (int)(ct.pt_off[c + 1] - ct.pt_off[c]);
-    int64_t e = d2[ct.mo[c] + (int64_t)packed_vert(p, 0) * n + packed_vert(p, 1)];
+    int64_t e = d2[ct.mo[c] + (int64_t)packed_vert(ct, p, 0) * n + packed_vert(ct, p, 1)];
     ed2[i] = e;
     int64_t f = 1;
     if (i > 0) {
       uint64_t q = vals[i - 1];
       int cq = (int)packed_cloud(q);
       if (cq == c) {
-        int64_t eq = d2[ct.mo[c] + (int64_t)packed_vert(q, 0) * n + packed_vert(q, 1)];
+        int64_t eq = d2[ct.mo[c] + (int64_t)packed_vert(ct, q, 0) * n + packed_vert(ct, q, 1)];
         f = (eq != e);
       }
     }
@@ -190,7 +191,7 @@ __global__ void k_edge_finish(const uint64_t* __restrict__ vals, int64_t E, Clou
     uint64_t p = vals[i];
     int c = (int)packed_cloud(p);
     int n = (int)(ct.pt_off[c + 1] - ct.pt_off[c]);
-    int a = packed_vert(p, 0), b = packed_vert(p, 1);
+    int a = packed_vert(ct, p, 0), b = packed_vert(ct, p, 1);
     int32_t rank = (int32_t)(excl[i] + flag[i] - 1);
     if (flag[i]) d2tab[rank] = ed2[i];
     int64_t id = id0 + i;
@@ -209,7 +210,7 @@ __global__ void k_edge_finish(const uint64_t* __restrict__ vals, int64_t E, Clou
   }
 }
 
-// candidates of dimension k-1 (k vertices, k = 3 or 4): key = largest edge rank
+// candidates of dimension k-1 (k vertices, 3 <= k <= 6): key = largest edge rank
 __global__ void k_simplex_cand(CloudTabs ct, const int64_t* __restrict__ cand, int64_t ncand,
                                int k, const int32_t* __restrict__ erank, uint64_t sent,
                                uint64_t* keys, uint64_t* vals, int64_t* count_per_cloud) {
@@ -217,7 +218,7 @@ __global__ void k_simplex_cand(CloudTabs ct, const int64_t* __restrict__ cand, i
        t += (int64_t)gridDim.x * blockDim.x) {
     int c = find_cloud(cand, ct.nc, t);
     int n = (int)(ct.pt_off[c + 1] - ct.pt_off[c]);
-    int v[4];
+    int v[kVrSlots];
     lex_unrank(t - cand[c], n, k, v);
     const int32_t* er = erank + ct.mo[c];
     int32_t mx = -1;
@@ -229,7 +230,7 @@ __global__ void k_simplex_cand(CloudTabs ct, const int64_t* __restrict__ cand, i
         mx = r > mx ? r : mx;
       }
     keys[t] = keep ? (uint64_t)mx : sent;
-    vals[t] = pack_simplex((uint32_t)c, k, v);
+    vals[t] = pack_simplex((uint32_t)c, k, v, ct.vbits);
     count_kept(count_per_cloud, c, keep);
   }
 }
@@ -255,7 +256,7 @@ __global__ void k_tri_finish(const uint64_t* __restrict__ keys, const uint64_t* 
     uint64_t p = vals[i];
     int c = (int)packed_cloud(p);
     int n = (int)(ct.pt_off[c + 1] - ct.pt_off[c]);
-    int v[3] = {packed_vert(p, 0), packed_vert(p, 1), packed_vert(p, 2)};
+    int v[3] = {packed_vert(ct, p, 0), packed_vert(ct, p, 1), packed_vert(ct, p, 2)};
     const int32_t* e = eid + ct.mo[c];
     int32_t r[3] = {e[(int64_t)v[1] * n + v[2]], e[(int64_t)v[0] * n + v[2]],
                     e[(int64_t)v[0] * n + v[1]]};
@@ -270,30 +271,36 @@ __global__ void k_tri_finish(const uint64_t* __restrict__ keys, const uint64_t* 
   }
 }
 
-__global__ void k_tet_finish(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals,
-                             int64_t Q, CloudTabs ct, const int32_t* __restrict__ tid_tab,
-                             const int64_t* __restrict__ tri_lex_off, int64_t id0, IdOut o,
-                             int64_t rowbase) {
+// simplices of k >= 4 vertices (dimension >= 3): faces are the (k-1)-subsets, found by their
+// lexicographic rank in the table the previous dimension filled; this dimension fills its own
+// table when a higher one follows
+__global__ void k_high_finish(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                              int64_t Q, int k, CloudTabs ct, const int32_t* __restrict__ face_tab,
+                              const int64_t* __restrict__ face_lex_off, int32_t* self_tab,
+                              const int64_t* __restrict__ self_lex_off, int64_t id0, IdOut o,
+                              int64_t rowbase) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t p = vals[i];
     int c = (int)packed_cloud(p);
     int n = (int)(ct.pt_off[c + 1] - ct.pt_off[c]);
-    int v[4] = {packed_vert(p, 0), packed_vert(p, 1), packed_vert(p, 2), packed_vert(p, 3)};
-    int32_t r[4];
-    for (int drop = 0; drop < 4; drop++) {
-      int f[3], k = 0;
-      for (int q = 0; q < 4; q++)
-        if (q != drop) f[k++] = v[q];
-      r[drop] = tid_tab[tri_lex_off[c] + lex_rank(f, n, 3)];
+    int v[kVrSlots];
+    for (int q = 0; q < k; q++) v[q] = packed_vert(ct, p, q);
+    int32_t r[kVrSlots];
+    for (int drop = 0; drop < k; drop++) {
+      int f[kVrSlots], m = 0;
+      for (int q = 0; q < k; q++)
+        if (q != drop) f[m++] = v[q];
+      r[drop] = face_tab[face_lex_off[c] + lex_rank(f, n, k - 1)];
     }
-    sort_small(r, 4);
+    sort_small(r, k);
     int64_t id = id0 + i;
-    for (int q = 0; q < 4; q++) o.rows0[rowbase + 4 * i + q] = r[q];
-    o.low[id] = r[3];
-    o.seg[id] = 3 * ct.nc + c;
+    for (int q = 0; q < k; q++) o.rows0[rowbase + (int64_t)k * i + q] = r[q];
+    o.low[id] = r[k - 1];
+    o.seg[id] = (k - 1) * ct.nc + c;
     o.key[id] = (int32_t)keys[i];
     o.verts[id] = p;
+    if (self_tab) self_tab[self_lex_off[c] + lex_rank(v, n, k)] = (int32_t)id;
   }
 }
 
@@ -305,7 +312,7 @@ __global__ void k_vertex_init(CloudTabs ct, int64_t N, IdOut o) {
     o.seg[i] = c;
     o.key[i] = -1;
     o.low[i] = -1;
-    o.verts[i] = pack_simplex((uint32_t)c, 1, &v);
+    o.verts[i] = pack_simplex((uint32_t)c, 1, &v, ct.vbits);
   }
 }
 
@@ -498,7 +505,8 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   PH_REQUIRE(coords != nullptr, PH_ERR_INVALID, "coords is NULL");
   PH_REQUIRE(nc >= 1 && nc <= kMaxClouds, PH_ERR_INVALID, "n_clouds out of range");
   PH_REQUIRE(D >= 1 && D <= 16, PH_ERR_INVALID, "D must be in 1..16");
-  PH_REQUIRE(max_dim >= 1 && max_dim <= kMaxVrDim, PH_ERR_INVALID, "max_dim must be 1..3");
+  PH_REQUIRE(max_dim >= 1 && max_dim <= kMaxVrDim, PH_ERR_INVALID, "max_dim must be 1..5");
+  const int vbits = vert_bits_for(max_dim);
   std::vector<int64_t> off(nc + 1);
   if (cloud_offsets) {
     for (int c = 0; c <= nc; c++) off[c] = cloud_offsets[c];
@@ -509,39 +517,44 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   }
   PH_REQUIRE(off[0] == 0 && off[nc] == n_points, PH_ERR_INVALID,
              "cloud_offsets must start at 0 and end at n_points");
-  std::vector<int64_t> mo(nc + 1, 0), cand2(nc + 1, 0), cand3(nc + 1, 0), cand4(nc + 1, 0);
+  // per cloud: n x n table offsets and, for k = 2..max_dim+1 vertices, the candidate offsets
+  const int K = max_dim + 1;  // largest vertex count
+  std::vector<int64_t> mo(nc + 1, 0);
+  std::vector<std::vector<int64_t>> cand(kVrSlots + 1, std::vector<int64_t>(nc + 1, 0));
+  int64_t ncand_all = 0;
   for (int c = 0; c < nc; c++) {
     int64_t n = off[c + 1] - off[c];
-    PH_REQUIRE(n >= 1 && n < kMaxCloudPoints, PH_ERR_CAPACITY,
-               "each cloud needs 1..4094 points");
+    PH_REQUIRE(n >= 1 && n < (1 << vbits) - 1, PH_ERR_CAPACITY,
+               max_dim <= 3 ? "each cloud needs 1..4094 points"
+                            : "each cloud needs 1..254 points above dimension 3");
     mo[c + 1] = mo[c] + n * n;
-    cand2[c + 1] = cand2[c] + binom_small(n, 2);
-    cand3[c + 1] = cand3[c] + (max_dim >= 2 ? binom_small(n, 3) : 0);
-    cand4[c + 1] = cand4[c] + (max_dim >= 3 ? binom_small(n, 4) : 0);
+    for (int k = 2; k <= kVrSlots; k++)
+      cand[k][c + 1] = cand[k][c] + (k <= K ? binom_small(n, k) : 0);
   }
-  PH_REQUIRE(n_points + cand2[nc] + cand3[nc] + cand4[nc] < INT32_MAX, PH_ERR_CAPACITY,
+  for (int k = 2; k <= K; k++) ncand_all += cand[k][nc];
+  PH_REQUIRE(n_points + ncand_all < INT32_MAX, PH_ERR_CAPACITY,
              "more than 2^31 - 1 candidate simplices");
   ctx->n_clouds = nc;
   ctx->max_dim = max_dim;
+  ctx->vbits = vbits;
   ctx->pt_off = off;
 
-  // device copies of the small tables
-  int64_t* d_tabs = alloc_n<int64_t>(ctx, 5 * (nc + 1));
+  // device copies of the small tables: off, mo, cand[2..kVrSlots]
+  const int ntab = 2 + (kVrSlots - 1);
+  int64_t* d_tabs = alloc_n<int64_t>(ctx, ntab * (nc + 1));
   std::vector<int64_t> h_tabs;
-  for (auto* v : {&off, &mo, &cand2, &cand3, &cand4}) h_tabs.insert(h_tabs.end(), v->begin(), v->end());
+  h_tabs.insert(h_tabs.end(), off.begin(), off.end());
+  h_tabs.insert(h_tabs.end(), mo.begin(), mo.end());
+  for (int k = 2; k <= kVrSlots; k++) h_tabs.insert(h_tabs.end(), cand[k].begin(), cand[k].end());
   PH_CUDA(cudaMemcpyAsync(d_tabs, h_tabs.data(), h_tabs.size() * sizeof(int64_t),
                           cudaMemcpyHostToDevice, st));
-  CloudTabs ct{d_tabs, d_tabs + (nc + 1), nc};
-  const int64_t* d_cand2 = d_tabs + 2 * (nc + 1);
-  const int64_t* d_cand3 = d_tabs + 3 * (nc + 1);
-  const int64_t* d_cand4 = d_tabs + 4 * (nc + 1);
+  CloudTabs ct{d_tabs, d_tabs + (nc + 1), nc, vbits};
+  auto d_cand = [&](int k) -> const int64_t* { return d_tabs + (int64_t)k * (nc + 1); };
 
-  // scratch: status words [0] bad coords, [1] max d2, [2..] per-cloud counts
-  int64_t* d_misc = alloc_n<int64_t>(ctx, 2 + 3 * nc);
-  PH_CUDA(cudaMemsetAsync(d_misc, 0, (2 + 3 * nc) * sizeof(int64_t), st));
-  int64_t* cnt_e = d_misc + 2;
-  int64_t* cnt_t = cnt_e + nc;
-  int64_t* cnt_q = cnt_t + nc;
+  // scratch: status words [0] bad coords, [1] max d2, then per-cloud counts of every dimension
+  int64_t* d_misc = alloc_n<int64_t>(ctx, 2 + (int64_t)kMaxVrDim * nc);
+  PH_CUDA(cudaMemsetAsync(d_misc, 0, (2 + (int64_t)kMaxVrDim * nc) * sizeof(int64_t), st));
+  auto cnt_dim = [&](int d) { return d_misc + 2 + (int64_t)(d - 1) * nc; };  // d >= 1
   k_check_coords<<<grid_for(ctx, n_points * D, kThreads), kThreads, 0, st>>>(
       coords, n_points * D, (int32_t*)d_misc);
   PH_CHECK_LAUNCH();
@@ -567,39 +580,46 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   const int d2bits = bitlen((uint64_t)h_misc[1]) + 1;  // one extra bit for the sentinel
 
   // ---------------- edges ----------------
-  int64_t ncand_max = std::max(std::max(cand2[nc], cand3[nc]), cand4[nc]);
+  int64_t ncand_max = 0;
+  for (int k = 2; k <= K; k++) ncand_max = std::max(ncand_max, cand[k][nc]);
   uint64_t* kbuf = alloc_n<uint64_t>(ctx, ncand_max);
   uint64_t* vbuf = alloc_n<uint64_t>(ctx, ncand_max);
   uint64_t* ktmp = alloc_n<uint64_t>(ctx, ncand_max);
   uint64_t* vtmp = alloc_n<uint64_t>(ctx, ncand_max);
   const uint64_t sent_e = (1ull << d2bits) - 1ull;
-  int64_t E = 0, T = 0, Q = 0;
-  std::vector<int64_t> h_cnt(3 * nc, 0);
-  if (cand2[nc] > 0) {
-    k_edge_cand<<<grid_for(ctx, cand2[nc], kThreads), kThreads, 0, st>>>(
-        ct, d_cand2, cand2[nc], d2, max_diam2, sent_e, kbuf, vbuf, cnt_e);
+  std::vector<int64_t> cnts(K, 0);  // simplices per dimension
+  cnts[0] = n_points;
+  std::vector<int64_t> h_cnt((int64_t)kMaxVrDim * nc, 0);  // per (dimension >= 1, cloud)
+  if (cand[2][nc] > 0) {
+    k_edge_cand<<<grid_for(ctx, cand[2][nc], kThreads), kThreads, 0, st>>>(
+        ct, d_cand(2), cand[2][nc], d2, max_diam2, sent_e, kbuf, vbuf, cnt_dim(1));
     PH_CHECK_LAUNCH();
-    radix_sort_u64(ctx, kbuf, vbuf, cand2[nc], 0, d2bits, ktmp, vtmp);
+    radix_sort_u64(ctx, kbuf, vbuf, cand[2][nc], 0, d2bits, ktmp, vtmp);
     if (nc > 1) {
-      k_rekey_cloud<<<grid_for(ctx, cand2[nc], kThreads), kThreads, 0, st>>>(
-          vbuf, kbuf, cand2[nc], sent_e, (uint64_t)nc);
+      k_rekey_cloud<<<grid_for(ctx, cand[2][nc], kThreads), kThreads, 0, st>>>(
+          vbuf, kbuf, cand[2][nc], sent_e, (uint64_t)nc);
       PH_CHECK_LAUNCH();
-      radix_sort_u64(ctx, kbuf, vbuf, cand2[nc], 0, bitlen((uint64_t)nc), ktmp, vtmp);
+      radix_sort_u64(ctx, kbuf, vbuf, cand[2][nc], 0, bitlen((uint64_t)nc), ktmp, vtmp);
     }
   }
-  PH_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt_e, nc * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  PH_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt_dim(1), nc * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          st));
   PH_CUDA(cudaStreamSynchronize(st));
-  for (int c = 0; c < nc; c++) E += h_cnt[c];
+  for (int c = 0; c < nc; c++) cnts[1] += h_cnt[c];
+  const int64_t E = cnts[1];
 
   // sizes known for dims 0, 1; ids and initial storage for those two now, higher dims after
   // their candidate counts are known. Provisional allocation uses candidate counts as bounds.
   const int64_t N = n_points;
-  int64_t m_bound = N + E + cand3[nc] + cand4[nc];
+  int64_t m_bound = N + E, nnz_bound = 2 * E;
+  for (int k = 3; k <= K; k++) {
+    m_bound += cand[k][nc];
+    nnz_bound += (int64_t)k * cand[k][nc];
+  }
   ctx->seg = alloc_n<int32_t>(ctx, m_bound);
   ctx->key = alloc_n<int32_t>(ctx, m_bound);
   ctx->low = alloc_n<int32_t>(ctx, m_bound);
   ctx->verts = alloc_n<uint64_t>(ctx, m_bound);
-  int64_t nnz_bound = 2 * E + 3 * cand3[nc] + 4 * cand4[nc];
   ctx->rows0 = alloc_n<int32_t>(ctx, nnz_bound);
   IdOut o{ctx->seg, ctx->key, ctx->low, ctx->verts, ctx->rows0};
 
@@ -629,50 +649,52 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   ctx->n_d2 = n_d2;
   const int rbits = bitlen((uint64_t)n_d2);  // keys 0..n_d2-1, sentinel n_d2
 
-  // ---------------- triangles ----------------
-  int32_t* tid_tab = nullptr;
-  int64_t* d_trilex = nullptr;
-  if (max_dim >= 3) {
-    tid_tab = alloc_n<int32_t>(ctx, cand3[nc]);
-    PH_CUDA(cudaMemsetAsync(tid_tab, 0xff, std::max<int64_t>(cand3[nc], 1) * sizeof(int32_t), st));
-    d_trilex = const_cast<int64_t*>(d_cand3);
-  }
-  if (max_dim >= 2 && cand3[nc] > 0) {
-    k_simplex_cand<<<grid_for(ctx, cand3[nc], kThreads), kThreads, 0, st>>>(
-        ct, d_cand3, cand3[nc], 3, erank, (uint64_t)n_d2, kbuf, vbuf, cnt_t);
-    PH_CHECK_LAUNCH();
-    radix_sort_u64(ctx, kbuf, vbuf, cand3[nc], 0, rbits, ktmp, vtmp);
-    PH_CUDA(cudaMemcpyAsync(h_cnt.data() + nc, cnt_t, nc * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, st));
-    PH_CUDA(cudaStreamSynchronize(st));
-    for (int c = 0; c < nc; c++) T += h_cnt[nc + c];
-    if (T > 0) {
-      k_tri_finish<<<grid_for(ctx, T, kThreads), kThreads, 0, st>>>(
-          kbuf, vbuf, T, ct, eid, N + E, o, 2 * E, tid_tab, d_trilex);
-      PH_CHECK_LAUNCH();
+  // ---------------- dimensions 2..max_dim ----------------
+  // id of each simplex by the lexicographic rank of its vertex set, for the next dimension's
+  // faces (edges use the n x n table eid instead)
+  std::vector<int32_t*> lex_tab(kVrSlots + 1, nullptr);
+  int64_t id0 = N + E, rowbase = 2 * E;
+  for (int k = 3; k <= K; k++) {
+    const int d = k - 1;
+    if (k < K) {  // the next dimension looks its faces up here
+      lex_tab[k] = alloc_n<int32_t>(ctx, std::max<int64_t>(cand[k][nc], 1));
+      PH_CUDA(cudaMemsetAsync(lex_tab[k], 0xff,
+                              std::max<int64_t>(cand[k][nc], 1) * sizeof(int32_t), st));
     }
-  }
-  // ---------------- tetrahedra ----------------
-  if (max_dim >= 3 && cand4[nc] > 0) {
-    k_simplex_cand<<<grid_for(ctx, cand4[nc], kThreads), kThreads, 0, st>>>(
-        ct, d_cand4, cand4[nc], 4, erank, (uint64_t)n_d2, kbuf, vbuf, cnt_q);
-    PH_CHECK_LAUNCH();
-    radix_sort_u64(ctx, kbuf, vbuf, cand4[nc], 0, rbits, ktmp, vtmp);
-    PH_CUDA(cudaMemcpyAsync(h_cnt.data() + 2 * nc, cnt_q, nc * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, st));
-    PH_CUDA(cudaStreamSynchronize(st));
-    for (int c = 0; c < nc; c++) Q += h_cnt[2 * nc + c];
+    int64_t Q = 0;
+    if (cand[k][nc] > 0) {
+      k_simplex_cand<<<grid_for(ctx, cand[k][nc], kThreads), kThreads, 0, st>>>(
+          ct, d_cand(k), cand[k][nc], k, erank, (uint64_t)n_d2, kbuf, vbuf, cnt_dim(d));
+      PH_CHECK_LAUNCH();
+      radix_sort_u64(ctx, kbuf, vbuf, cand[k][nc], 0, rbits, ktmp, vtmp);
+      PH_CUDA(cudaMemcpyAsync(h_cnt.data() + (int64_t)(d - 1) * nc, cnt_dim(d),
+                              nc * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      PH_CUDA(cudaStreamSynchronize(st));
+      for (int c = 0; c < nc; c++) Q += h_cnt[(int64_t)(d - 1) * nc + c];
+    }
     if (Q > 0) {
-      k_tet_finish<<<grid_for(ctx, Q, kThreads), kThreads, 0, st>>>(
-          kbuf, vbuf, Q, ct, tid_tab, d_trilex, N + E + T, o, 2 * E + 3 * T);
+      if (k == 3) {
+        k_tri_finish<<<grid_for(ctx, Q, kThreads), kThreads, 0, st>>>(
+            kbuf, vbuf, Q, ct, eid, id0, o, rowbase, lex_tab[3], d_cand(3));
+      } else {
+        k_high_finish<<<grid_for(ctx, Q, kThreads), kThreads, 0, st>>>(
+            kbuf, vbuf, Q, k, ct, lex_tab[k - 1], d_cand(k - 1), lex_tab[k], d_cand(k), id0, o,
+            rowbase);
+      }
       PH_CHECK_LAUNCH();
     }
+    cnts[d] = Q;
+    id0 += Q;
+    rowbase += (int64_t)k * Q;
   }
 
   // ---------------- layout ----------------
-  ctx->m = N + E + T + Q;
-  ctx->nnz = 2 * E + 3 * T + 4 * Q;
-  int64_t cnts[4] = {N, E, T, Q};
+  ctx->m = 0;
+  ctx->nnz = 0;
+  for (int d = 0; d <= max_dim; d++) {
+    ctx->m += cnts[d];
+    if (d > 0) ctx->nnz += (int64_t)(d + 1) * cnts[d];
+  }
   ctx->dimoff[0] = 0;
   for (int d = 0; d <= max_dim; d++) ctx->dimoff[d + 1] = ctx->dimoff[d] + cnts[d];
   ctx->seg_start.assign((max_dim + 1) * nc + 1, 0);
@@ -680,7 +702,7 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   for (int d = 0; d <= max_dim; d++)
     for (int c = 0; c < nc; c++) {
       ctx->seg_start[d * nc + c] = pos;
-      pos += d == 0 ? off[c + 1] - off[c] : h_cnt[(d - 1) * nc + c];
+      pos += d == 0 ? off[c + 1] - off[c] : h_cnt[(int64_t)(d - 1) * nc + c];
     }
   ctx->seg_start[(max_dim + 1) * nc] = pos;
   finish_layout(ctx);
@@ -700,7 +722,8 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   ctx->dfree(d2);
   ctx->dfree(eid);
   ctx->dfree(erank);
-  if (tid_tab) ctx->dfree(tid_tab);
+  for (int32_t* t : lex_tab)
+    if (t) ctx->dfree(t);
   ctx->dfree(d_misc);
   // d_tabs holds pt_off, needed by extraction: keep it alive as ctx->... (freed with ctx)
 }

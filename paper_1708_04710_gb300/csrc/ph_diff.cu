@@ -23,6 +23,7 @@ struct DiagLayout {
   int64_t rowbase[kMaxDim + 2];
   int maxd;
   int nc;
+  int vbits;  // bits per packed vertex of the build
 };
 
 __global__ void k_to_grid(const float* __restrict__ x, int64_t n, int32_t* g, int32_t* bad) {
@@ -52,8 +53,8 @@ __device__ __forceinline__ void realising_edge(const DiagLayout& L, const int32_
   }
   const uint64_t v = verts[x];
   const int64_t base = pt_off[(int)(v >> 48)];
-  p = base + (int64_t)((v >> 36) & 0xfffu);
-  q = base + (int64_t)((v >> 24) & 0xfffu);
+  p = base + (int64_t)packed_vert_at(v, 0, L.vbits);
+  q = base + (int64_t)packed_vert_at(v, 1, L.vbits);
 }
 
 __device__ __forceinline__ float edge_len(const float* __restrict__ x, int D, int64_t p,
@@ -154,6 +155,7 @@ __global__ void k_diag_bwd(DiagLayout L, int dd, int64_t lo, int64_t hi,
 static DiagLayout layout_of(ph_ctx* ctx) {
   DiagLayout L{};
   L.maxd = ctx->max_dim;
+  L.vbits = ctx->vbits;
   L.nc = ctx->n_clouds;
   int64_t rb = 0;
   for (int d = 0; d <= ctx->max_dim + 1; d++) L.dimoff[d] = ctx->dimoff[d];

@@ -18,9 +18,20 @@
 namespace ph {
 
 constexpr int kMaxDim = 8;  // largest simplex dimension of a loaded complex
-constexpr int kMaxVrDim = 3;
-constexpr int kVertBits = 12;  // packed vertex tuples: 4 x 12 bits + 16-bit cloud
+constexpr int kMaxVrDim = 5;   // largest simplex dimension of a VR build (6 vertices)
+constexpr int kVrSlots = kMaxVrDim + 1;
+// packed vertex tuples: a 16-bit cloud above 48 bits of vertex slots, 4 x 12 bits when the
+// build stops at dimension 3, 6 x 8 bits above (an all-ones slot marks no vertex)
+constexpr int kVertBits = 12;
+constexpr int kVertBitsHigh = 8;
 constexpr int kMaxCloudPoints = 1 << kVertBits;
+
+__host__ __device__ __forceinline__ int vert_bits_for(int max_dim) {
+  return max_dim <= 3 ? kVertBits : kVertBitsHigh;
+}
+__host__ __device__ __forceinline__ int packed_vert_at(uint64_t p, int i, int vbits) {
+  return (int)((p >> (48 - vbits * (i + 1))) & ((1u << vbits) - 1u));
+}
 constexpr int kMaxClouds = 65535;
 
 // column flags
@@ -135,7 +146,8 @@ struct ph_ctx {
   int32_t* beta = nullptr;    // per id: beta, as an id (-1 none)
   int32_t* key = nullptr;     // per id: dense squared-diameter rank (-1: vertex/loaded)
   int64_t* gidx = nullptr;    // per id: filtration index within its cloud
-  uint64_t* verts = nullptr;  // per id: packed (cloud, v0..v3)
+  uint64_t* verts = nullptr;  // per id: packed (cloud, vertex slots of vbits bits)
+  int vbits = ph::kVertBits;  // bits per packed vertex of this build
   int64_t* d2tab = nullptr;   // dense rank -> squared diameter
   int64_t n_d2 = 0;
   int32_t* rows0 = nullptr;   // initial column storage (boundary matrix, CSC by id)

@@ -318,7 +318,7 @@ class Context:
                                                byref(n)))
         k = n.value
         out = dict(dim=np.empty(k, np.int32), diam2=np.empty(k, np.int64),
-                   verts=np.empty((k, 4), np.int32), beta=np.empty(k, np.int32),
+                   verts=np.empty((k, 6), np.int32), beta=np.empty(k, np.int32),
                    low=np.empty(k, np.int32))
         self._check(self.lib.ph_get_filtration(self._h, cloud, _ptr(out["dim"]),
                                                _ptr(out["diam2"]), _ptr(out["verts"]),

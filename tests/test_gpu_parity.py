@@ -116,6 +116,12 @@ CASES = [
     ("two_points", lambda: pc.random_cloud(2, 3, 8), 2, -1),
     ("three_points", lambda: pc.random_cloud(3, 3, 9), 3, -1),
     ("all_cut", lambda: pc.random_cloud(10, 3, 10), 2, 0),
+    # dimensions 4 and 5 (six vertex slots of 8 bits); 15 points up to dimension 5 is the size
+    # of the paper's ensembles (9,948 simplices)
+    ("gauss_3d_dim4", lambda: pc.random_cloud(11, 3, 31), 4, -1),
+    ("gauss_3d_dim5", lambda: pc.random_cloud(15, 3, 32), 5, -1),
+    ("gauss_4d_dim5_cut", lambda: pc.random_cloud(16, 4, 33), 5, int(2.0 * 65536 ** 2)),
+    ("lattice_dim4_ties", lambda: pc.lattice_cloud(14, 3, 34, side=3), 4, -1),
 ]
 
 
@@ -255,7 +261,10 @@ def test_invalid_arguments(ph):
     ctx = ph.Context()
     x = torch.zeros((4, 3), dtype=torch.int32, device="cuda")
     with pytest.raises(ph.PHError):
-        ctx.build_filtration(x, None, 4)  # max_dim out of range
+        ctx.build_filtration(x, None, 6)  # max_dim out of range
+    with pytest.raises(ph.PHError) as err:  # above dimension 3 a cloud holds at most 254 points
+        ctx.build_filtration(torch.zeros((255, 3), dtype=torch.int32, device="cuda"), None, 4)
+    assert err.value.code == -4
     with pytest.raises(ph.PHError):
         ctx.build_filtration(x, [0, 2, 3], 2)  # offsets must end at N
     big = torch.full((3, 2), 1 << 25, dtype=torch.int32, device="cuda")
