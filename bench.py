@@ -162,6 +162,9 @@ def main():
                     help="library default options (short profiler captures)")
     ap.add_argument("--pass-loop", default="graph", choices=["graph", "host"],
                     help="pass loop of the timed steps: one CUDA graph, or host-driven")
+    ap.add_argument("--experiment", choices=["early"],
+                    help="instead of the throughput line: early-stopping quality per iteration "
+                         "on the four 15-point ensembles (complete complex to dimension 5)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -169,6 +172,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.experiment == "early":
+        return run_early()
 
     import torch
 
@@ -349,6 +354,43 @@ def main():
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_early():
+    """Iterations of Algorithm 2 to given levels of relative l1 error of low (Eq. rel_error),
+    unreduced share and essential-estimate precision, per ensemble, for the left-most source
+    (default) and the printed rule (strict_phase2). One JSON line."""
+    import torch
+
+    from paper_1708_04710_gb300 import build as _build
+
+    _build.build()
+    import paper_1708_04710_gb300 as ph
+    from paper_1708_04710_gb300 import early
+
+    torch.cuda.set_device(0)
+    res = {}
+    for name in pc.ENSEMBLES:
+        x = torch.from_numpy(pc.ensemble15(name)).cuda()
+        res[name] = {}
+        for mode, strict in (("leftmost", False), ("strict", True)):
+            ctx = ph.Context(collect_stats=True, strict_phase2=strict)
+            ctx.build_filtration(x, None, 5)
+            pr = early.profile(ctx)
+            res[name][mode] = {
+                "m": pr["m"], "passes": pr["passes"], "ess": pr["ess"],
+                "total_adds": pr["adds"][-1], "total_xors": pr["xors"][-1],
+                "iterations_to_l1_error": early.iterations_to(
+                    pr["l1_error"], [0.1, 0.01, 0.001, 0.0001, 0.0]),
+                "iterations_to_unreduced": early.iterations_to(
+                    pr["unreduced"], [0.9, 0.5, 0.1, 0.05, 0.01]),
+                "iterations_to_precision": early.iterations_to(
+                    pr["precision"], [0.1, 0.5, 0.9, 0.95, 1.0], below=False),
+                "precision": [round(v, 4) for v in pr["precision"]],
+            }
+    print(json.dumps({"experiment": "early", "data": "synthetic",
+                      "desc": "15 points per ensemble, complete VR complex to dimension 5",
+                      "results": res}), flush=True)
 
 
 def _timed(torch, fn, reps=2):

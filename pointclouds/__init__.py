@@ -17,6 +17,12 @@ clouds stand in for them; they follow the sizes and shapes of the benchmark conf
 * ``batch512``   512 clouds, n_i uniform in {20..120}; cloud i is drawn from family i mod 3:
                  unit 2-sphere (normalised N(0, I_3)), torus (R=2, r=1), N(0, I_3).
 * ``diff256``    256 clouds of 64 points, unit 2-sphere plus N(0, 0.02^2 I_3), kept in fp32.
+* ``ensemble15`` the four ensembles of the paper's iteration experiments (Sec. 4: Gaussian
+                 points in R^3, figure-8, trefoil knot, S^2 x S^2; N = 15, complete complex up
+                 to dimension 5). The paper gives no sampling laws, so these are stand-ins:
+                 N(0, I_3); a figure-8 (lemniscate of Gerono) and a trefoil knot, each with the
+                 curve parameter uniform and N(0, 0.05^2 I_3) noise; normalised N(0, I_3) pairs
+                 in R^6 for S^2 x S^2.
 """
 from __future__ import annotations
 
@@ -25,7 +31,9 @@ import numpy as np
 GRID_SCALE = 65536  # 2^16 grid units per unit length
 BASE_SEED = 1708_04710
 
-CONFIG_IDS = {"circle40": 1, "torus400": 2, "gauss8_120": 3, "batch512": 4, "diff256": 5}
+CONFIG_IDS = {"circle40": 1, "torus400": 2, "gauss8_120": 3, "batch512": 4, "diff256": 5,
+              "gaussian15": 10, "figure8_15": 11, "trefoil15": 12, "sphere_product15": 13}
+ENSEMBLES = ("gaussian15", "figure8_15", "trefoil15", "sphere_product15")
 
 
 def to_grid(x: np.ndarray) -> np.ndarray:
@@ -123,3 +131,36 @@ def lattice_cloud(n: int, d: int, seed: int, side: int = 4) -> np.ndarray:
     """Points on a coarse integer lattice: many exactly equal squared distances (tie stress)."""
     rng = np.random.Generator(np.random.PCG64(BASE_SEED + 104729 * (seed + 1)))
     return (rng.integers(0, side, size=(n, d)) * GRID_SCALE).astype(np.int32)
+
+
+def figure8(n: int, rng: np.random.Generator, noise: float = 0.05) -> np.ndarray:
+    t = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    pts = np.stack([np.cos(t), np.sin(t) * np.cos(t), np.zeros(n)], axis=1)
+    return pts + rng.normal(0.0, noise, size=(n, 3))
+
+
+def trefoil(n: int, rng: np.random.Generator, noise: float = 0.05) -> np.ndarray:
+    t = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    pts = np.stack([np.sin(t) + 2.0 * np.sin(2.0 * t), np.cos(t) - 2.0 * np.cos(2.0 * t),
+                    -np.sin(3.0 * t)], axis=1)
+    return pts + rng.normal(0.0, noise, size=(n, 3))
+
+
+def sphere_product(n: int, rng: np.random.Generator) -> np.ndarray:
+    return np.concatenate([sphere(n, rng), sphere(n, rng)], axis=1)
+
+
+def ensemble15(name: str, sample: int = 0, n: int = 15) -> np.ndarray:
+    """One point cloud of an iteration-experiment ensemble (names in ENSEMBLES), on the grid."""
+    rng = rng_for(CONFIG_IDS[name], salt=sample)
+    if name == "gaussian15":
+        x = gaussian(n, 3, rng)
+    elif name == "figure8_15":
+        x = figure8(n, rng)
+    elif name == "trefoil15":
+        x = trefoil(n, rng)
+    elif name == "sphere_product15":
+        x = sphere_product(n, rng)
+    else:
+        raise ValueError(name)
+    return to_grid(x)
