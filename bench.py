@@ -369,13 +369,16 @@ def run_early():
     from paper_1708_04710_gb300 import early
 
     torch.cuda.set_device(0)
+    step, n_scales = pc.GRID_SCALE // 2, 10  # the paper's grid: r_T = 5 in h = 10 divisions
     res = {}
     for name in pc.ENSEMBLES:
         x = torch.from_numpy(pc.ensemble15(name)).cuda()
         res[name] = {}
-        for mode, strict in (("leftmost", False), ("strict", True)):
-            ctx = ph.Context(collect_stats=True, strict_phase2=strict)
-            ctx.build_filtration(x, None, 5)
+        for mode, strict, cor10 in (("leftmost", False, True), ("strict", True, True),
+                                    ("leftmost_no_cor10", False, False),
+                                    ("strict_no_cor10", True, False)):
+            ctx = ph.Context(collect_stats=True, strict_phase2=strict, use_cor10=cor10)
+            ctx.build_filtration_scales(x, None, 5, step, n_scales)
             pr = early.profile(ctx)
             res[name][mode] = {
                 "m": pr["m"], "passes": pr["passes"], "ess": pr["ess"],
@@ -389,7 +392,8 @@ def run_early():
                 "precision": [round(v, 4) for v in pr["precision"]],
             }
     print(json.dumps({"experiment": "early", "data": "synthetic",
-                      "desc": "15 points per ensemble, complete VR complex to dimension 5",
+                      "desc": "15 points per ensemble, VR complex to dimension 5 on the scale "
+                              "grid r_i = 0.5 i, i <= 10",
                       "results": res}), flush=True)
 
 

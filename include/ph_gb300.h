@@ -150,6 +150,18 @@ int ph_build_filtration(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud
                         int32_t n_clouds, int64_t n_points, int32_t D, int32_t max_dim,
                         int64_t max_diam2, int64_t* m_out);
 
+/* The same VR complex on a grid of scales, the setting of the paper's experiments (Sec. 4:
+ * scales r_1 < ... < r_T with uniform spacing h): a simplex enters at the first scale
+ * r_i = i * scale_step with diameter <= 2 r_i (Sec. 2.2), i = 0..n_scales, and simplices above
+ * r_T = n_scales * scale_step are left out. The order is (scale index, dimension, lexicographic
+ * vertex tuple), so simplices of one scale tie and are ordered by dimension and vertices. The
+ * squared diameters that ph_get_pairs and ph_get_essential report are then scale indices.
+ *   scale_step    grid units (1 = 2^-16), 1..2^26.   n_scales   >= 1.
+ * Other arguments and limits as ph_build_filtration. */
+int ph_build_filtration_scales(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets,
+                               int32_t n_clouds, int64_t n_points, int32_t D, int32_t max_dim,
+                               int64_t scale_step, int32_t n_scales, int64_t* m_out);
+
 /* As ph_build_filtration, from fp32 coordinates (device float [N][D], plain units): each is
  * rounded on the device to the 2^-16 grid, rint(x * 65536) with ties to even, and must be
  * finite with |x| <= 256 (PH_ERR_INVALID otherwise). The pairing is computed from the rounded

@@ -51,6 +51,8 @@ def _load():
         i32, i64 = ctypes.c_int32, ctypes.c_int64
         L.orc_vr_build.argtypes = [P, i32, i32, i32, i64, ctypes.POINTER(P)]
         L.orc_vr_build.restype = ctypes.c_int
+        L.orc_vr_build_scales.argtypes = [P, i32, i32, i32, i64, i32, ctypes.POINTER(P)]
+        L.orc_vr_build_scales.restype = ctypes.c_int
         L.orc_complex_size.argtypes = [P]
         L.orc_complex_size.restype = i64
         L.orc_complex_nnz.argtypes = [P]
@@ -86,13 +88,20 @@ class Complex(dict):
 VR_NV = 6  # vertex slots per simplex of a VR build (dimension <= 5), -1 padded
 
 
-def vr_build(coords: np.ndarray, max_dim: int, max_diam2: int = -1) -> Complex:
-    """Vietoris-Rips filtration of int32 grid points (Sec. 2.2) with its boundary matrix."""
+def vr_build(coords: np.ndarray, max_dim: int, max_diam2: int = -1, scale_step: int = 0,
+             n_scales: int = 0) -> Complex:
+    """Vietoris-Rips filtration of int32 grid points (Sec. 2.2) with its boundary matrix. With
+    scale_step > 0 the filtration values are indices on the grid of scales r_i = i * scale_step
+    (i = 0..n_scales, Sec. 4) and "diam2" holds them."""
     L = _load()
     c = np.ascontiguousarray(coords, dtype=np.int32)
     n, D = c.shape
     h = ctypes.c_void_p()
-    rc = L.orc_vr_build(_ptr(c), n, D, max_dim, int(max_diam2), ctypes.byref(h))
+    if scale_step > 0:
+        rc = L.orc_vr_build_scales(_ptr(c), n, D, max_dim, int(scale_step), int(n_scales),
+                                   ctypes.byref(h))
+    else:
+        rc = L.orc_vr_build(_ptr(c), n, D, max_dim, int(max_diam2), ctypes.byref(h))
     if rc != 0:
         raise RuntimeError(f"orc_vr_build failed: {rc}")
     try:

@@ -156,11 +156,36 @@ static int64_t sqdist(const int32_t* coords, int D, int a, int b) {
   return s;
 }
 
+/* Scale index of a squared diameter on the grid r_i = i * step (Sec. 4's grid of scales): the
+ * first i >= 0 with diameter <= 2 r_i (Sec. 2.2), found by counting up. */
+static int64_t scale_index(int64_t d2, int64_t step) {
+  int64_t i = 0;
+  while ((2 * i * step) * (2 * i * step) < d2) i++;
+  return i;
+}
+
+static int vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim,
+                    int64_t max_diam2, int64_t step, int32_t n_scales, orc_complex** out);
+
 /* Build the VR filtration of the n points `coords` (int32 grid units, row-major n x D) up to
  * dimension max_dim (<= 5). Simplices with squared diameter above max_diam2 are dropped when
  * max_diam2 >= 0. Returns a heap object released by orc_complex_free. */
 int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, int64_t max_diam2,
                  orc_complex** out) {
+  return vr_build(coords, n, D, max_dim, max_diam2, 0, 0, out);
+}
+
+/* The same on the grid of scales r_i = i * step, i = 0..n_scales: a simplex's filtration value
+ * (stored in place of its squared diameter) is the scale index of its diameter, and simplices
+ * above the last scale are dropped. */
+int orc_vr_build_scales(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim,
+                        int64_t step, int32_t n_scales, orc_complex** out) {
+  if (step <= 0 || n_scales < 1) return ORC_ERR_INVALID;
+  return vr_build(coords, n, D, max_dim, -1, step, n_scales, out);
+}
+
+static int vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim,
+                    int64_t max_diam2, int64_t step, int32_t n_scales, orc_complex** out) {
   if (!coords || n <= 0 || D <= 0 || max_dim < 0 || max_dim > ORC_VR_MAX_DIM || !out)
     return ORC_ERR_INVALID;
   /* count candidates: C(n, d + 1) for d = 0..max_dim */
@@ -185,7 +210,9 @@ int orc_vr_build(const int32_t* coords, int32_t n, int32_t D, int32_t max_dim, i
           int64_t t = sqdist(coords, D, v[p], v[q]);
           if (t > d2) d2 = t;
         }
-      if (k == 1 || max_diam2 < 0 || d2 <= max_diam2) {
+      if (step > 0) d2 = scale_index(d2, step);  /* value on the grid of scales */
+      int keep = step > 0 ? d2 <= n_scales : (max_diam2 < 0 || d2 <= max_diam2);
+      if (k == 1 || keep) {
         simplex_t s;
         s.diam2 = d2;
         s.dim = k - 1;

@@ -323,6 +323,21 @@ int ph_build_filtration(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud
   PH_API_END
 }
 
+int ph_build_filtration_scales(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets,
+                               int32_t n_clouds, int64_t n_points, int32_t D, int32_t max_dim,
+                               int64_t scale_step, int32_t n_scales, int64_t* m_out) {
+  PH_API_BEGIN
+  PH_REQUIRE(scale_step >= 1, PH_ERR_INVALID, "scale_step must be >= 1 grid unit");
+  ctx->free_all();
+  ph::build_vr(ctx, coords, cloud_offsets, n_clouds, n_points, D, max_dim, -1, scale_step,
+               n_scales);
+  ctx->built = true;
+  ctx->is_vr = true;
+  if (m_out) *m_out = ctx->m;
+  return PH_OK;
+  PH_API_END
+}
+
 int ph_load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* colptr,
                      const int32_t* rows) {
   PH_API_BEGIN

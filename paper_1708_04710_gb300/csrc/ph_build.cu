@@ -119,6 +119,23 @@ __global__ void k_pairwise(const int32_t* __restrict__ x, int D, CloudTabs ct, i
   if ((threadIdx.x & 31) == 0) atomicMax(maxd2, mx);
 }
 
+// Index of the first scale r_i = i * step with d <= 2 r_i for a squared distance d2 (Sec. 2.2:
+// a simplex is in the complex at scale r when its diameter is at most 2r), by exact integer
+// comparison: the smallest i >= 0 with d2 <= (2 i step)^2.
+__host__ __device__ __forceinline__ int64_t scale_index_of(int64_t d2, int64_t step) {
+  if (d2 <= 0) return 0;
+  int64_t i = (int64_t)ceil(sqrt((double)d2) / (2.0 * (double)step));
+  while (i > 0 && (2 * (i - 1) * step) * (2 * (i - 1) * step) >= d2) i--;
+  while ((2 * i * step) * (2 * i * step) < d2) i++;
+  return i;
+}
+
+__global__ void k_scale_index(int64_t* d2, int64_t n, int64_t step) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    d2[t] = scale_index_of(d2[t], step);
+}
+
 // count one kept candidate for cloud c with one atomic per group of lanes sharing c
 __device__ __forceinline__ void count_kept(int64_t* count_per_cloud, int c, bool keep) {
   const unsigned peers = __match_any_sync(__activemask(), keep ? c : -1);
@@ -500,7 +517,8 @@ void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* c
 }
 
 void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, int32_t nc,
-              int64_t n_points, int32_t D, int32_t max_dim, int64_t max_diam2) {
+              int64_t n_points, int32_t D, int32_t max_dim, int64_t max_diam2,
+              int64_t scale_step, int32_t n_scales) {
   cudaStream_t st = ctx->stream;
   PH_REQUIRE(coords != nullptr, PH_ERR_INVALID, "coords is NULL");
   PH_REQUIRE(nc >= 1 && nc <= kMaxClouds, PH_ERR_INVALID, "n_clouds out of range");
@@ -577,7 +595,16 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   PH_CUDA(cudaMemcpyAsync(h_misc, d_misc, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   PH_CUDA(cudaStreamSynchronize(st));
   PH_REQUIRE(h_misc[0] == 0, PH_ERR_INVALID, "coordinates must lie in [-2^24, 2^24] grid units");
-  const int d2bits = bitlen((uint64_t)h_misc[1]) + 1;  // one extra bit for the sentinel
+  int64_t maxkey = h_misc[1];
+  if (scale_step > 0) {  // filtration values on the grid of scales: d2 -> scale index
+    PH_REQUIRE(n_scales >= 1 && scale_step <= (int64_t)1 << 26, PH_ERR_INVALID,
+               "the scale grid needs n_scales >= 1 and a step of at most 2^26 grid units");
+    k_scale_index<<<grid_for(ctx, nn, kThreads), kThreads, 0, st>>>(d2, nn, scale_step);
+    PH_CHECK_LAUNCH();
+    maxkey = scale_index_of(h_misc[1], scale_step);
+    max_diam2 = n_scales;  // simplices above the largest scale are left out
+  }
+  const int d2bits = bitlen((uint64_t)maxkey) + 1;  // one extra bit for the sentinel
 
   // ---------------- edges ----------------
   int64_t ncand_max = 0;

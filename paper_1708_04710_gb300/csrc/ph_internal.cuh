@@ -282,8 +282,11 @@ __device__ __forceinline__ SegMax warp_incl_segmax(SegMax v) {
 
 // host entry points shared between translation units
 namespace ph {
+// scale_step > 0: simplices enter at the first scale r_i = i * scale_step (grid units,
+// i = 0..n_scales) with diameter <= 2 r_i, and the filtration value is i
 void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, int32_t n_clouds,
-              int64_t n_points, int32_t D, int32_t max_dim, int64_t max_diam2);
+              int64_t n_points, int32_t D, int32_t max_dim, int64_t max_diam2,
+              int64_t scale_step = 0, int32_t n_scales = 0);
 void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* colptr,
                    const int32_t* rows);
 void compute_beta(ph_ctx* ctx);

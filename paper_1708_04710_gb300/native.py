@@ -56,6 +56,9 @@ SIGNATURES = {
                                     c_int32, c_int64, POINTER(c_int64)]),
     "ph_build_filtration_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int64,
                                         c_int32, c_int32, c_int64, POINTER(c_int64)]),
+    "ph_build_filtration_scales": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int64,
+                                           c_int32, c_int32, c_int64, c_int32,
+                                           POINTER(c_int64)]),
     "ph_load_boundary": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "ph_diagram_loss": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p,
                                 POINTER(c_int64)]),
@@ -194,6 +197,26 @@ class Context:
         m = c_int64(0)
         self._check(self.lib.ph_build_filtration(self._h, _ptr(coords), _ptr(offs), nc, N, D,
                                                  max_dim, int(max_diam2), byref(m)))
+        self.n_clouds = nc
+        self.m = m.value
+        return self.m
+
+    def build_filtration_scales(self, coords, cloud_offsets=None, max_dim: int = 2,
+                                scale_step: int = 1, n_scales: int = 1) -> int:
+        """Like build_filtration on a grid of scales r_i = i * scale_step (grid units),
+        i = 0..n_scales: the filtration value of a simplex is its scale index."""
+        torch = self._torch
+        assert coords.is_cuda and coords.dtype == torch.int32 and coords.dim() == 2
+        coords = coords.contiguous()
+        self._coords = coords
+        N, D = coords.shape
+        offs = None if cloud_offsets is None else np.ascontiguousarray(
+            np.asarray(cloud_offsets, dtype=np.int64))
+        nc = 1 if offs is None else len(offs) - 1
+        m = c_int64(0)
+        self._check(self.lib.ph_build_filtration_scales(self._h, _ptr(coords), _ptr(offs), nc, N,
+                                                        D, max_dim, int(scale_step),
+                                                        int(n_scales), byref(m)))
         self.n_clouds = nc
         self.m = m.value
         return self.m

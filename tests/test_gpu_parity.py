@@ -141,6 +141,30 @@ def test_filtration_and_reduction(ph, orc, name, gen, max_dim, cut):
     _check_counters(ctx, ref)
 
 
+@pytest.mark.parametrize("name,gen,max_dim,step,n_scales", [
+    ("gaussian15_paper_grid", lambda: pc.ensemble15("gaussian15"), 5, 32768, 10),
+    ("sphere_product15_paper_grid", lambda: pc.ensemble15("sphere_product15"), 5, 32768, 10),
+    ("gauss_2d_coarse", lambda: pc.random_cloud(40, 2, 43), 2, 20000, 6),
+    ("lattice_one_scale", lambda: pc.lattice_cloud(30, 2, 44, side=4), 3, 1 << 20, 1),
+])
+def test_scale_grid_filtration_and_reduction(ph, orc, name, gen, max_dim, step, n_scales):
+    import torch
+
+    x = gen()
+    K = orc.vr_build(x, max_dim, scale_step=step, n_scales=n_scales)
+    ctx = ph.Context(collect_stats=True)
+    ctx.build_filtration_scales(torch.from_numpy(x).cuda(), None, max_dim, step, n_scales)
+    assert ctx.m == K.m
+    _check_filtration(orc, ctx, 0, K)
+    for strict, cor10 in ((False, True), (True, False)):
+        ctx2 = ph.Context(collect_stats=True, strict_phase2=strict, use_cor10=cor10)
+        ctx2.build_filtration_scales(torch.from_numpy(x).cuda(), None, max_dim, step, n_scales)
+        st = ctx2.reduce()
+        ref = _check_reduced(orc, ctx2, 0, K, strict=strict, cor10=cor10)
+        assert st["passes"] == ref.passes
+        _check_counters(ctx2, ref)
+
+
 @pytest.mark.parametrize("strict,cor10", [(True, True), (False, False), (True, False)])
 def test_modes(ph, orc, strict, cor10):
     x = pc.random_cloud(40, 3, 11)

@@ -222,6 +222,45 @@ def test_vr_filtration_properties(orc):
             assert pre.max() == len(pre) - 1
 
 
+def test_scale_grid_sublevel_sets(orc):
+    # on the grid of scales r_i = i h (Sec. 4), the complex at scale r_i is the VR complex of
+    # radius r_i (Sec. 2.2): its simplices are exactly those of squared diameter <= (2 r_i)^2,
+    # they form a prefix of the order, and within one scale the order is (dim, lex)
+    for x, k, h, T in [(pc.ensemble15("gaussian15"), 3, 32768, 10),
+                       (pc.random_cloud(12, 2, 41), 4, 20000, 6),
+                       (pc.lattice_cloud(10, 2, 42, side=3), 3, 10000, 3)]:
+        G = orc.vr_build(x, k, scale_step=h, n_scales=T)
+        E = orc.vr_build(x, k)
+        vg = {tuple(G["verts"][j, :G["dim"][j] + 1]): int(G["diam2"][j]) for j in range(G.m)}
+        for i in range(T + 1):
+            want = {tuple(E["verts"][j, :E["dim"][j] + 1]) for j in range(E.m)
+                    if E["diam2"][j] <= (2 * i * h) ** 2}
+            have = {v for v, lv in vg.items() if lv <= i}
+            assert have == want
+            pre = np.nonzero(G["diam2"] <= i)[0]
+            assert len(pre) == 0 or pre.max() == len(pre) - 1
+        keys = [(int(G["diam2"][j]), int(G["dim"][j]), tuple(G["verts"][j, :G["dim"][j] + 1]))
+                for j in range(G.m)]
+        assert keys == sorted(keys) and max(vg.values()) <= T
+
+
+def test_column_addition_ratios_match_table1(orc):
+    # Table 1 prints, for its four 15-point ensembles reduced to dimension 5 on the scale grid
+    # r_T = 5, h = 10, the ratio of total column additions of Algorithm 2 to the standard
+    # reduction (0.40-0.52) and to the twist (1.00-1.01). The stand-in ensembles reproduce
+    # them with the Phase I / Phase II rules alone (no Corollary 10 zero case); the zero case,
+    # an addition of this build, only removes further additions.
+    for name in pc.ENSEMBLES:
+        K = orc.vr_build(pc.ensemble15(name), 5, scale_step=32768, n_scales=10)
+        std = orc.reduce_std(K)[1][0]
+        twist = orc.reduce_twist(K)[1][0]
+        for strict in (False, True):
+            pms = orc.reduce_pms(K, strict=strict, cor10=False).stats[:, 6].sum()
+            assert 0.40 <= pms / std <= 0.55, (name, pms / std)
+            assert 0.98 <= pms / twist <= 1.02, (name, pms / twist)
+            assert orc.reduce_pms(K, strict=strict).stats[:, 6].sum() <= pms
+
+
 def test_euler_characteristic_vr(orc):
     for seed in range(3):
         x = pc.random_cloud(11, 3, seed)
