@@ -89,6 +89,11 @@ typedef struct {
   /* wall-clock bound of one ph_reduce's pass loop in ms, checked on the device at the end of
    * every pass (0 = library default, 60000); past it the call returns PH_ERR_TIMEOUT */
   int32_t timeout_ms;
+  /* 1: every pass also applies the non-zero case of Corollary 10 (Lemma 9): an active column j
+   * with beta_j >= 0 whose candidate set L_j (rows of K_{d-1} in [beta_j, low(j)] not known to
+   * be paired) holds one row i has lowstar(j) = i, which ph_get_predicted_lows reports before
+   * the column is reduced. 0 (default): off. */
+  int32_t predict_pairs;
 } ph_opts;
 
 /* Per-pass counters (rows of ph_get_pass_stats), in this order. */
@@ -104,6 +109,9 @@ enum {
   PH_PS_COPIED,        /* rows moved without an addition (survivors and new pivots) */
   PH_PS_ESS_EST,       /* |E^l| after the pass's marks: the essential estimate of
                         * Eq. (essential_iteration), which contains Ess (Lemma 11) */
+  PH_PS_PREDICTED,     /* columns whose pair Corollary 10 (non-zero case) predicts for the first
+                        * time (needs predict_pairs) */
+  PH_PS_EMPTY_L,       /* columns with an empty candidate set L_j: always 0 (Lemma 9) */
   PH_PS_N
 };
 
@@ -233,6 +241,13 @@ int ph_get_essential(ph_ctx* ctx, int32_t cloud, int64_t* idx, int32_t* dim, int
  * of the cloud in filtration order: 1 if in E^l. With in_e == NULL only *count is written.
  * Needs ph_reduce first. Synchronises the stream. */
 int ph_get_essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* in_e, int64_t* count);
+
+/* Pairs predicted by Corollary 10 (non-zero case) so far, for cloud `cloud`: host buffer
+ * `pred` of `count` int32, one per simplex in filtration order, holding the predicted
+ * lowstar as a filtration index, or -1 where no prediction was made. Every prediction is
+ * exact (Lemma 9), also after a partial reduction. With pred == NULL only *count is written.
+ * Needs ph_reduce first with predict_pairs = 1. Synchronises the stream. */
+int ph_get_predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* pred, int64_t* count);
 
 /* Inspection of the filtration of cloud `cloud` in filtration order, for testing the build
  * against an independent implementation. Host buffers of `count` entries (any may be NULL):

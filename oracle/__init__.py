@@ -29,7 +29,7 @@ _LIB_PATH = _HERE / "libph_oracle.so"
 _lib = None
 
 PS_FIELDS = ("active", "new_pivots", "zero_final", "cor10", "cleared", "targets", "adds",
-             "xors", "ess_est")
+             "xors", "ess_est", "predicted", "empty_l")
 
 
 def build_lib(force: bool = False) -> Path:
@@ -67,7 +67,7 @@ def _load():
         L.orc_reduce_std.restype = ctypes.c_int
         L.orc_reduce_twist.argtypes = [i64, P, P, P, P, P]
         L.orc_reduce_twist.restype = ctypes.c_int
-        L.orc_reduce_pms.argtypes = [i64, P, P, P, P, i32, i32, i32, P, P, P, P, P]
+        L.orc_reduce_pms.argtypes = [i64, P, P, P, P, i32, i32, i32, P, P, P, P, P, P]
         L.orc_reduce_pms.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -180,7 +180,7 @@ def reduce_twist(K: Complex):
 
 class PmsResult(dict):
     """low, passes, stats (rows per executed pass, columns PS_FIELDS), ess_est, proven,
-    converged."""
+    predicted (Corollary 10 non-zero case: lowstar of the column, or -1), converged."""
 
     def __getattr__(self, k):
         return self[k]
@@ -197,14 +197,15 @@ def reduce_pms(K: Complex, max_passes: int = 100000, strict: bool = False, cor10
     npass = ctypes.c_int32(0)
     ess = np.zeros(max(m, 1), np.uint8)
     proven = np.zeros(max(m, 1), np.uint8)
+    pred = np.full(max(m, 1), -1, np.int32)
     rc = L.orc_reduce_pms(m, _ptr(K["colptr"]), _ptr(K["rows"]), _ptr(K["dim"]), _ptr(b),
                           max_passes, int(strict), int(cor10), _ptr(low), _ptr(ps),
-                          ctypes.byref(npass), _ptr(ess), _ptr(proven))
+                          ctypes.byref(npass), _ptr(ess), _ptr(proven), _ptr(pred))
     if rc < 0:
         raise RuntimeError(rc)
     p = npass.value
     return PmsResult(low=low, passes=p, stats=ps[:p + 1], ess_est=ess[:m].astype(bool),
-                     proven=proven[:m].astype(bool), converged=(rc == 0))
+                     proven=proven[:m].astype(bool), predicted=pred[:m], converged=(rc == 0))
 
 
 def pairs_and_essential(low: np.ndarray, dim: np.ndarray):

@@ -477,14 +477,21 @@ int orc_reduce_twist(int64_t m, const int64_t* colptr, const int32_t* rows, cons
 /*   3 Cor-10 zeroings                4 cleared columns that were active                        */
 /*   5 colliding columns (targets)    6 additions done   7 nontrivial XORs                      */
 /*   8 |E| after the pass (essential estimate, Eq. essential_iteration)                         */
+/*   9 columns whose pair is predicted by Corollary 10 (non-zero case) for the first time       */
+/*  10 columns with an empty candidate set L_j (impossible by Lemma 9; counted as a check)      */
+/*                                                                                              */
+/* Corollary 10, non-zero case (pred_out): for an active column j of dimension d >= 1 with      */
+/* beta_j >= 0 (hence negative, Thm 5, so 0 is not a candidate) that this pass neither proves   */
+/* nor zeroes, L_j is the set of rows of K_{d-1} in [beta_j, low(j)] not in Paired (start of    */
+/* the pass). If it holds one row i, lowstar(j) = i (Lemma 9): pred_out[j] = i from then on.    */
 /* ------------------------------------------------------------------------------------------ */
-#define ORC_PS_N 9
+#define ORC_PS_N 11
 #define ORC_MAX_DIM 16
 
 int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const int32_t* dim,
                    const int32_t* beta, int32_t max_passes, int32_t strict, int32_t use_cor10,
                    int32_t* low_out, int64_t* pass_stats, int32_t* passes_out,
-                   uint8_t* ess_est_out, uint8_t* proven_out) {
+                   uint8_t* ess_est_out, uint8_t* proven_out, int32_t* pred_out) {
   col_t* R = cols_from_csc(m, colptr, rows);
   int64_t M = m > 0 ? m : 1;
   int32_t* low = (int32_t*)malloc((size_t)M * sizeof(int32_t));
@@ -495,8 +502,11 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
   uint8_t* newpiv = (uint8_t*)calloc((size_t)M, 1);
   uint8_t* zeroed = (uint8_t*)calloc((size_t)M, 1); /* zeroed during the current pass */
   uint8_t* in_E = (uint8_t*)malloc((size_t)M);
+  uint8_t* unpaired = (uint8_t*)malloc((size_t)M); /* start of the pass */
+  int32_t* pred = (int32_t*)malloc((size_t)M * sizeof(int32_t));
   col_t tmp = {0, 0, 0};
-  if (!R || !low || !tab || !owner || !proven || !final_ || !newpiv || !zeroed || !in_E)
+  if (!R || !low || !tab || !owner || !proven || !final_ || !newpiv || !zeroed || !in_E ||
+      !unpaired || !pred)
     return ORC_ERR_ALLOC;
   int32_t maxd = 0;
   for (int64_t j = 0; j < m; j++)
@@ -507,6 +517,7 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
     low[j] = col_low(&R[j]);
     owner[j] = -1;
     in_E[j] = 1; /* E^0 = [m] */
+    pred[j] = -1;
   }
   int status = ORC_NOT_CONVERGED;
   int32_t pass = 0;
@@ -521,6 +532,7 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
     for (int d = 0; d < ORC_MAX_DIM; d++) first_unpaired[d] = m;
     for (int64_t x = m - 1; x >= 0; x--) {
       int paired = proven[x] || beta[x] >= 0 || owner[x] >= 0;
+      unpaired[x] = (uint8_t)!paired;
       if (!paired) first_unpaired[dim[x]] = x;
     }
     /* 3. marks from the start-of-pass state */
@@ -543,6 +555,19 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
         } else if (use_cor10 && d >= 1 && beta[j] < 0 && low[j] < first_unpaired[d - 1]) {
           zeroed[j] = 1;
           st[3]++;
+        } else if (d >= 1 && beta[j] >= 0) {
+          /* the candidate set L_j: unpaired rows of K_{d-1} in [beta_j, low(j)] */
+          int64_t n_cand = 0, last = -1;
+          for (int64_t x = beta[j]; x <= low[j]; x++)
+            if (dim[x] == d - 1 && unpaired[x]) {
+              n_cand++;
+              last = x;
+            }
+          if (n_cand == 0) st[10]++;
+          if (n_cand == 1 && pred[j] < 0) {
+            pred[j] = (int32_t)last;
+            st[9]++;
+          }
         }
         if (!leftmost && low[j] > P) P = low[j];
       }
@@ -598,6 +623,7 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
   for (int64_t j = 0; j < m; j++) low_out[j] = low[j];
   if (ess_est_out) memcpy(ess_est_out, in_E, (size_t)m);
   if (proven_out) memcpy(proven_out, proven, (size_t)m);
+  if (pred_out) memcpy(pred_out, pred, (size_t)m * sizeof(int32_t));
   cols_free(R, m);
   free(low);
   free(tab);
@@ -607,6 +633,8 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
   free(newpiv);
   free(zeroed);
   free(in_E);
+  free(unpaired);
+  free(pred);
   free(tmp.v);
   return status;
 }

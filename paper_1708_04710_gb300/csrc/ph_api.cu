@@ -277,6 +277,7 @@ void ph_default_opts(ph_opts* o) {
   o->time_kernels = 0;
   o->add_blocks_per_sm = 0;
   o->timeout_ms = 0;
+  o->predict_pairs = 0;
 }
 
 int ph_create(ph_ctx** out, const ph_opts* opts, const ph_allocator* alloc, void* stream) {
@@ -471,6 +472,22 @@ int ph_get_essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* in_e, int64_t
   if (count) *count = n;
   if (!in_e) return PH_OK;
   ph::essential_estimate(ctx, cloud, in_e, n);
+  return PH_OK;
+  PH_API_END
+}
+
+int ph_get_predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* pred, int64_t* count) {
+  PH_API_BEGIN
+  PH_REQUIRE(ctx->reduced && ctx->rs.init, PH_ERR_INVALID, "call ph_reduce first");
+  PH_REQUIRE(ctx->opts.predict_pairs, PH_ERR_INVALID, "the context was made without predict_pairs");
+  PH_REQUIRE(cloud >= 0 && cloud < ctx->n_clouds, PH_ERR_INVALID, "cloud out of range");
+  const int nc = ctx->n_clouds;
+  int64_t n = 0;
+  for (int d = 0; d <= ctx->max_dim; d++)
+    n += ctx->seg_start[d * nc + cloud + 1] - ctx->seg_start[d * nc + cloud];
+  if (count) *count = n;
+  if (!pred) return PH_OK;
+  ph::predicted_lows(ctx, cloud, pred, n);
   return PH_OK;
   PH_API_END
 }

@@ -92,6 +92,9 @@ struct ReduceState {
   void* look = nullptr;        // look-back states of the survivor scan
   void* dlist = nullptr;       // deferred column updates
   void* src_e = nullptr;       // per active slot: source candidate of Phase II
+  uint32_t* unp_bits = nullptr;  // Corollary 10 predictions: unpaired-row bitmap
+  int32_t* unp_words = nullptr;  // and its per-word prefix counts
+  int32_t* pred = nullptr;       // per id: predicted lowstar, -1
   int64_t tiles_bytes = 0;
   void* dstate = nullptr;      // per-pass state in device memory
   void* hstate = nullptr;      // pinned host mirror of it
@@ -296,6 +299,8 @@ void extract_all(ph_ctx* ctx);
 void free_reduce_state(ph_ctx* ctx);
 // E^l of one cloud, one byte per simplex in filtration order, into host memory (n bytes)
 void essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* host_out, int64_t n);
+// predicted lowstar per simplex of one cloud (filtration indices, -1), into host memory
+void predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* host_out, int64_t n);
 // generic device helpers (ph_scan.cu)
 void excl_scan_i64(ph_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev);
 void radix_sort_u64(ph_ctx* ctx, uint64_t* keys, uint64_t* vals, int64_t n, int lo_bit,

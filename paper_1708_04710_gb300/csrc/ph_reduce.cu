@@ -89,6 +89,10 @@ struct RArgs {
   unsigned long long* look;  // per 256-entry chunk: look-back state of the survivor count
   int32_t* dlist;     // active slots whose column update waits for k_commit
   int32_t* src_e;     // per active slot: the colliding column's left-most column, -1 if none
+  int predict;        // 1: Corollary 10 non-zero case (pair predictions)
+  uint32_t* unp_bits; // per row, bit: not known to be paired at the start of the pass
+  int32_t* unp_words; // [nwords + 1] exclusive prefix of unpaired rows per 32-row word
+  int32_t* pred;      // per id: predicted lowstar (Corollary 10), -1
   int staged_max;     // merges of more rows than this run from global memory
   int force_km;       // > 0: merge-path positions per lane for every warp
 };
@@ -129,6 +133,16 @@ __device__ __forceinline__ void stat_add(int64_t* stats, int k, int64_t v) {
 }
 
 
+// True in the one block that finishes the grid last; it then sees every other block's writes.
+__device__ __forceinline__ bool last_block(unsigned int* done) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return s_last;
+}
+
 // ------------------------------------------------------------------------------------------
 __global__ void k_tab_init(RArgs a) {
   DevState* ds = a.ds;
@@ -141,13 +155,66 @@ __global__ void k_tab_init(RArgs a) {
     ds->n_deferred = 0;
     ds->totals[0] = ds->totals[1] = 0;
   }
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < a.rows_end;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    int32_t o = a.owner[x];
-    a.tab[x] = o < 0 ? INT32_MAX : o;
-    bool paired = (a.meta[x].flags & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
-    if (!paired) atomicMin(&a.first_unp[a.seg[x]], (int32_t)x);
+  // warp-uniform loop: each iteration a warp covers 32 consecutive rows, one bitmap word
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); x0 < a.rows_end;
+       x0 += stride) {
+    const int64_t x = x0 + (threadIdx.x & 31);
+    bool unpaired = false;
+    if (x < a.rows_end) {
+      int32_t o = a.owner[x];
+      a.tab[x] = o < 0 ? INT32_MAX : o;
+      bool paired = (a.meta[x].flags & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
+      if (!paired) atomicMin(&a.first_unp[a.seg[x]], (int32_t)x);
+      unpaired = !paired;
+    }
+    if (a.predict) {
+      const unsigned w = __ballot_sync(0xffffffffu, unpaired);
+      if ((threadIdx.x & 31) == 0) a.unp_bits[x0 >> 5] = w;
+    }
   }
+  if (a.predict && last_block(&ds->blocks_done)) {  // prefix counts of the words
+    __shared__ int64_t sh[kWarps + 1];
+    const int64_t nwords = (a.rows_end + 31) / 32;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nwords; base += kThreads) {
+      const int64_t w = base + threadIdx.x;
+      const int64_t c = w < nwords ? __popc(__ldcg(a.unp_bits + w)) : 0;
+      int64_t tot;
+      const int64_t ex = block_excl_sum<int64_t>(c, sh, tot);
+      if (w < nwords) a.unp_words[w] = (int32_t)(carry + ex);
+      carry += tot;
+    }
+    if (threadIdx.x == 0) {
+      a.unp_words[nwords] = (int32_t)carry;
+      ds->blocks_done = 0;
+    }
+  }
+}
+
+// rows of the start-of-pass unpaired bitmap before row x
+__device__ __forceinline__ int32_t unpaired_before(const RArgs& a, int64_t x) {
+  const int64_t w = x >> 5;
+  const unsigned low_bits = (x & 31) ? (0xffffffffu >> (32 - (x & 31))) : 0u;
+  return a.unp_words[w] + ((x & 31) ? __popc(a.unp_bits[w] & low_bits) : 0);
+}
+
+// Corollary 10, non-zero case: beta_j >= 0 makes j negative (Thm 5), so its candidate set L_j
+// holds the unpaired rows of K_{d-1} in [beta_j, low(j)] only (rows of one cloud's segment are
+// contiguous ids). One candidate is lowstar(j) (Lemma 9). Returns it, -1 if there are several,
+// -2 if there is none (impossible; counted as a check).
+__device__ __forceinline__ int32_t predicted_low(const RArgs& a, int32_t b, int32_t l) {
+  const int32_t c0 = unpaired_before(a, b);
+  const int32_t n = unpaired_before(a, (int64_t)l + 1) - c0;
+  if (n != 1) return n == 0 ? -2 : -1;
+  int64_t lo = b >> 5, hi = l >> 5;  // last word whose prefix is <= c0
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (a.unp_words[mid] <= c0) lo = mid; else hi = mid - 1;
+  }
+  unsigned bits = a.unp_bits[lo];
+  for (int32_t k = c0 - a.unp_words[lo]; k > 0; k--) bits &= bits - 1;  // skip k set bits
+  return (int32_t)(lo * 32 + __ffs(bits) - 1);
 }
 
 __global__ void k_tab(RArgs a) {
@@ -205,15 +272,6 @@ __device__ __forceinline__ SegMax block_scan_segmax(SegMax v, SegMax carry, SegM
   return ex;
 }
 
-// True in the one block that finishes the grid last; it then sees every other block's writes.
-__device__ __forceinline__ bool last_block(unsigned int* done) {
-  __shared__ bool s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
-  __syncthreads();
-  return s_last;
-}
 
 // scan of the tile aggregates to tile prefixes, by one block
 __device__ __forceinline__ void p1_top(const RArgs& a, const PV& v, SegMax* sh) {
@@ -304,7 +362,7 @@ __global__ void k_mark(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
-  int64_t n_zero = 0, n_piv = 0, n_c10 = 0;
+  int64_t n_zero = 0, n_piv = 0, n_c10 = 0, n_pred = 0, n_empty = 0;
   for (int64_t chunk = blockIdx.x; chunk < v.nchunks; chunk += gridDim.x) {
     const int64_t tile = chunk / kRItems;
     SegMax carry = a.tile_sm[tile];
@@ -334,6 +392,14 @@ __global__ void k_mark(RArgs a) {
         } else if (a.cor10 && b < 0 && l < a.first_unp[val.seg - a.nc]) {
           a.meta[j].flags = f | F_FINAL;  // Corollary 10, zero case
           n_c10++;
+        } else if (a.predict && b >= 0 && a.pred[j] < 0) {
+          const int32_t i = predicted_low(a, b, l);
+          if (i >= 0) {
+            a.pred[j] = i;
+            n_pred++;
+          } else if (i == -2) {
+            n_empty++;
+          }
         }
       }
     }
@@ -341,6 +407,8 @@ __global__ void k_mark(RArgs a) {
   if (v.stats) {
     stat_add(v.stats, PH_PS_ZERO_FINAL, n_zero);
     stat_add(v.stats, PH_PS_NEW_PIVOTS, n_piv);
+    stat_add(v.stats, PH_PS_PREDICTED, n_pred);
+    stat_add(v.stats, PH_PS_EMPTY_L, n_empty);
     stat_add(v.stats, PH_PS_COR10, n_c10);
   }
 }
@@ -1161,6 +1229,10 @@ static RArgs make_args(ph_ctx* ctx) {
   a.look = static_cast<unsigned long long*>(rs.look);
   a.dlist = static_cast<int32_t*>(rs.dlist);
   a.src_e = static_cast<int32_t*>(rs.src_e);
+  a.predict = ctx->opts.predict_pairs ? 1 : 0;
+  a.unp_bits = rs.unp_bits;
+  a.unp_words = rs.unp_words;
+  a.pred = rs.pred;
   a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
                                                  : kStage;
   a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
@@ -1232,6 +1304,14 @@ void reduce_init(ph_ctx* ctx) {
   PH_CUDA(cudaMemsetAsync(rs.look, 0, nchunks * sizeof(unsigned long long), st));
   rs.dlist = alloc_n<int32_t>(ctx, m);
   rs.src_e = alloc_n<int32_t>(ctx, m);
+  if (ctx->opts.predict_pairs) {
+    const int64_t rows = ctx->dimoff[ctx->max_dim];
+    const int64_t nwords = (rows + 31) / 32;
+    rs.unp_bits = alloc_n<uint32_t>(ctx, nwords + 1);
+    rs.unp_words = alloc_n<int32_t>(ctx, nwords + 1);
+    rs.pred = alloc_n<int32_t>(ctx, m);
+    PH_CUDA(cudaMemsetAsync(rs.pred, 0xff, (size_t)m * sizeof(int32_t), st));
+  }
   rs.dstate = ctx->dalloc(sizeof(DevState));
   PH_CUDA(cudaMallocHost(&rs.hstate, sizeof(DevState)));
   rs.h_stats.clear();
@@ -1465,6 +1545,44 @@ void essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* host_out, int64_t n
   PH_REQUIRE(bad == 0, PH_ERR_INVALID, "internal error: filtration index out of range");
 }
 
+__global__ void k_pred_out(int64_t lo, int64_t hi, const int32_t* __restrict__ pred,
+                           const int64_t* __restrict__ gidx, int64_t n, int32_t* out,
+                           int32_t* bad) {
+  for (int64_t x = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < hi;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = gidx[x];
+    if (g < 0 || g >= n) {
+      *bad = 1;
+      continue;
+    }
+    const int32_t p = pred[x];
+    out[g] = p >= 0 ? (int32_t)gidx[p] : -1;
+  }
+}
+
+void predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* host_out, int64_t n) {
+  ReduceState& rs = ctx->rs;
+  const int nc = ctx->n_clouds;
+  int32_t* d_out = alloc_n<int32_t>(ctx, std::max<int64_t>(n, 1));
+  int32_t* d_bad = alloc_n<int32_t>(ctx, 1);
+  PH_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int32_t), ctx->stream));
+  for (int d = 0; d <= ctx->max_dim; d++) {
+    const int64_t lo = ctx->seg_start[d * nc + cloud], hi = ctx->seg_start[d * nc + cloud + 1];
+    if (hi <= lo) continue;
+    k_pred_out<<<grid_for(ctx, hi - lo, kThreads), kThreads, 0, ctx->stream>>>(
+        lo, hi, rs.pred, ctx->gidx, n, d_out, d_bad);
+    PH_CHECK_LAUNCH();
+  }
+  int32_t bad = 0;
+  PH_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  PH_CUDA(cudaMemcpyAsync(host_out, d_out, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  PH_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->dfree(d_out);
+  ctx->dfree(d_bad);
+  PH_REQUIRE(bad == 0, PH_ERR_INVALID, "internal error: filtration index out of range");
+}
+
 void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
   if (rs.graph_exec) cudaGraphExecDestroy(rs.graph_exec);
@@ -1472,7 +1590,8 @@ void free_reduce_state(ph_ctx* ctx) {
   for (void* p : {(void*)rs.act, (void*)rs.act2, rs.meta,
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
                   (void*)rs.first_unp, rs.tiles, rs.dstate,
-                  rs.look, rs.dlist, rs.src_e,
+                  rs.look, rs.dlist, rs.src_e, (void*)rs.unp_bits, (void*)rs.unp_words,
+                  (void*)rs.pred,
                   (void*)rs.pass_stats})
     ctx->dfree(p);
   for (auto& a : rs.arena) ctx->dfree(a.p);

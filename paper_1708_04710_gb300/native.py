@@ -17,7 +17,7 @@ LIB_PATH = Path(__file__).resolve().parent / "libph_gb300.so"
 
 PH_OK, PH_NOT_CONVERGED = 0, 1
 PS_FIELDS = ("active", "new_pivots", "zero_final", "cor10", "cleared", "targets", "adds",
-             "xors", "copied", "ess_est")
+             "xors", "copied", "ess_est", "predicted", "empty_l")
 
 
 class PHError(RuntimeError):
@@ -30,7 +30,8 @@ class PhOpts(Structure):
     _fields_ = [("strict_phase2", c_int32), ("use_cor10", c_int32), ("block_threads", c_int32),
                 ("staged_merge_max", c_int32), ("merge_items", c_int32),
                 ("collect_stats", c_int32), ("use_graph", c_int32), ("time_kernels", c_int32),
-                ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32)]
+                ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32),
+                ("predict_pairs", c_int32)]
 
 
 class PhStats(Structure):
@@ -75,6 +76,7 @@ SIGNATURES = {
     "ph_beta_static": (c_int, [c_void_p, c_int64, c_int32, c_int64, c_void_p, c_void_p]),
     "ph_get_add_times": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "ph_get_essential_estimate": (c_int, [c_void_p, c_int32, c_void_p, POINTER(c_int64)]),
+    "ph_get_predicted_lows": (c_int, [c_void_p, c_int32, c_void_p, POINTER(c_int64)]),
     "ph_kernel_launches": (c_int64, [c_void_p]),
     "ph_last_error": (c_char_p, [c_void_p]),
 }
@@ -122,7 +124,7 @@ class Context:
     def __init__(self, *, strict_phase2: bool = False, use_cor10: bool = True,
                  collect_stats: bool = False, staged_merge_max: int = 0, merge_items: int = 0,
                  use_graph: bool = True, time_kernels: bool = False, add_blocks_per_sm: int = 0,
-                 timeout_ms: int = 0,
+                 timeout_ms: int = 0, predict_pairs: bool = False,
                  stream=None):
         torch = _torch()
         self._torch = torch
@@ -139,6 +141,7 @@ class Context:
         opts.time_kernels = int(time_kernels)
         opts.add_blocks_per_sm = int(add_blocks_per_sm)
         opts.timeout_ms = int(timeout_ms)
+        opts.predict_pairs = int(predict_pairs)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
         dev_index = self.device.index if self.device.index is not None else 0
@@ -290,6 +293,15 @@ class Context:
         out = np.zeros(n.value, np.uint8)
         self._check(self.lib.ph_get_essential_estimate(self._h, int(cloud), _ptr(out), byref(n)))
         return out.astype(bool)
+
+    def predicted_lows(self, cloud: int = 0) -> np.ndarray:
+        """lowstar predicted by Corollary 10 (non-zero case) per simplex of the cloud in
+        filtration order (filtration index, -1 where none); needs predict_pairs."""
+        n = c_int64(0)
+        self._check(self.lib.ph_get_predicted_lows(self._h, int(cloud), None, byref(n)))
+        out = np.zeros(n.value, np.int32)
+        self._check(self.lib.ph_get_predicted_lows(self._h, int(cloud), _ptr(out), byref(n)))
+        return out
 
     def kernel_launches(self) -> int:
         return int(self.lib.ph_kernel_launches(self._h))

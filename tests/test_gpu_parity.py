@@ -260,6 +260,36 @@ def test_time_bound_stops_between_passes_and_resumes(ph, orc, use_graph):
     assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_corollary10_predictions(ph, orc, use_graph):
+    # the non-zero case of Corollary 10: the GPU predicts exactly the oracle's pairs, pass by
+    # pass, and every prediction is a true pair of the finished reduction (Lemma 9)
+    import torch
+
+    cases = [(pc.random_cloud(40, 3, 109), 2, False, -1, 0), (pc.random_cloud(40, 3, 105), 2, True, -1, 0),
+             (pc.ensemble15("trefoil15"), 5, False, 32768, 10), (pc.circle40(), 2, False, -1, 0)]
+    for x, k, strict, step, ns in cases:
+        K = (orc.vr_build(x, k, scale_step=step, n_scales=ns) if step > 0 else orc.vr_build(x, k))
+        full = orc.reduce_pms(K, strict=strict)
+        for mp in list(range(min(full.passes, 3))) + [-1]:
+            ref = full if mp < 0 else orc.reduce_pms(K, max_passes=mp, strict=strict)
+            ctx = ph.Context(collect_stats=True, strict_phase2=strict, predict_pairs=True,
+                             use_graph=use_graph)
+            xt = torch.from_numpy(x).cuda()
+            if step > 0:
+                ctx.build_filtration_scales(xt, None, k, step, ns)
+            else:
+                ctx.build_filtration(xt, None, k)
+            ctx.reduce(max_passes=mp)
+            pred = ctx.predicted_lows(0)
+            assert np.array_equal(pred, ref.predicted)
+            ps = ctx.pass_stats()
+            assert np.array_equal(ps[:, 10], ref.stats[:, 9])
+            assert not ps[:, 11].any()
+            sel = pred >= 0
+            assert np.array_equal(pred[sel], full.low[sel])
+
+
 def test_triangulations(ph, orc):
     from helpers import closure, random_compatible_order
 

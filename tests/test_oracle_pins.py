@@ -261,6 +261,26 @@ def test_column_addition_ratios_match_table1(orc):
             assert orc.reduce_pms(K, strict=strict).stats[:, 6].sum() <= pms
 
 
+def test_corollary10_predictions_are_pairs(orc):
+    # Lemma 9 / Corollary 10: lowstar(j) lies in L_j at every iteration, so a one-element L_j
+    # (beta_j >= 0) names lowstar(j). Checked against the standard reduction; L_j is never empty
+    n_pred = 0
+    for x, k, strict in [(pc.random_cloud(40, 3, 109), 2, False),
+                         (pc.random_cloud(40, 3, 105), 2, True),
+                         (pc.random_cloud(30, 3, 5), 3, False), (pc.ensemble15("gaussian15"), 5, False)]:
+        K = orc.vr_build(x, k)
+        lowstar = orc.reduce_std(K)[0]
+        full = orc.reduce_pms(K, strict=strict)
+        for mp in range(full.passes + 1):
+            r = orc.reduce_pms(K, max_passes=mp, strict=strict)
+            sel = r.predicted >= 0
+            assert np.array_equal(r.predicted[sel], lowstar[sel])
+            assert not r.stats[:, 10].any()
+            assert np.all(full.predicted[sel] == r.predicted[sel])  # predictions persist
+        n_pred += int((full.predicted >= 0).sum())
+    assert n_pred >= 10
+
+
 def test_euler_characteristic_vr(orc):
     for seed in range(3):
         x = pc.random_cloud(11, 3, seed)
