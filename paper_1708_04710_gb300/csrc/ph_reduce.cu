@@ -309,32 +309,56 @@ __device__ __forceinline__ void check_capacity(DevState* ds) {
 __global__ void k_p1_tiles(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
   __shared__ int64_t shs[kWarps + 1];
+  __shared__ SegMax s_warp[kRItems][kWarps];  // aggregate of each warp's 32 slots per chunk
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
   int64_t bw = 0, bp = 0;
   for (int64_t t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
     const int64_t tile0 = t * kRTile;
-    SegMax carry{-1, -1};
+    // every load of the tile's kRItems slots per thread is issued before any is used
+    int32_t j[kRItems], l[kRItems], sg[kRItems], n[kRItems];
+#pragma unroll
     for (int it = 0; it < kRItems; it++) {
       const int64_t e = tile0 + it * kThreads + threadIdx.x;
-      SegMax val = p1_value(a, v, e);
-      SegMax tot;
-      block_scan_segmax(val, SegMax{-1, -1}, sh, tot);  // this chunk alone
-      if (threadIdx.x == 0) a.chunk_sm[t * kRItems + it] = tot;
-      carry = segmax_combine(carry, tot);
-      if (e < v.n_act) {
-        const int32_t j = v.act[e];
-        const int32_t n = a.meta[j].len;
-        bw += n;
-        const int32_t l = a.low[j];
-        if (l >= 0) {
-          const int32_t s = a.tab[l];
-          if (s != j) bw += a.meta[s].len;  // a target: its source may be added
-          else bp += n;                 // left-most: it may be proven and move
-        }
-      }
+      j[it] = e < v.n_act ? v.act[e] : -1;
     }
-    if (threadIdx.x == 0) a.tile_sm[t] = carry;
+#pragma unroll
+    for (int it = 0; it < kRItems; it++) {
+      l[it] = j[it] >= 0 ? a.low[j[it]] : -1;
+      sg[it] = j[it] >= 0 ? a.seg[j[it]] : INT32_MAX;
+      n[it] = j[it] >= 0 ? a.meta[j[it]].len : 0;
+    }
+#pragma unroll
+    for (int it = 0; it < kRItems; it++) {
+      const int32_t s = l[it] >= 0 ? a.tab[l[it]] : -1;
+      const bool collide = l[it] >= 0 && s != j[it];
+      bw += n[it];
+      if (collide) bw += a.meta[s].len;  // a target: its source may be added
+      else if (l[it] >= 0) bp += n[it];  // left-most: it may be proven and move
+      // Phase I value: the low of a colliding column, in its (cloud, dim) segment
+      SegMax val{sg[it], collide ? l[it] : -1};
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {  // ordered reduction over the warp's 32 slots
+        SegMax u;
+        u.seg = __shfl_down_sync(0xffffffffu, val.seg, o);
+        u.val = __shfl_down_sync(0xffffffffu, val.val, o);
+        if ((lane & (2 * o - 1)) == 0) val = segmax_combine(val, u);
+      }
+      if (lane == 0) s_warp[it][warp] = val;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      SegMax carry{-1, -1};
+      for (int it = 0; it < kRItems; it++) {
+        SegMax c = s_warp[it][0];
+        for (int w = 1; w < kWarps; w++) c = segmax_combine(c, s_warp[it][w]);
+        a.chunk_sm[t * kRItems + it] = c;  // this chunk alone
+        carry = segmax_combine(carry, c);
+      }
+      a.tile_sm[t] = carry;
+    }
+    __syncthreads();
   }
   int64_t tw, tp;
   block_excl_sum<int64_t>(bw, shs, tw);
@@ -1250,7 +1274,7 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   PH_CHECK_LAUNCH();
   k_tab<<<sms * 8, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_p1_tiles<<<sms * 4, kThreads, 0, st>>>(a);
+  k_p1_tiles<<<sms * 8, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
   k_mark<<<sms * 8, kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
