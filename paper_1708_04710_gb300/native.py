@@ -324,8 +324,8 @@ class Context:
         k = n.value
         if on_device:
             mk = lambda dt: torch.empty(k, dtype=dt, device=self.device)  # noqa: E731
-        else:
-            mk = lambda dt: torch.empty(k, dtype=dt)  # noqa: E731
+        else:  # page-locked, so the device-to-host copies run at full speed
+            mk = lambda dt: torch.empty(k, dtype=dt, pin_memory=True)  # noqa: E731
         out = dict(birth=mk(torch.int64), death=mk(torch.int64), dim=mk(torch.int32),
                    birth_diam2=mk(torch.int64), death_diam2=mk(torch.int64))
         self._check(self.lib.ph_get_pairs(self._h, cloud, _ptr(out["birth"]), _ptr(out["death"]),
@@ -339,10 +339,11 @@ class Context:
         n = c_int64(0)
         self._check(self.lib.ph_get_essential(self._h, cloud, None, None, None, 0, byref(n), 0))
         k = n.value
-        dev = self.device if on_device else "cpu"
-        out = dict(idx=torch.empty(k, dtype=torch.int64, device=dev),
-                   dim=torch.empty(k, dtype=torch.int32, device=dev),
-                   diam2=torch.empty(k, dtype=torch.int64, device=dev))
+        if on_device:
+            mk = lambda dt: torch.empty(k, dtype=dt, device=self.device)  # noqa: E731
+        else:  # page-locked, so the device-to-host copies run at full speed
+            mk = lambda dt: torch.empty(k, dtype=dt, pin_memory=True)  # noqa: E731
+        out = dict(idx=mk(torch.int64), dim=mk(torch.int32), diam2=mk(torch.int64))
         self._check(self.lib.ph_get_essential(self._h, cloud, _ptr(out["idx"]), _ptr(out["dim"]),
                                               _ptr(out["diam2"]), k, byref(n), int(on_device)))
         return out
