@@ -134,11 +134,13 @@ __device__ __forceinline__ void stat_add(int64_t* stats, int k, int64_t v) {
 
 
 // True in the one block that finishes the grid last; it then sees every other block's writes.
-__device__ __forceinline__ bool last_block(unsigned int* done) {
+// Only the first `participants` blocks of the grid may call it (the others have no work and
+// may leave at once).
+__device__ __forceinline__ bool last_block(unsigned int* done, unsigned int participants) {
   __shared__ bool s_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == participants - 1;
   __syncthreads();
   return s_last;
 }
@@ -173,7 +175,7 @@ __global__ void k_tab_init(RArgs a) {
       if ((threadIdx.x & 31) == 0) a.unp_bits[x0 >> 5] = w;
     }
   }
-  if (a.predict && last_block(&ds->blocks_done)) {  // prefix counts of the words
+  if (a.predict && last_block(&ds->blocks_done, gridDim.x)) {  // prefix counts of the words
     __shared__ int64_t sh[kWarps + 1];
     const int64_t nwords = (a.rows_end + 31) / 32;
     int64_t carry = 0;
@@ -312,6 +314,9 @@ __global__ void k_p1_tiles(RArgs a) {
   __shared__ SegMax s_warp[kRItems][kWarps];  // aggregate of each warp's 32 slots per chunk
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
+  // blocks beyond the tiles leave at once; block 0 always takes part (it checks capacity)
+  const unsigned parts = (unsigned)std::max<int64_t>(1, std::min<int64_t>(gridDim.x, v.ntiles));
+  if (blockIdx.x >= parts) return;
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   int64_t bw = 0, bp = 0;
   for (int64_t t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
@@ -368,7 +373,7 @@ __global__ void k_p1_tiles(RArgs a) {
     atomicAdd(&a.ds->bound_piv, (unsigned long long)tp);
   }
   // the last block scans the tile aggregates and checks capacity (no extra launches)
-  if (last_block(&a.ds->blocks_done)) {
+  if (last_block(&a.ds->blocks_done, parts)) {
     p1_top(a, v, sh);
     if (threadIdx.x == 0) {
       a.ds->blocks_done = 0;
@@ -1145,11 +1150,15 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
 
 // the deferred column updates, then (last block) the end of the pass
 __global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
-  if (a.ds->status == ST_RUN) {
+  // as many blocks as the deferred list needs take part; block 0 always does (it ends the pass)
+  const int64_t n = a.ds->status == ST_RUN ? (int64_t)a.ds->n_deferred : 0;
+  const unsigned parts =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(gridDim.x, (n + blockDim.x - 1) / blockDim.x));
+  if (blockIdx.x >= parts) return;
+  if (n > 0) {
     const PV v = pass_view(a.ds);
-    const int64_t n = a.ds->n_deferred;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+         i += (int64_t)parts * blockDim.x) {
       const int32_t e = a.dlist[i];
       const int32_t j = v.act[e];
       a.meta[j].ptr = a.nxt_ptr[e];
@@ -1157,7 +1166,7 @@ __global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph)
       a.meta[j].flags &= (uint8_t)~F_NEWPIV;
     }
   }
-  if (last_block(&a.ds->blocks_done) && threadIdx.x == 0) {
+  if (last_block(&a.ds->blocks_done, parts) && threadIdx.x == 0) {
     a.ds->blocks_done = 0;
     end_of_pass(a, cond, in_graph);
   }
