@@ -81,6 +81,7 @@ struct RArgs {
   int32_t* first_unp;
   const int32_t* seg;
   int64_t rows_end;
+  int nseg;           // (cloud, dim) segments
   int nc;
   int strict;
   int cor10;
@@ -1166,9 +1167,13 @@ __global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph)
       a.meta[j].flags &= (uint8_t)~F_NEWPIV;
     }
   }
-  if (last_block(&a.ds->blocks_done, parts) && threadIdx.x == 0) {
-    a.ds->blocks_done = 0;
-    end_of_pass(a, cond, in_graph);
+  if (last_block(&a.ds->blocks_done, parts)) {
+    // the first unpaired row of each segment is found afresh (atomicMin) by the next pass
+    for (int i = threadIdx.x; i < a.nseg; i += blockDim.x) a.first_unp[i] = INT32_MAX;
+    if (threadIdx.x == 0) {
+      a.ds->blocks_done = 0;
+      end_of_pass(a, cond, in_graph);
+    }
   }
 }
 
@@ -1254,6 +1259,7 @@ static RArgs make_args(ph_ctx* ctx) {
   a.first_unp = rs.first_unp;
   a.seg = ctx->seg;
   a.rows_end = ctx->dimoff[ctx->max_dim];
+  a.nseg = (int)ctx->seg_start.size() - 1;
   a.nc = ctx->n_clouds;
   a.strict = ctx->opts.strict_phase2;
   a.cor10 = ctx->opts.use_cor10;
@@ -1277,15 +1283,19 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
                         bool in_graph, bool time_add, cudaStream_t st) {
   ReduceState& rs = ctx->rs;
   const int sms = ctx->num_sms;
-  const int nseg = (int)ctx->seg_start.size() - 1;
-  PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, nseg * sizeof(int32_t), st));
+  // grids: the full machine for large complexes, no more blocks than the largest active list
+  // (all m columns) can use for small ones, so a small complex's pass costs little
+  const int64_t m = std::max<int64_t>(ctx->m, 1);
+  auto blocks = [&](int64_t full, int64_t per_block) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (m + per_block - 1) / per_block));
+  };
   k_tab_init<<<grid_for(ctx, a.rows_end, kThreads), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_tab<<<sms * 8, kThreads, 0, st>>>(a);
+  k_tab<<<blocks(sms * 8, kThreads), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_p1_tiles<<<sms * 8, kThreads, 0, st>>>(a);
+  k_p1_tiles<<<blocks(sms * 8, kRTile), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_mark<<<sms * 8, kThreads, 0, st>>>(a);
+  k_mark<<<blocks(sms * 8, kThreads), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
   if (ctx->opts.collect_stats) {
     k_ess_count<<<sms * 4, kThreads, 0, st>>>(a, ctx->m);
@@ -1300,10 +1310,11 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
     PH_CUDA(cudaEventRecord(e0, st));
   }
   const int add_bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
-  k_add<<<sms * add_bps * (kThreads / kAddThreads), kAddThreads, kAddSmem, st>>>(a);
+  k_add<<<blocks(sms * add_bps * (kThreads / kAddThreads), kAddThreads), kAddThreads, kAddSmem,
+          st>>>(a);
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
-  k_commit<<<sms * 2, kThreads, 0, st>>>(a, cond, in_graph ? 1 : 0);
+  k_commit<<<blocks(sms * 2, kThreads), kThreads, 0, st>>>(a, cond, in_graph ? 1 : 0);
   PH_CHECK_LAUNCH();
 }
 
@@ -1329,6 +1340,7 @@ void reduce_init(ph_ctx* ctx) {
   rs.tab = alloc_n<int32_t>(ctx, m);
   int nseg = (int)ctx->seg_start.size() - 1;
   rs.first_unp = alloc_n<int32_t>(ctx, nseg);
+  PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, nseg * sizeof(int32_t), st));  // above every id
   int64_t ntiles = (m + kRTile - 1) / kRTile;
   rs.tiles_bytes = ntiles * (1 + kRItems) * sizeof(SegMax);
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
