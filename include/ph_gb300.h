@@ -94,6 +94,13 @@ typedef struct {
    * be paired) holds one row i has lowstar(j) = i, which ph_get_predicted_lows reports before
    * the column is reduced. 0 (default): off. */
   int32_t predict_pairs;
+  /* Bit-packed columns: when a column addition (target + source rows) exceeds
+   * max(dense_threshold, the bitmap's words), the result is kept as a bitmap over the column's
+   * row segment (one bit per (d-1)-simplex of its cloud, after a 1-word header) and later
+   * additions into it XOR whole words; a bit-packed source is XORed word by word. Results are
+   * identical either way. 0 (default): the threshold is 32 rows, so a column goes bit-packed
+   * once the bitmap is its smaller form; < 0: never. */
+  int32_t dense_threshold;
 } ph_opts;
 
 /* Per-pass counters (rows of ph_get_pass_stats), in this order. */
@@ -112,6 +119,8 @@ enum {
   PH_PS_PREDICTED,     /* columns whose pair Corollary 10 (non-zero case) predicts for the first
                         * time (needs predict_pairs) */
   PH_PS_EMPTY_L,       /* columns with an empty candidate set L_j: always 0 (Lemma 9) */
+  PH_PS_PACKED,        /* additions computed on bitmaps (see dense_threshold); a property of
+                        * the storage, not of Algorithm 2 */
   PH_PS_N
 };
 

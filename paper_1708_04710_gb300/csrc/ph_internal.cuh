@@ -102,8 +102,10 @@ struct ReduceState {
   int32_t stats_rows = 0;
   ColStore arena[2];           // pass p writes its survivors into arena[p & 1]
   std::vector<ColStore> pivots;  // chunks holding proven columns
-  cudaGraph_t graph = nullptr;   // one pass as the body of a conditional while node
-  cudaGraphExec_t graph_exec = nullptr;
+  // the pass loop: one pass as the body of a conditional while node; [1] with the additions
+  // kernel that handles bit-packed columns
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   int32_t passes = 0;
   bool init = false;
   bool done = false;

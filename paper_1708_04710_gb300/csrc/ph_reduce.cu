@@ -39,7 +39,7 @@ constexpr int kRItems = 8;
 constexpr int kRTile = kThreads * kRItems;
 
 enum : int32_t { ST_RUN = 0, ST_DONE = 1, ST_CAPPED = 2, ST_HOST = 3, ST_FAULT = 4,
-                 ST_TIMEOUT = 5 };
+                 ST_TIMEOUT = 5, ST_SWITCH = 6 };
 constexpr int kSpinLimit = 1 << 22;  // iterations of a look-back wait before it gives up
 
 struct DevState {
@@ -67,6 +67,11 @@ struct DevState {
   unsigned int queue;             // next chunk for k_add
   int32_t n_deferred;             // entries of dlist
   int32_t fault;                  // a bounded wait ran out
+  // bit-packed columns: the passes after the first one that saw a target that may reach its
+  // threshold run the additions kernel that handles them (and converts columns); the pass loop
+  // stops once there (ST_SWITCH) so that the host continues it with that kernel
+  int32_t dense_on;
+  int32_t dense_want;
 };
 
 struct RArgs {
@@ -90,6 +95,14 @@ struct RArgs {
   unsigned long long* look;  // per 256-entry chunk: look-back state of the survivor count
   int32_t* dlist;     // active slots whose column update waits for k_commit
   int32_t* src_e;     // per active slot: the colliding column's left-most column, -1 if none
+  // bit-packed columns: a job's result is a bitmap over its row segment when the sum of the two
+  // row counts exceeds the threshold, max(the stored bitmap's words, t0) with t0 = dense_mode
+  // when > 0, else 32 (dense_mode < 0: never), or when either column is already a bitmap
+  int dense_mode;
+  int32_t dense_floor;             // no addition of at most this many rows goes bit-packed
+  int32_t dense_min[kMaxDim + 1];  // per column dimension: smallest threshold of its segments
+  int32_t dim_start[kMaxDim + 1];  // first column id of each dimension (m above the top one)
+  const int64_t* seg_start;        // device copy of the segment table
   int predict;        // 1: Corollary 10 non-zero case (pair predictions)
   uint32_t* unp_bits; // per row, bit: not known to be paired at the start of the pass
   int32_t* unp_words; // [nwords + 1] exclusive prefix of unpaired rows per 32-row word
@@ -109,6 +122,7 @@ struct PV {
   int64_t* stats;
   int32_t* arena_next;
   int32_t* piv_base;
+  int dense_on;
 };
 
 __device__ __forceinline__ PV pass_view(const DevState* ds) {
@@ -122,6 +136,7 @@ __device__ __forceinline__ PV pass_view(const DevState* ds) {
   v.stats = ds->stats ? ds->stats + (int64_t)ds->pass * PH_PS_N : nullptr;
   v.arena_next = ds->arena[ds->pass & 1];
   v.piv_base = ds->piv_base;
+  v.dense_on = ds->dense_on;
   return v;
 }
 
@@ -235,6 +250,66 @@ __global__ void k_tab(RArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
+// bit-packed columns
+// ------------------------------------------------------------------------------------------
+// the smallest threshold over the segments of column j's dimension (fixed indices only: a
+// kernel parameter array indexed at run time would be copied out)
+__device__ __forceinline__ int32_t dense_min_of(const RArgs& a, int32_t j) {
+  int32_t t = a.dense_min[0];
+#pragma unroll
+  for (int k = 1; k <= kMaxDim; k++) t = j >= a.dim_start[k] ? a.dense_min[k] : t;
+  return t;
+}
+
+// first column id of column j's dimension
+__device__ __forceinline__ int32_t dim_start_of(const RArgs& a, int32_t j) {
+  int32_t b = 0;
+#pragma unroll
+  for (int k = 1; k <= kMaxDim; k++) b = j >= a.dim_start[k] ? a.dim_start[k] : b;
+  return b;
+}
+// the smallest threshold over the dimensions of the columns j0..j1 (none: INT32_MAX)
+__device__ __forceinline__ int32_t dense_min_between(const RArgs& a, int32_t j0, int32_t j1) {
+  int32_t t = INT32_MAX;
+#pragma unroll
+  for (int k = 0; k <= kMaxDim; k++) {
+    const int32_t end = k < kMaxDim ? a.dim_start[k + 1] : INT32_MAX;
+    if (j0 <= j1 && a.dim_start[k] <= j1 && end > j0) t = min(t, a.dense_min[k]);
+  }
+  return t;
+}
+
+// row segment of column j: first row id and bitmap words
+__device__ __forceinline__ void row_segment(const RArgs& a, int32_t j, int64_t& base,
+                                            int32_t& words) {
+  const int rs = a.seg[j] - a.nc;
+  base = a.seg_start[rs];
+  words = (int32_t)((a.seg_start[rs + 1] - base + 31) / 32);
+}
+
+// A bit-packed column is stored as one header word (its row count) followed by the bitmap, bit
+// r - base of word (r - base) / 32 for row r of the segment. Its length field holds
+// -(stored words) - 1, so a plain length load tells the two forms apart, and the stored words of
+// either form are what a move of the column takes: Phase I reserves that much for it.
+constexpr int kDenseHead = 1;
+__device__ __forceinline__ int32_t stored_words(int32_t len) { return len < 0 ? -len - 1 : len; }
+__device__ __forceinline__ int32_t dense_len(int32_t words) { return -words - 1; }
+
+// does an addition of n rows in all (target + source) into column j produce a bitmap? The
+// stored bitmap is smaller than n, so it fits the n words Phase I reserved for the result
+__device__ __noinline__ bool goes_dense_slow(const RArgs& a, int32_t j, int64_t n) {
+  int64_t base;
+  int32_t words;
+  row_segment(a, j, base, words);
+  return n > max(words + kDenseHead, a.dense_mode > 0 ? a.dense_mode : 32);
+}
+// the cheap part first: no bitmap at or below the floor, nor below every segment of j's dimension
+__device__ __forceinline__ bool goes_dense(const RArgs& a, int32_t j, int64_t n) {
+  return n > a.dense_floor && n > dense_min_of(a, j) && goes_dense_slow(a, j, n);
+}
+
+
+// ------------------------------------------------------------------------------------------
 // Phase I scan
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ SegMax p1_value(const RArgs& a, const PV& v, int64_t e) {
@@ -320,8 +395,19 @@ __global__ void k_p1_tiles(RArgs a) {
   if (blockIdx.x >= parts) return;
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   int64_t bw = 0, bp = 0;
+  bool want = false;  // a target whose addition may reach its dimension's bit-packing threshold
   for (int64_t t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
     const int64_t tile0 = t * kRTile;
+    // bit-packing thresholds of the tile's columns (ascending ids, so dimensions too): exact in
+    // the top dimension (ids from t_b on), the smallest of the others below it
+    int32_t t_b = 0, t_hi = INT32_MAX, t_lo = INT32_MAX;
+    if (a.dense_floor != INT32_MAX) {
+      const int32_t j0 = v.act[tile0];
+      const int32_t j1 = v.act[min(tile0 + kRTile, v.n_act) - 1];
+      t_b = dim_start_of(a, j1);
+      t_hi = dense_min_of(a, j1);
+      t_lo = dense_min_between(a, j0, t_b - 1);
+    }
     // every load of the tile's kRItems slots per thread is issued before any is used
     int32_t j[kRItems], l[kRItems], sg[kRItems], n[kRItems];
 #pragma unroll
@@ -339,9 +425,15 @@ __global__ void k_p1_tiles(RArgs a) {
     for (int it = 0; it < kRItems; it++) {
       const int32_t s = l[it] >= 0 ? a.tab[l[it]] : -1;
       const bool collide = l[it] >= 0 && s != j[it];
-      bw += n[it];
-      if (collide) bw += a.meta[s].len;  // a target: its source may be added
-      else if (l[it] >= 0) bp += n[it];  // left-most: it may be proven and move
+      // a column's reservation is its stored words: its rows, or its bitmap with the header
+      bw += stored_words(n[it]);
+      if (collide) {  // a target: its source may be added
+        const int32_t ns = stored_words(a.meta[s].len);
+        bw += ns;
+        want |= n[it] + ns > (j[it] >= t_b ? t_hi : t_lo);
+      } else if (l[it] >= 0) {
+        bp += stored_words(n[it]);  // left-most: it may be proven and move
+      }
       // Phase I value: the low of a colliding column, in its (cloud, dim) segment
       SegMax val{sg[it], collide ? l[it] : -1};
 #pragma unroll
@@ -366,6 +458,7 @@ __global__ void k_p1_tiles(RArgs a) {
     }
     __syncthreads();
   }
+  if (want && !v.dense_on) a.ds->dense_want = 1;  // bit-packed additions from the next pass
   int64_t tw, tp;
   block_excl_sum<int64_t>(bw, shs, tw);
   block_excl_sum<int64_t>(bp, shs, tp);
@@ -446,6 +539,60 @@ __global__ void k_mark(RArgs a) {
 // ------------------------------------------------------------------------------------------
 // what happens to an active column in Phase II
 // ------------------------------------------------------------------------------------------
+// One job by the whole warp on bitmaps: column A (rows, or a bit-packed column if dense_a) plus
+// source B (likewise, dense_b) into the bit-packed column T, the job's reserved slot. Writes
+// T's header and returns its row count; its largest row goes to low, its stored words to words.
+__device__ __noinline__ int32_t dense_job_warp(const RArgs& a, int32_t j, const int32_t* A,
+                                              int na, bool dense_a, const int32_t* B, int nb,
+                                              bool dense_b, int32_t* T, int32_t& low,
+                                              int32_t& words) {
+  const int lane = lane_id();
+  int64_t base;
+  int32_t W;
+  row_segment(a, j, base, W);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(T + kDenseHead);
+  const uint32_t* Ab = reinterpret_cast<const uint32_t*>(A + kDenseHead);
+  const uint32_t* Bb = reinterpret_cast<const uint32_t*>(B + kDenseHead);
+  const bool wb = B != nullptr && dense_b;
+  for (int w = lane; w < W; w += 32) bits[w] = (dense_a ? Ab[w] : 0u) ^ (wb ? Bb[w] : 0u);
+  __syncwarp();
+  // the row lists, scattered bit by bit (rows of one list are distinct; the lists may share)
+  if (!dense_a)
+    for (int q = lane; q < na; q += 32) {
+      const int64_t r = A[q] - base;
+      atomicXor(bits + (r >> 5), 1u << (r & 31));
+    }
+  if (B != nullptr && !dense_b)
+    for (int q = lane; q < nb; q += 32) {
+      const int64_t r = B[q] - base;
+      atomicXor(bits + (r >> 5), 1u << (r & 31));
+    }
+  __syncwarp();
+  // rows and the largest row of the result (read from L2, where the atomics landed)
+  int cnt = 0, top_w = -1;
+  uint32_t top_bits = 0;
+  for (int w = lane; w < W; w += 32) {
+    const uint32_t x = __ldcg(bits + w);
+    cnt += __popc(x);
+    if (x) {
+      top_w = w;
+      top_bits = x;
+    }
+  }
+  const int best = __reduce_max_sync(0xffffffffu, (unsigned)(top_w + 1)) - 1;
+  const unsigned who = __ballot_sync(0xffffffffu, top_w == best && best >= 0);
+  low = -1;
+  if (best >= 0) {
+    const uint32_t tb = __shfl_sync(0xffffffffu, top_bits, __ffs(who) - 1);
+    low = (int32_t)(base + 32 * (int64_t)best + 31 - __clz(tb));
+  }
+  const int32_t rows = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+  if (lane == 0) T[0] = rows;
+  __syncwarp();
+  words = W + kDenseHead;
+  return rows;
+}
+
 struct Job {
   int32_t j;
   int32_t src;    // source column for an addition, -1 if none
@@ -456,10 +603,13 @@ struct Job {
   const int32_t* A;  // the column's rows (new pivots and survivors)
   const int32_t* B;  // the source's rows (additions)
   int na, nb;
+  bool dense_a, dense_b;  // A / B is a bit-packed column (na / nb are then its stored words)
 };
 
+// kDense: columns may be bit-packed (the length field tells); otherwise every column is a row list
+template <bool kDense>
 __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
-  Job jb{-1, -1, false, false, false, 0, nullptr, nullptr, 0, 0};
+  Job jb{-1, -1, false, false, false, 0, nullptr, nullptr, 0, 0, false, false};
   if (e >= v.n_act) return jb;
   // every load is issued up front: the column and its source candidate are known from the
   // active list and k_mark's per-slot source, so no load waits on another's result
@@ -468,7 +618,7 @@ __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
   const ColMeta mj = load_meta(a.meta + j);  // one 16-byte load per column
   const uint8_t f = mj.flags;
   const uint8_t cj = mj.cleared;
-  const int32_t nj = mj.len;
+  const int32_t nj = kDense ? stored_words(mj.len) : mj.len;
   const int32_t* pj = mj.ptr;
   uint8_t fs = 0, cs = 0;
   int32_t ns = 0;
@@ -489,15 +639,17 @@ __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
       jb.target = true;
       if (v.do_adds && !(fs & F_FINAL) && !cs && (!a.strict || (fs & F_PROVEN))) {
         jb.src = s;
-        jb.words += ns;
+        jb.dense_b = kDense && ns < 0;
+        jb.nb = kDense ? stored_words(ns) : ns;
+        jb.words += jb.nb;
         jb.B = ps;
-        jb.nb = ns;
       }
     }
   }
   if (jb.newpiv || jb.surv) {
     jb.A = pj;
     jb.na = nj;
+    jb.dense_a = kDense && mj.len < 0;
   }
   return jb;
 }
@@ -859,7 +1011,9 @@ __device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p
 // longer than the staging bound run from global memory. Targets and zeroed columns are updated
 // in place (no other job reads them this pass); new pivots and left-most survivors, which other
 // jobs may be reading as sources, are updated by k_commit.
-enum : int { kCntTargets, kCntActive, kCntCleared, kCntAdds, kCntXors, kCntCopied, kNumCnt };
+enum : int {
+  kCntTargets, kCntActive, kCntCleared, kCntAdds, kCntXors, kCntCopied, kCntPacked, kNumCnt
+};
 
 __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
 #pragma unroll
@@ -867,12 +1021,13 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
   return v;
 }
 
+template <bool kDense>
 __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
                                           WarpStage& S, int64_t* sh, int64_t* s_prefix,
                                           unsigned long long* s_cnt) {
   const int lane = lane_id();
   const int64_t e = chunk * kAddThreads + threadIdx.x;
-  Job jb = job_of(a, v, e);
+  Job jb = job_of<kDense>(a, v, e);
   // one block scan gives both the survivor rank (high 16 bits) and the arena words (low 48)
   constexpr int kRankShift = 48;
   constexpr int64_t kWordMask = (int64_t(1) << kRankShift) - 1;
@@ -899,7 +1054,8 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   int32_t* o_ptr = nullptr;  // the column's new place and length
   int o_len = 0;
 
-  // ---- new pivots: their columns never change again; move them to the pivot store
+  // ---- new pivots: their columns never change again; move them to the pivot store (a
+  // bit-packed column moves as its stored words)
   unsigned pmask = __ballot_sync(0xffffffffu, jb.newpiv);
   while (pmask) {
     const int src = __ffs(pmask) - 1;
@@ -913,7 +1069,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     for (int q = lane; q < wna; q += 32) dst[q] = wA[q];
     if (lane == src) {
       o_ptr = dst;
-      o_len = wna;
+      o_len = kDense && jb.dense_a ? dense_len(wna) : wna;
     }
   }
 
@@ -925,8 +1081,12 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   // most of the warp takes it; a few short jobs among long ones would keep the rest of the warp
   // waiting, so they join the staged path instead. One network size serves the whole warp.
   const int need = max(na, nb);
-  int cls = !jb.surv ? 0 : (need <= 16 ? 1 : 3);
-  if (__popc(__ballot_sync(0xffffffffu, cls == 1)) < 12 && cls != 0) cls = 3;
+  // cls 4: bit-packed (the column is, or the source is, or the sum exceeds the threshold)
+  const bool dense_job =
+      kDense && jb.surv &&
+      (jb.dense_a || (B != nullptr && (jb.dense_b || goes_dense(a, jb.j, N))));
+  int cls = !jb.surv ? 0 : (dense_job ? 4 : (need <= 16 ? 1 : 3));
+  if (__popc(__ballot_sync(0xffffffffu, cls == 1)) < 12 && cls == 1) cls = 3;
   const unsigned wneed = __reduce_max_sync(0xffffffffu, cls == 1 ? (unsigned)need : 0u);
   if (cls == 1) {
     int32_t last;
@@ -1034,6 +1194,35 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       }
     }
   }
+  // ---- bit-packed columns, one job at a time by the whole warp
+  unsigned dnmask = kDense ? __ballot_sync(0xffffffffu, cls == 4) : 0u;
+  while (dnmask) {
+    const int src = __ffs(dnmask) - 1;
+    dnmask &= dnmask - 1;
+    const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src);
+    const int32_t* wB = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)B, src);
+    const int wna = __shfl_sync(0xffffffffu, na, src);
+    int32_t* wd = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)slot, src);
+    const bool wdense_a = __shfl_sync(0xffffffffu, (int)jb.dense_a, src) != 0;
+    if (wB == nullptr) {  // a bit-packed column with nothing to add moves as it is
+      for (int q = lane; q < wna; q += 32) wd[q] = wA[q];
+      if (lane == src) {
+        o_ptr = wd;
+        o_len = dense_len(wna);
+      }
+      continue;
+    }
+    int32_t low, words;
+    const int32_t rows = dense_job_warp(a, __shfl_sync(0xffffffffu, jb.j, src), wA, wna, wdense_a,
+                                        wB, __shfl_sync(0xffffffffu, nb, src),
+                                        __shfl_sync(0xffffffffu, (int)jb.dense_b, src) != 0, wd,
+                                        low, words);
+    if (lane == src) {
+      o_ptr = wd;
+      o_len = rows ? dense_len(words) : 0;  // a zero column stores nothing
+      a.low[jb.j] = low;
+    }
+  }
   // ---- the survivors' places in the next active list
   if (threadIdx.x < 32) {
     const int64_t pre = look_back(a, pass, chunk, n_surv);
@@ -1073,18 +1262,27 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     const int n_act = __popc(__ballot_sync(0xffffffffu, jb.j >= 0));
     const int n_clr = __popc(__ballot_sync(0xffffffffu, jb.j >= 0 && a.meta[jb.j].cleared));
     const int n_add = __popc(__ballot_sync(0xffffffffu, add));
-    const int64_t xr = warp_sum64(add ? (na + nb + o_len) / 2 : 0);
-    const int64_t cp = warp_sum64(copy ? na : 0);
+    const int n_pk = kDense ? __popc(__ballot_sync(0xffffffffu, add && cls == 4)) : 0;
+    // row counts: a bit-packed column keeps its own in its header
+    const int ra = kDense && jb.dense_a ? A[0] : na;
+    const int64_t xr = warp_sum64(
+        add ? (ra + (kDense && jb.dense_b ? B[0] : nb) + (kDense && o_len < 0 ? o_ptr[0] : o_len)) / 2
+            : 0);
+    const int64_t cp = warp_sum64(copy ? ra : 0);
     if (lane == 0) {
       atomicAdd(&s_cnt[kCntActive], (unsigned long long)n_act);
       atomicAdd(&s_cnt[kCntCleared], (unsigned long long)n_clr);
       atomicAdd(&s_cnt[kCntAdds], (unsigned long long)n_add);
       atomicAdd(&s_cnt[kCntXors], (unsigned long long)xr);
       atomicAdd(&s_cnt[kCntCopied], (unsigned long long)cp);
+      if (n_pk) atomicAdd(&s_cnt[kCntPacked], (unsigned long long)n_pk);
     }
   }
 }
 
+// kDense: the pass may meet bit-packed columns or convert some (the graph's if / else node, or
+// the host, picks the variant from DevState::dense_on); the row-list variant carries none of it
+template <bool kDense>
 __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   __shared__ int64_t sh[kAddWarps + 1];
   __shared__ int64_t s_chunk;
@@ -1104,12 +1302,12 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
     const int64_t nchunks = (v.n_act + kAddThreads - 1) / kAddThreads;
     __syncthreads();
     if (chunk >= nchunks) break;
-    add_chunk(a, v, chunk, S, sh, s_prefix, s_cnt);
+    add_chunk<kDense>(a, v, chunk, S, sh, s_prefix, s_cnt);
   }
   if (threadIdx.x == 0 && s_cnt[kCntTargets]) atomicAdd(&a.ds->totals[1], s_cnt[kCntTargets]);
   if (v.stats && threadIdx.x == 0) {
     const int idx[kNumCnt] = {PH_PS_TARGETS, PH_PS_ACTIVE, PH_PS_CLEARED,
-                              PH_PS_ADDS,    PH_PS_XORS,   PH_PS_COPIED};
+                              PH_PS_ADDS,    PH_PS_XORS,   PH_PS_COPIED, PH_PS_PACKED};
     for (int i = 0; i < kNumCnt; i++)
       if (s_cnt[i]) atomicAdd((unsigned long long*)&v.stats[idx[i]], s_cnt[i]);
   }
@@ -1191,6 +1389,8 @@ __global__ void k_clock_start(DevState* ds) { ds->t_start = global_ns(); }
 __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int in_graph) {
   DevState* ds = a.ds;
   if (ds->status == ST_RUN && ds->fault) ds->status = ST_FAULT;
+  const bool to_dense = ds->dense_want && !ds->dense_on;
+  if (to_dense) ds->dense_on = 1;
   if (ds->status == ST_RUN) {
     const int32_t p = ds->pass;
     ds->n_act = (int64_t)ds->totals[0];
@@ -1207,6 +1407,7 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
       ds->pass = p + 1;
       // the pass is complete, so a later call can resume from the next one
       if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
+      else if (to_dense) ds->status = ST_SWITCH;  // continued with the bit-packing kernel
     }
   }
   if (in_graph) cudaGraphSetConditional(cond, ds->status == ST_RUN ? 1u : 0u);
@@ -1275,12 +1476,30 @@ static RArgs make_args(ph_ctx* ctx) {
   a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
                                                  : kStage;
   a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
+  // bit-packed columns: per column dimension the smallest threshold over its row segments
+  a.dense_mode = ctx->opts.dense_threshold;
+  a.seg_start = ctx->d_seg_start;
+  for (int d = 0; d <= kMaxDim; d++)
+    a.dim_start[d] = (int32_t)(d <= ctx->max_dim ? ctx->dimoff[d] : ctx->m);
+  const int64_t t0 = a.dense_mode > 0 ? a.dense_mode : 32;
+  a.dense_floor = INT32_MAX;
+  for (int d = 0; d <= kMaxDim; d++) {
+    int64_t mn = INT32_MAX;
+    for (int c = 0; a.dense_mode >= 0 && d >= 1 && d <= ctx->max_dim && c < ctx->n_clouds; c++) {
+      const int rs = (d - 1) * ctx->n_clouds + c;
+      const int64_t n = ctx->seg_start[rs + 1] - ctx->seg_start[rs];
+      if (n > 0) mn = std::min<int64_t>(mn, std::max<int64_t>((n + 31) / 32 + kDenseHead, t0));
+    }
+    a.dense_min[d] = (int32_t)std::min<int64_t>(mn, INT32_MAX);
+    a.dense_floor = std::min(a.dense_floor, a.dense_min[d]);
+  }
   return a;
 }
 
 // the kernels of one pass, in order; grids are fixed (persistent blocks loop over the work)
+// dense_on: the additions kernel that handles bit-packed columns (DevState::dense_on)
 static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
-                        bool in_graph, bool time_add, cudaStream_t st) {
+                        bool in_graph, bool dense_on, bool time_add, cudaStream_t st) {
   ReduceState& rs = ctx->rs;
   const int sms = ctx->num_sms;
   // grids: the full machine for large complexes, no more blocks than the largest active list
@@ -1310,8 +1529,11 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
     PH_CUDA(cudaEventRecord(e0, st));
   }
   const int add_bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
-  k_add<<<blocks(sms * add_bps * (kThreads / kAddThreads), kAddThreads), kAddThreads, kAddSmem,
-          st>>>(a);
+  const unsigned add_grid = blocks(sms * add_bps * (kThreads / kAddThreads), kAddThreads);
+  if (dense_on)
+    k_add<true><<<add_grid, kAddThreads, kAddSmem, st>>>(a);
+  else
+    k_add<false><<<add_grid, kAddThreads, kAddSmem, st>>>(a);
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
   k_commit<<<blocks(sms * 2, kThreads), kThreads, 0, st>>>(a, cond, in_graph ? 1 : 0);
@@ -1399,7 +1621,9 @@ void reduce_init(ph_ctx* ctx) {
   h.pass = 0;
   h.status = ST_RUN;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  PH_CUDA(cudaFuncSetAttribute(k_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PH_CUDA(cudaFuncSetAttribute(k_add<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kAddSmem));
+  PH_CUDA(cudaFuncSetAttribute(k_add<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kAddSmem));
   rs.passes = 0;
   rs.init = true;
@@ -1442,7 +1666,9 @@ static void serve_host_request(ph_ctx* ctx, DevState& h) {
   h.status = ST_RUN;
 }
 
-static void build_graph(ph_ctx* ctx, const RArgs& a) {
+// the pass loop as one graph: a conditional while node around one pass (dense: with the
+// additions kernel that handles bit-packed columns)
+static void build_graph(ph_ctx* ctx, const RArgs& a, bool dense) {
   ReduceState& rs = ctx->rs;
   cudaGraph_t g;
   PH_CUDA(cudaGraphCreate(&g, 0));
@@ -1469,7 +1695,7 @@ static void build_graph(ph_ctx* ctx, const RArgs& a) {
   }
   const int64_t counted = ctx->launches;  // captured launches run later, counted per pass
   try {
-    launch_pass(ctx, a, cond, true, false, cs);
+    launch_pass(ctx, a, cond, true, dense, false, cs);
     ctx->launches = counted;
   } catch (...) {
     cudaStreamEndCapture(cs, &body);
@@ -1483,8 +1709,8 @@ static void build_graph(ph_ctx* ctx, const RArgs& a) {
   PH_CUDA(ce);
   cudaGraphExec_t exec;
   PH_CUDA(cudaGraphInstantiate(&exec, g, 0));
-  rs.graph = g;
-  rs.graph_exec = exec;
+  rs.graph[dense] = g;
+  rs.graph_exec[dense] = exec;
 }
 
 int reduce_run(ph_ctx* ctx, int32_t max_passes) {
@@ -1511,13 +1737,15 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   k_clock_start<<<1, 1, 0, st>>>(static_cast<DevState*>(rs.dstate));
   PH_CHECK_LAUNCH();
   const RArgs a = make_args(ctx);
-  if (use_graph && !rs.graph_exec) build_graph(ctx, a);
+
   for (;;) {
     const int32_t first_pass = h.pass;
     if (use_graph) {
-      PH_CUDA(cudaGraphLaunch(rs.graph_exec, st));
+      const bool dense = h.dense_on != 0;
+      if (!rs.graph_exec[dense]) build_graph(ctx, a, dense);
+      PH_CUDA(cudaGraphLaunch(rs.graph_exec[dense], st));
     } else {
-      launch_pass(ctx, a, 0, false, time_add, st);
+      launch_pass(ctx, a, 0, false, h.dense_on != 0, time_add, st);
       if (time_add) rs.add_launches++;
     }
     PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
@@ -1528,6 +1756,11 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
       ctx->launches += per_pass * (int64_t)(last - first_pass + 1);
     }
     if (h.status == ST_RUN) continue;
+    if (h.status == ST_SWITCH) {  // the next pass on, with the bit-packing additions kernel
+      h.status = ST_RUN;
+      PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+      continue;
+    }
     if (h.status == ST_HOST) {
       if (time_add && rs.ev.size() >= 2) {  // the stopped pass's k_add did no work
         cudaEventDestroy(rs.ev.back());
@@ -1630,8 +1863,10 @@ void predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* host_out, int64_t n) {
 
 void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
-  if (rs.graph_exec) cudaGraphExecDestroy(rs.graph_exec);
-  if (rs.graph) cudaGraphDestroy(rs.graph);
+  for (int d = 0; d < 2; d++) {
+    if (rs.graph_exec[d]) cudaGraphExecDestroy(rs.graph_exec[d]);
+    if (rs.graph[d]) cudaGraphDestroy(rs.graph[d]);
+  }
   for (void* p : {(void*)rs.act, (void*)rs.act2, rs.meta,
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
                   (void*)rs.first_unp, rs.tiles, rs.dstate,

@@ -17,7 +17,7 @@ LIB_PATH = Path(__file__).resolve().parent / "libph_gb300.so"
 
 PH_OK, PH_NOT_CONVERGED = 0, 1
 PS_FIELDS = ("active", "new_pivots", "zero_final", "cor10", "cleared", "targets", "adds",
-             "xors", "copied", "ess_est", "predicted", "empty_l")
+             "xors", "copied", "ess_est", "predicted", "empty_l", "packed")
 
 
 class PHError(RuntimeError):
@@ -31,7 +31,7 @@ class PhOpts(Structure):
                 ("staged_merge_max", c_int32), ("merge_items", c_int32),
                 ("collect_stats", c_int32), ("use_graph", c_int32), ("time_kernels", c_int32),
                 ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32),
-                ("predict_pairs", c_int32)]
+                ("predict_pairs", c_int32), ("dense_threshold", c_int32)]
 
 
 class PhStats(Structure):
@@ -124,7 +124,7 @@ class Context:
     def __init__(self, *, strict_phase2: bool = False, use_cor10: bool = True,
                  collect_stats: bool = False, staged_merge_max: int = 0, merge_items: int = 0,
                  use_graph: bool = True, time_kernels: bool = False, add_blocks_per_sm: int = 0,
-                 timeout_ms: int = 0, predict_pairs: bool = False,
+                 timeout_ms: int = 0, predict_pairs: bool = False, dense_threshold: int = 0,
                  stream=None):
         torch = _torch()
         self._torch = torch
@@ -142,6 +142,7 @@ class Context:
         opts.add_blocks_per_sm = int(add_blocks_per_sm)
         opts.timeout_ms = int(timeout_ms)
         opts.predict_pairs = int(predict_pairs)
+        opts.dense_threshold = int(dense_threshold)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
         dev_index = self.device.index if self.device.index is not None else 0

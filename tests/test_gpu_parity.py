@@ -190,6 +190,82 @@ def test_merge_paths_agree(ph, orc, staged_max, items, bps):
     assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
 
 
+# bit-packed columns: small clouds built to high dimension have short row segments, so their
+# columns fill in past the bitmap's size and additions run on bitmaps (dense + sparse and
+# dense + dense); the results and every counter of Algorithm 2 stay the oracle's
+DENSE_CASES = [
+    ("gauss_3d_dim4", lambda: pc.random_cloud(11, 3, 31), 4, -1),
+    ("gauss_2d_dim3", lambda: pc.random_cloud(14, 2, 2), 3, -1),
+    ("gauss_3d_dim5", lambda: pc.random_cloud(15, 3, 32), 5, -1),
+    ("lattice_dim4_ties", lambda: pc.lattice_cloud(14, 3, 34, side=3), 4, -1),
+    ("circle40", pc.circle40, 2, -1),
+    ("gauss_4d_dim5_cut", lambda: pc.random_cloud(16, 4, 33), 5, int(2.0 * 65536 ** 2)),
+]
+
+
+@pytest.mark.parametrize("threshold", [1, 0, 24])
+@pytest.mark.parametrize("name,gen,max_dim,cut", DENSE_CASES, ids=[c[0] for c in DENSE_CASES])
+def test_bit_packed_columns(ph, orc, name, gen, max_dim, cut, threshold):
+    x = gen()
+    K = orc.vr_build(x, max_dim, cut)
+    packed = []
+    for use_graph in (False, True):
+        ctx = _gpu(ph, x, max_dim, cut, dense_threshold=threshold, use_graph=use_graph)
+        st = ctx.reduce()
+        assert st["converged"]
+        ref = _check_reduced(orc, ctx, 0, K)
+        assert st["passes"] == ref.passes
+        _check_counters(ctx, ref)
+        packed.append(ctx.pass_stats()[:, 12])
+        assert packed[-1].sum() <= ref.stats[:, 6].sum()
+    # the switch to bit-packing happens at the same pass in the graph and host-driven loops
+    assert np.array_equal(packed[0], packed[1])
+    if threshold == 1 and name in ("gauss_3d_dim4", "gauss_2d_dim3", "gauss_3d_dim5"):
+        assert packed[0].sum() > 0, "no addition ran on bitmaps"
+
+
+def test_bit_packed_columns_larger_complex(ph, orc):
+    # 24 points to dimension 4 (55,454 simplices over several blocks): edge and triangle
+    # segments are short enough that many columns go bit-packed, and bit-packed columns are
+    # added to each other, moved, proven and cleared over many passes
+    x = pc.random_cloud(24, 3, 77)
+    K = orc.vr_build(x, 4)
+    ref = orc.reduce_pms(K)
+    ctx = _gpu(ph, x, 4, dense_threshold=1)
+    st = ctx.reduce()
+    assert st["passes"] == ref.passes
+    assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+    _check_counters(ctx, ref)
+    assert ctx.pass_stats()[:, 12].sum() > 0
+
+
+@pytest.mark.parametrize("strict,cor10", [(True, True), (False, False)])
+def test_bit_packed_columns_modes_and_batches(ph, orc, strict, cor10):
+    import torch
+
+    # a batch of clouds of different sizes (row segments, so bitmap sizes, differ per cloud)
+    sizes = [9, 14, 3, 12, 1, 11]
+    clouds = [pc.random_cloud(n, 3, 200 + i) for i, n in enumerate(sizes)]
+    x = np.concatenate(clouds)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ctx = _gpu(ph, x, 4, offsets=off, dense_threshold=1, strict_phase2=strict, use_cor10=cor10)
+    ctx.reduce()
+    assert ctx.pass_stats()[:, 12].sum() > 0
+    for c, xc in enumerate(clouds):
+        _check_reduced(orc, ctx, c, orc.vr_build(xc, 4), strict=strict, cor10=cor10)
+    # the paper's ensemble grid at dimension 5, partial and full
+    xe = pc.ensemble15("sphere_product15")
+    K = orc.vr_build(xe, 5, scale_step=32768, n_scales=10)
+    for mp in (2, -1):
+        ref = orc.reduce_pms(K, strict=strict, cor10=cor10, **({} if mp < 0 else {"max_passes": mp}))
+        ctx = ph.Context(collect_stats=True, strict_phase2=strict, use_cor10=cor10,
+                         dense_threshold=1)
+        ctx.build_filtration_scales(torch.from_numpy(xe).cuda(), None, 5, 32768, 10)
+        ctx.reduce(max_passes=mp)
+        assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+        _check_counters(ctx, ref)
+
+
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_batched_clouds(ph, orc, use_graph):
     sizes = [1, 2, 3, 17, 40, 5, 60, 33]
