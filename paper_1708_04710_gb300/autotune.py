@@ -1,12 +1,17 @@
 """Autotuner for the Phase II addition kernel.
 
-Three knobs shape the hot loop: how long a merge may be and still be staged in shared memory
-(``staged_merge_max``, the threshold between the staged and the straight-from-memory merge),
-how many merge-path positions a lane takes (``merge_items``, 0 = chosen per warp), and how many
-persistent blocks per SM the kernel runs (``add_blocks_per_sm``, the grid shape). The tuner times
-full reductions of the caller's own filtration, one knob at a time (coordinate descent from the
-library defaults), and caches the winner per GPU model and workload class in a JSON file
-(``$PH_GB300_CACHE`` or ``~/.cache/ph_gb300/autotune.json``).
+Four knobs shape the hot loop:
+- ``staged_merge_max``: the longest merge that is still staged in shared memory (the threshold
+  between the staged and the straight-from-memory merge);
+- ``merge_items``: merge-path positions per lane (0 = chosen per warp);
+- ``add_blocks_per_sm``: persistent blocks per SM (the grid shape);
+- ``dense_threshold``: when a column's addition goes bit-packed (0 = as soon as the bitmap is
+  the smaller form and the sum exceeds 32 rows, -1 = never, t > 0 = beyond max(bitmap words + 1,
+  t) rows), the row-list to bitmap switch.
+The tuner times full reductions of the caller's own filtration, one knob at a time (coordinate
+descent from the library defaults), and caches the winner per GPU model and workload class in a
+JSON file (``$PH_GB300_CACHE`` or ``~/.cache/ph_gb300/autotune.json``). Every option gives the
+same results; only the time differs.
 """
 from __future__ import annotations
 
@@ -22,8 +27,10 @@ KNOBS = {
     "staged_merge_max": (1024, 512, 256),
     "merge_items": (0, 4, 8, 16),
     "add_blocks_per_sm": (4, 3, 2),
+    "dense_threshold": (0, -1, 128, 1024),
 }
-DEFAULTS = {"staged_merge_max": 1024, "merge_items": 0, "add_blocks_per_sm": 4}
+DEFAULTS = {"staged_merge_max": 1024, "merge_items": 0, "add_blocks_per_sm": 4,
+            "dense_threshold": 0}
 
 
 def cache_path() -> Path:
