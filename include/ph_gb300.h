@@ -101,6 +101,12 @@ typedef struct {
    * identical either way. 0 (default): the threshold is 32 rows, so a column goes bit-packed
    * once the bitmap is its smaller form; < 0: never. */
   int32_t dense_threshold;
+  /* Phase II work shape: while the active list holds at least this many columns, a block of 4
+   * warps claims 128 columns at a time (one block scan and barrier per chunk); below it every
+   * warp claims its own 32 columns (no block barriers, 4x the queue atomics). The list only
+   * shrinks, so a reduction switches at most once. Results are identical either way.
+   * 0 (default): 4,194,304; < 0: block chunks throughout. */
+  int32_t warp_chunks_below;
 } ph_opts;
 
 /* Per-pass counters (rows of ph_get_pass_stats), in this order. */

@@ -279,6 +279,7 @@ void ph_default_opts(ph_opts* o) {
   o->timeout_ms = 0;
   o->predict_pairs = 0;
   o->dense_threshold = 0;
+  o->warp_chunks_below = 0;
 }
 
 int ph_create(ph_ctx** out, const ph_opts* opts, const ph_allocator* alloc, void* stream) {

@@ -102,10 +102,10 @@ struct ReduceState {
   int32_t stats_rows = 0;
   ColStore arena[2];           // pass p writes its survivors into arena[p & 1]
   std::vector<ColStore> pivots;  // chunks holding proven columns
-  // the pass loop: one pass as the body of a conditional while node; [1] with the additions
-  // kernel that handles bit-packed columns
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  // the pass loop: one pass as the body of a conditional while node, per variant of the
+  // additions kernel (+1 bit-packed columns, +2 one chunk per warp)
+  cudaGraph_t graph[4] = {};
+  cudaGraphExec_t graph_exec[4] = {};
   int32_t passes = 0;
   bool init = false;
   bool done = false;

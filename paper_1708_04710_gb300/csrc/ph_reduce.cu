@@ -50,7 +50,9 @@ struct DevState {
   int64_t arena_cap[2];
   int32_t* piv_base;  // current chunk of the pivot store
   int64_t piv_cap;
-  unsigned long long piv_used;
+  // counters that many blocks update by atomics each sit on their own 128-byte line, so that
+  // different L2 slices serve them
+  alignas(128) unsigned long long piv_used;
   int64_t* stats;  // [stats_rows][PH_PS_N] or nullptr
   int32_t stats_rows;
   int32_t pass;
@@ -61,17 +63,22 @@ struct DevState {
   unsigned int blocks_done;       // blocks of the current grid that have finished (last-block)
   unsigned long long t_start;     // global timer (ns) when this ph_reduce's loop began
   unsigned long long t_limit;     // ns the loop may run before it stops with ST_TIMEOUT
-  unsigned long long totals[2];  // survivors and targets of the current pass
+  alignas(128) unsigned long long totals[2];  // survivors and targets of the current pass
   unsigned long long bound_words, bound_piv;
-  unsigned long long arena_used;  // words taken in the arena of the current pass
-  unsigned int queue;             // next chunk for k_add
-  int32_t n_deferred;             // entries of dlist
-  int32_t fault;                  // a bounded wait ran out
+  alignas(128) unsigned long long arena_used;  // words taken in the arena of the current pass
+  alignas(128) unsigned int queue;             // next chunk for k_add
+  alignas(128) int32_t n_deferred;             // entries of dlist
+  alignas(128) int32_t fault;                  // a bounded wait ran out
   // bit-packed columns: the passes after the first one that saw a target that may reach its
   // threshold run the additions kernel that handles them (and converts columns); the pass loop
   // stops once there (ST_SWITCH) so that the host continues it with that kernel
   int32_t dense_on;
   int32_t dense_want;
+  // Phase II work shape: 128-slot chunks per block while the active list is long, 32-slot
+  // chunks per warp (no block barriers, more queue atomics) once it holds fewer than warp_below
+  // columns; the list only shrinks, so this also switches once (ST_SWITCH)
+  int32_t warp_on;
+  int64_t warp_below;
 };
 
 struct RArgs {
@@ -922,6 +929,7 @@ __device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p
                                               int km) {
   const int lane = lane_id();
   const int in_c = S.in_off[c];
+  int cx = 0, cy = 0;  // the end split of the previous round's last piece
   for (int h0 = 0; h0 < nch; h0 += 32) {
     const int h = h0 + lane;
     int cnt = 0, k = -1, x0 = 0, y0 = 0, x1 = 0, y1 = 0;
@@ -943,21 +951,23 @@ __device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p
       ka = S.na[k];
       sA = S.in + (S.in_off[k] - in_c);
       sB = sA + ka;
-      merge_split(sA, ka, sB, nk - ka, d, x0, y0);
-    }
-    // a piece ends where the next one (the next lane's, same job) starts
-    const int nx0 = __shfl_down_sync(0xffffffffu, x0, 1);
-    const int ny0 = __shfl_down_sync(0xffffffffu, y0, 1);
-    if (k >= 0) {
+      // each lane finds where its piece ends; a piece starts where the previous one ends
       if (d + km >= nk) {
         x1 = ka;
         y1 = nk - ka;
-      } else if (lane < 31) {
-        x1 = nx0;
-        y1 = ny0;
       } else {
         merge_split(sA, ka, sB, nk - ka, d + km, x1, y1);
       }
+    }
+    const int px = __shfl_up_sync(0xffffffffu, x1, 1);
+    const int py = __shfl_up_sync(0xffffffffu, y1, 1);
+    if (k >= 0 && d > 0) {  // not a job's first piece: the previous piece is the same job's
+      x0 = lane > 0 ? px : cx;
+      y0 = lane > 0 ? py : cy;
+    }
+    cx = __shfl_sync(0xffffffffu, x1, 31);
+    cy = __shfl_sync(0xffffffffu, y1, 31);
+    if (k >= 0) {
       if constexpr (KM > 0) {
         lane_merge_regs<KM>(sA, x0, x1, sB, y0, y1, m);
 #pragma unroll
@@ -1021,32 +1031,54 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
   return v;
 }
 
-template <bool kDense>
+// kWarp: the chunk is 32 slots of one warp (warp scan, no block barrier); otherwise 128 slots of
+// the whole block
+template <bool kDense, bool kWarp>
 __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
                                           WarpStage& S, int64_t* sh, int64_t* s_prefix,
                                           unsigned long long* s_cnt) {
   const int lane = lane_id();
-  const int64_t e = chunk * kAddThreads + threadIdx.x;
+  const int64_t e = kWarp ? chunk * 32 + lane : chunk * kAddThreads + threadIdx.x;
   Job jb = job_of<kDense>(a, v, e);
-  // one block scan gives both the survivor rank (high 16 bits) and the arena words (low 48)
-  constexpr int kRankShift = 48;
-  constexpr int64_t kWordMask = (int64_t(1) << kRankShift) - 1;
-  const int64_t packed = jb.surv ? ((int64_t(1) << kRankShift) | jb.words) : 0;
-  int64_t tot;
-  const int64_t excl = block_excl_sum<int64_t, kAddWarps>(packed, sh, tot);
-  const int64_t n_surv = tot >> kRankShift;
   const int32_t pass = a.ds->pass;
-  if (threadIdx.x == 0) {
-    look_publish(a, pass, chunk, n_surv);
-    // the chunk's survivors take one contiguous run of the next arena
-    s_prefix[1] = (tot & kWordMask)
-                      ? (int64_t)atomicAdd(&a.ds->arena_used, (unsigned long long)(tot & kWordMask))
-                      : 0;
-    if (n_surv) atomicAdd(&a.ds->totals[0], (unsigned long long)n_surv);
+  int64_t off, n_surv;
+  int rank;
+  if constexpr (kWarp) {
+    // survivor ranks by ballot, arena words by a warp scan
+    const unsigned survm = __ballot_sync(0xffffffffu, jb.surv);
+    n_surv = __popc(survm);
+    rank = __popc(survm & ((1u << lane) - 1));
+    const int64_t w = jb.surv ? jb.words : 0;
+    const int64_t wincl = warp_incl_sum(w);
+    const int64_t wtot = __shfl_sync(0xffffffffu, wincl, 31);
+    unsigned long long wbase = 0;
+    if (lane == 0) {
+      look_publish(a, pass, chunk, n_surv);
+      // the chunk's survivors take one contiguous run of the next arena
+      if (wtot) wbase = atomicAdd(&a.ds->arena_used, (unsigned long long)wtot);
+      if (n_surv) atomicAdd(&a.ds->totals[0], (unsigned long long)n_surv);
+    }
+    off = (int64_t)__shfl_sync(0xffffffffu, wbase, 0) + wincl - w;
+  } else {
+    // one block scan gives both the survivor rank (high 16 bits) and the arena words (low 48)
+    constexpr int kRankShift = 48;
+    constexpr int64_t kWordMask = (int64_t(1) << kRankShift) - 1;
+    const int64_t packed = jb.surv ? ((int64_t(1) << kRankShift) | jb.words) : 0;
+    int64_t tot;
+    const int64_t excl = block_excl_sum<int64_t, kAddWarps>(packed, sh, tot);
+    n_surv = tot >> kRankShift;
+    if (threadIdx.x == 0) {
+      look_publish(a, pass, chunk, n_surv);
+      // the chunk's survivors take one contiguous run of the next arena
+      s_prefix[1] = (tot & kWordMask) ? (int64_t)atomicAdd(&a.ds->arena_used,
+                                                           (unsigned long long)(tot & kWordMask))
+                                      : 0;
+      if (n_surv) atomicAdd(&a.ds->totals[0], (unsigned long long)n_surv);
+    }
+    __syncthreads();
+    off = s_prefix[1] + (excl & kWordMask);
+    rank = (int)(excl >> kRankShift);
   }
-  __syncthreads();
-  const int64_t off = s_prefix[1] + (excl & kWordMask);
-  const int rank = (int)(excl >> kRankShift);
 
   const int32_t* A = jb.A;
   const int32_t* B = jb.B;
@@ -1057,15 +1089,21 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   // ---- new pivots: their columns never change again; move them to the pivot store (a
   // bit-packed column moves as its stored words)
   unsigned pmask = __ballot_sync(0xffffffffu, jb.newpiv);
+  if (pmask) {  // the warp's new pivots take one run of the pivot store
+    const int mine = jb.newpiv ? na : 0;
+    const int incl = warp_incl_sum(mine);
+    const int ptot = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long w0 = 0;
+    if (lane == 0) w0 = atomicAdd(&a.ds->piv_used, (unsigned long long)ptot);
+    w0 = __shfl_sync(0xffffffffu, w0, 0) + (unsigned long long)(incl - mine);
+    if (jb.newpiv) o_ptr = v.piv_base + w0;
+  }
   while (pmask) {
     const int src = __ffs(pmask) - 1;
     pmask &= pmask - 1;
     const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src);
     const int wna = __shfl_sync(0xffffffffu, na, src);
-    unsigned long long w0 = 0;
-    if (lane == src) w0 = atomicAdd(&a.ds->piv_used, (unsigned long long)wna);
-    w0 = __shfl_sync(0xffffffffu, w0, src);
-    int32_t* dst = v.piv_base + w0;
+    int32_t* dst = (int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)o_ptr, src);
     for (int q = lane; q < wna; q += 32) dst[q] = wA[q];
     if (lane == src) {
       o_ptr = dst;
@@ -1224,12 +1262,17 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     }
   }
   // ---- the survivors' places in the next active list
-  if (threadIdx.x < 32) {
+  if constexpr (kWarp) {
     const int64_t pre = look_back(a, pass, chunk, n_surv);
-    if (threadIdx.x == 0) s_prefix[0] = pre;
+    if (jb.surv) v.act2[pre + rank] = jb.j;
+  } else {
+    if (threadIdx.x < 32) {
+      const int64_t pre = look_back(a, pass, chunk, n_surv);
+      if (threadIdx.x == 0) s_prefix[0] = pre;
+    }
+    __syncthreads();
+    if (jb.surv) v.act2[s_prefix[0] + rank] = jb.j;
   }
-  __syncthreads();
-  if (jb.surv) v.act2[s_prefix[0] + rank] = jb.j;
   // ---- publish: in place for targets and zeroed columns, through k_commit for the others
   if (jb.j >= 0) {
     if (jb.surv && jb.target) {
@@ -1280,9 +1323,10 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   }
 }
 
-// kDense: the pass may meet bit-packed columns or convert some (the graph's if / else node, or
-// the host, picks the variant from DevState::dense_on); the row-list variant carries none of it
-template <bool kDense>
+// kDense: the pass may meet bit-packed columns or convert some; the row-list variant carries none
+// of it. kWarp: chunks of 32 slots claimed by single warps. The host picks the variant from
+// DevState::dense_on and warp_on (a separate graph for each).
+template <bool kDense, bool kWarp>
 __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   __shared__ int64_t sh[kAddWarps + 1];
   __shared__ int64_t s_chunk;
@@ -1295,14 +1339,27 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   const PV& v = s_v;
   WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[threadIdx.x >> 5];
   if (threadIdx.x < kNumCnt) s_cnt[threadIdx.x] = 0;
-  for (;;) {  // device work queue of chunks, claimed in order
-    if (threadIdx.x == 0) s_chunk = atomicAdd(&a.ds->queue, 1u);
-    __syncthreads();  // also publishes s_v, written by thread 0 before the loop
-    const int64_t chunk = s_chunk;
-    const int64_t nchunks = (v.n_act + kAddThreads - 1) / kAddThreads;
+  if constexpr (kWarp) {
+    __syncthreads();  // publishes s_v and the zeroed counters
+    const int64_t nchunks = (v.n_act + 31) / 32;
+    for (;;) {  // device work queue of 32-slot chunks, claimed in order by whole warps
+      unsigned int chunk = 0;
+      if (lane_id() == 0) chunk = atomicAdd(&a.ds->queue, 1u);
+      chunk = __shfl_sync(0xffffffffu, chunk, 0);
+      if ((int64_t)chunk >= nchunks) break;
+      add_chunk<kDense, true>(a, v, chunk, S, sh, s_prefix, s_cnt);
+    }
     __syncthreads();
-    if (chunk >= nchunks) break;
-    add_chunk<kDense>(a, v, chunk, S, sh, s_prefix, s_cnt);
+  } else {
+    for (;;) {  // device work queue of 128-slot chunks, claimed in order
+      if (threadIdx.x == 0) s_chunk = atomicAdd(&a.ds->queue, 1u);
+      __syncthreads();  // also publishes s_v, written by thread 0 before the loop
+      const int64_t chunk = s_chunk;
+      const int64_t nchunks = (v.n_act + kAddThreads - 1) / kAddThreads;
+      __syncthreads();
+      if (chunk >= nchunks) break;
+      add_chunk<kDense, false>(a, v, chunk, S, sh, s_prefix, s_cnt);
+    }
   }
   if (threadIdx.x == 0 && s_cnt[kCntTargets]) atomicAdd(&a.ds->totals[1], s_cnt[kCntTargets]);
   if (v.stats && threadIdx.x == 0) {
@@ -1405,9 +1462,11 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
       ds->passes = p;
     } else {
       ds->pass = p + 1;
+      const bool to_warp = !ds->warp_on && ds->n_act < ds->warp_below;
+      if (to_warp) ds->warp_on = 1;
       // the pass is complete, so a later call can resume from the next one
       if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
-      else if (to_dense) ds->status = ST_SWITCH;  // continued with the bit-packing kernel
+      else if (to_dense || to_warp) ds->status = ST_SWITCH;  // continued with the other kernel
     }
   }
   if (in_graph) cudaGraphSetConditional(cond, ds->status == ST_RUN ? 1u : 0u);
@@ -1497,9 +1556,10 @@ static RArgs make_args(ph_ctx* ctx) {
 }
 
 // the kernels of one pass, in order; grids are fixed (persistent blocks loop over the work)
-// dense_on: the additions kernel that handles bit-packed columns (DevState::dense_on)
+// variant: the additions kernel, 1 = handles bit-packed columns (DevState::dense_on) + 2 = one
+// chunk per warp (DevState::warp_on)
 static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
-                        bool in_graph, bool dense_on, bool time_add, cudaStream_t st) {
+                        bool in_graph, int variant, bool time_add, cudaStream_t st) {
   ReduceState& rs = ctx->rs;
   const int sms = ctx->num_sms;
   // grids: the full machine for large complexes, no more blocks than the largest active list
@@ -1530,10 +1590,12 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   }
   const int add_bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
   const unsigned add_grid = blocks(sms * add_bps * (kThreads / kAddThreads), kAddThreads);
-  if (dense_on)
-    k_add<true><<<add_grid, kAddThreads, kAddSmem, st>>>(a);
-  else
-    k_add<false><<<add_grid, kAddThreads, kAddSmem, st>>>(a);
+  switch (variant) {
+    case 0: k_add<false, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 1: k_add<true, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 2: k_add<false, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    default: k_add<true, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+  }
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
   k_commit<<<blocks(sms * 2, kThreads), kThreads, 0, st>>>(a, cond, in_graph ? 1 : 0);
@@ -1566,7 +1628,7 @@ void reduce_init(ph_ctx* ctx) {
   int64_t ntiles = (m + kRTile - 1) / kRTile;
   rs.tiles_bytes = ntiles * (1 + kRItems) * sizeof(SegMax);
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
-  const int64_t nchunks = (m + kAddThreads - 1) / kAddThreads + 1;
+  const int64_t nchunks = (m + 31) / 32 + 1;  // chunks of either shape
   rs.look = alloc_n<unsigned long long>(ctx, nchunks);
   PH_CUDA(cudaMemsetAsync(rs.look, 0, nchunks * sizeof(unsigned long long), st));
   rs.dlist = alloc_n<int32_t>(ctx, m);
@@ -1620,10 +1682,18 @@ void reduce_init(ph_ctx* ctx) {
   h.stats_rows = rs.stats_rows;
   h.pass = 0;
   h.status = ST_RUN;
+  h.warp_below = ctx->opts.warp_chunks_below < 0   ? 0
+                 : ctx->opts.warp_chunks_below == 0 ? (int64_t)1 << 22
+                                                    : ctx->opts.warp_chunks_below;
+  h.warp_on = m < h.warp_below ? 1 : 0;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  PH_CUDA(cudaFuncSetAttribute(k_add<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PH_CUDA(cudaFuncSetAttribute(k_add<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kAddSmem));
-  PH_CUDA(cudaFuncSetAttribute(k_add<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PH_CUDA(cudaFuncSetAttribute(k_add<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kAddSmem));
+  PH_CUDA(cudaFuncSetAttribute(k_add<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kAddSmem));
+  PH_CUDA(cudaFuncSetAttribute(k_add<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kAddSmem));
   rs.passes = 0;
   rs.init = true;
@@ -1666,9 +1736,9 @@ static void serve_host_request(ph_ctx* ctx, DevState& h) {
   h.status = ST_RUN;
 }
 
-// the pass loop as one graph: a conditional while node around one pass (dense: with the
-// additions kernel that handles bit-packed columns)
-static void build_graph(ph_ctx* ctx, const RArgs& a, bool dense) {
+// the pass loop as one graph: a conditional while node around one pass, with one of the
+// additions kernel variants (see launch_pass)
+static void build_graph(ph_ctx* ctx, const RArgs& a, int variant) {
   ReduceState& rs = ctx->rs;
   cudaGraph_t g;
   PH_CUDA(cudaGraphCreate(&g, 0));
@@ -1695,7 +1765,7 @@ static void build_graph(ph_ctx* ctx, const RArgs& a, bool dense) {
   }
   const int64_t counted = ctx->launches;  // captured launches run later, counted per pass
   try {
-    launch_pass(ctx, a, cond, true, dense, false, cs);
+    launch_pass(ctx, a, cond, true, variant, false, cs);
     ctx->launches = counted;
   } catch (...) {
     cudaStreamEndCapture(cs, &body);
@@ -1709,8 +1779,8 @@ static void build_graph(ph_ctx* ctx, const RArgs& a, bool dense) {
   PH_CUDA(ce);
   cudaGraphExec_t exec;
   PH_CUDA(cudaGraphInstantiate(&exec, g, 0));
-  rs.graph[dense] = g;
-  rs.graph_exec[dense] = exec;
+  rs.graph[variant] = g;
+  rs.graph_exec[variant] = exec;
 }
 
 int reduce_run(ph_ctx* ctx, int32_t max_passes) {
@@ -1741,11 +1811,11 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   for (;;) {
     const int32_t first_pass = h.pass;
     if (use_graph) {
-      const bool dense = h.dense_on != 0;
-      if (!rs.graph_exec[dense]) build_graph(ctx, a, dense);
-      PH_CUDA(cudaGraphLaunch(rs.graph_exec[dense], st));
+      const int variant = (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0);
+      if (!rs.graph_exec[variant]) build_graph(ctx, a, variant);
+      PH_CUDA(cudaGraphLaunch(rs.graph_exec[variant], st));
     } else {
-      launch_pass(ctx, a, 0, false, h.dense_on != 0, time_add, st);
+      launch_pass(ctx, a, 0, false, (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0), time_add, st);
       if (time_add) rs.add_launches++;
     }
     PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
@@ -1863,7 +1933,7 @@ void predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* host_out, int64_t n) {
 
 void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
-  for (int d = 0; d < 2; d++) {
+  for (int d = 0; d < 4; d++) {
     if (rs.graph_exec[d]) cudaGraphExecDestroy(rs.graph_exec[d]);
     if (rs.graph[d]) cudaGraphDestroy(rs.graph[d]);
   }

@@ -266,6 +266,38 @@ def test_bit_packed_columns_modes_and_batches(ph, orc, strict, cor10):
         _check_counters(ctx, ref)
 
 
+@pytest.mark.parametrize("below", [-1, 1 << 30, 20000, 3000])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_chunk_shapes_agree(ph, orc, below, use_graph):
+    # Phase II in 128-slot block chunks throughout (-1), 32-slot warp chunks throughout (2^30),
+    # or switching from the first to the second mid-reduction (the active list drops below 20,000
+    # or 3,000 columns); a batch of clouds, and a dense-mode run, switch too
+    x = pc.random_cloud(60, 3, 12)
+    K = orc.vr_build(x, 2)
+    ref = orc.reduce_pms(K)
+    ctx = _gpu(ph, x, 2, use_graph=use_graph, warp_chunks_below=below)
+    st = ctx.reduce()
+    assert st["passes"] == ref.passes
+    assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+    _check_counters(ctx, ref)
+    sizes = [17, 40, 5, 33]
+    clouds = [pc.random_cloud(n, 3, 300 + i) for i, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ctx = _gpu(ph, np.concatenate(clouds), 2, offsets=off, use_graph=use_graph,
+               warp_chunks_below=below // 2 if below > 0 else below)
+    ctx.reduce()
+    for c, xc in enumerate(clouds):
+        _check_reduced(orc, ctx, c, orc.vr_build(xc, 2))
+    xd = pc.random_cloud(11, 3, 31)
+    Kd = orc.vr_build(xd, 4)
+    refd = orc.reduce_pms(Kd)
+    ctx = _gpu(ph, xd, 4, use_graph=use_graph, dense_threshold=1,
+               warp_chunks_below=min(below, 2000) if below > 0 else below)
+    ctx.reduce()
+    assert np.array_equal(ctx.filtration(0)["low"], refd.low)
+    _check_counters(ctx, refd)
+
+
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_batched_clouds(ph, orc, use_graph):
     sizes = [1, 2, 3, 17, 40, 5, 60, 33]
