@@ -67,7 +67,7 @@ def _load():
         L.orc_reduce_std.restype = ctypes.c_int
         L.orc_reduce_twist.argtypes = [i64, P, P, P, P, P]
         L.orc_reduce_twist.restype = ctypes.c_int
-        L.orc_reduce_pms.argtypes = [i64, P, P, P, P, i32, i32, i32, P, P, P, P, P, P]
+        L.orc_reduce_pms.argtypes = [i64, P, P, P, P, i32, i32, i32, i32, i32, P, P, P, P, P, P]
         L.orc_reduce_pms.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -187,8 +187,11 @@ class PmsResult(dict):
 
 
 def reduce_pms(K: Complex, max_passes: int = 100000, strict: bool = False, cor10: bool = True,
-               beta_arr: np.ndarray | None = None) -> PmsResult:
-    """Algorithm 2, pass by pass (see ph_oracle.c for the pass definition)."""
+               beta_arr: np.ndarray | None = None, sets: int = 0,
+               priority: int = 0) -> PmsResult:
+    """Algorithm 2, pass by pass (see ph_oracle.c for the pass definition). sets > 0: Phase II
+    acts on that many neighbour sets per pass, ordered by |N| (priority 0) or by known-negative
+    targets first (priority 1), Sec. 3.4."""
     L = _load()
     m = K.m
     b = beta(K) if beta_arr is None else np.ascontiguousarray(beta_arr, np.int32)
@@ -199,7 +202,8 @@ def reduce_pms(K: Complex, max_passes: int = 100000, strict: bool = False, cor10
     proven = np.zeros(max(m, 1), np.uint8)
     pred = np.full(max(m, 1), -1, np.int32)
     rc = L.orc_reduce_pms(m, _ptr(K["colptr"]), _ptr(K["rows"]), _ptr(K["dim"]), _ptr(b),
-                          max_passes, int(strict), int(cor10), _ptr(low), _ptr(ps),
+                          max_passes, int(strict), int(cor10), int(sets), int(priority),
+                          _ptr(low), _ptr(ps),
                           ctypes.byref(npass), _ptr(ess), _ptr(proven), _ptr(pred))
     if rc < 0:
         raise RuntimeError(rc)

@@ -17,7 +17,8 @@
  *   orc_reduce_twist  standard reduction with a twist (clearing), Algorithm 3.
  *   orc_reduce_pms    parallel multi-scale reduction, Algorithm 2 (Phase 0, Phase I as in
  *                     Algorithm 5, Phase II), executed pass by pass, with clearing, the zero
- *                     case of Corollary 10 and the essential estimate of Eq. essential_iteration.
+ *                     case of Corollary 10, the essential estimate of Eq. essential_iteration
+ *                     and, optionally, Phase II limited to p neighbour sets (Sec. 3.4).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -480,6 +481,13 @@ int orc_reduce_twist(int64_t m, const int64_t* colptr, const int32_t* rows, cons
 /*   9 columns whose pair is predicted by Corollary 10 (non-zero case) for the first time       */
 /*  10 columns with an empty candidate set L_j (impossible by Lemma 9; counted as a check)      */
 /*                                                                                              */
+/* Phase II with p processors (sets > 0; Sec. 3.4.1-3.4.2): the targets of a pass fall into   */
+/* neighbour sets N, one per row i, holding the targets whose addition this pass may do        */
+/* (source tab[i], eligible as above). Only the targets of the first p sets in priority order  */
+/* receive their addition; the rest stay active unchanged. Order: priority 0 by |N| (larger    */
+/* first, Sec. 3.4.1); priority 1 by the number of targets known to be negative (beta >= 0,    */
+/* Thm 5), then by |N| (Sec. 3.4.2); ties by the smaller row i.                                */
+/*                                                                                              */
 /* Corollary 10, non-zero case (pred_out): for an active column j of dimension d >= 1 with      */
 /* beta_j >= 0 (hence negative, Thm 5, so 0 is not a candidate) that this pass neither proves   */
 /* nor zeroes, L_j is the set of rows of K_{d-1} in [beta_j, low(j)] not in Paired (start of    */
@@ -488,10 +496,21 @@ int orc_reduce_twist(int64_t m, const int64_t* colptr, const int32_t* rows, cons
 #define ORC_PS_N 11
 #define ORC_MAX_DIM 16
 
+/* priority order of neighbour sets (rows): key1 descending, then key2 descending, then row */
+static const int64_t* g_set_key1;
+static const int64_t* g_set_key2;
+static int cmp_sets(const void* a, const void* b) {
+  const int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+  if (g_set_key1[x] != g_set_key1[y]) return g_set_key1[x] > g_set_key1[y] ? -1 : 1;
+  if (g_set_key2[x] != g_set_key2[y]) return g_set_key2[x] > g_set_key2[y] ? -1 : 1;
+  return x < y ? -1 : (x > y);
+}
+
 int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const int32_t* dim,
                    const int32_t* beta, int32_t max_passes, int32_t strict, int32_t use_cor10,
-                   int32_t* low_out, int64_t* pass_stats, int32_t* passes_out,
-                   uint8_t* ess_est_out, uint8_t* proven_out, int32_t* pred_out) {
+                   int32_t sets, int32_t priority, int32_t* low_out, int64_t* pass_stats,
+                   int32_t* passes_out, uint8_t* ess_est_out, uint8_t* proven_out,
+                   int32_t* pred_out) {
   col_t* R = cols_from_csc(m, colptr, rows);
   int64_t M = m > 0 ? m : 1;
   int32_t* low = (int32_t*)malloc((size_t)M * sizeof(int32_t));
@@ -504,9 +523,13 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
   uint8_t* in_E = (uint8_t*)malloc((size_t)M);
   uint8_t* unpaired = (uint8_t*)malloc((size_t)M); /* start of the pass */
   int32_t* pred = (int32_t*)malloc((size_t)M * sizeof(int32_t));
+  int64_t* set_n = (int64_t*)calloc((size_t)M, sizeof(int64_t));   /* |N| per row */
+  int64_t* set_neg = (int64_t*)calloc((size_t)M, sizeof(int64_t)); /* targets with beta >= 0 */
+  int64_t* set_rows = (int64_t*)malloc((size_t)M * sizeof(int64_t));
+  uint8_t* set_on = (uint8_t*)calloc((size_t)M, 1);                /* set acted on this pass */
   col_t tmp = {0, 0, 0};
   if (!R || !low || !tab || !owner || !proven || !final_ || !newpiv || !zeroed || !in_E ||
-      !unpaired || !pred)
+      !unpaired || !pred || !set_n || !set_neg || !set_rows || !set_on)
     return ORC_ERR_ALLOC;
   int32_t maxd = 0;
   for (int64_t j = 0; j < m; j++)
@@ -594,6 +617,26 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
       if (proven[x] || beta[x] >= 0 || owner[x] >= 0) in_E[x] = 0;
     for (int64_t j = 0; j < m; j++)
       if (tab[j] >= 0) in_E[j] = 0; /* j is the low of some column */
+    /* 5'. with p processors: the neighbour sets this pass acts on */
+    if (sets > 0 && pass < max_passes) {
+      memset(set_n, 0, (size_t)M * sizeof(int64_t));
+      memset(set_neg, 0, (size_t)M * sizeof(int64_t));
+      memset(set_on, 0, (size_t)M);
+      for (int64_t l = 0; l < m; l++) {
+        if (proven[l] || final_[l]) continue;
+        int32_t s = tab[low[l]];
+        if (s == l || zeroed[s] || (strict && !proven[s])) continue;
+        set_n[low[l]]++;
+        if (beta[l] >= 0) set_neg[low[l]]++;
+      }
+      int64_t nsets = 0;
+      for (int64_t i = 0; i < m; i++)
+        if (set_n[i] > 0) set_rows[nsets++] = i;
+      g_set_key1 = priority == 1 ? set_neg : set_n;
+      g_set_key2 = set_n; /* priority 0: the same key again, so rows decide ties */
+      qsort(set_rows, (size_t)nsets, sizeof(int64_t), cmp_sets);
+      for (int64_t k = 0; k < nsets && k < sets; k++) set_on[set_rows[k]] = 1;
+    }
     /* 5. Phase II additions (none once max_passes passes with additions have been done) */
     for (int64_t l = 0; l < m; l++) {
       if (proven[l] || final_[l]) continue;
@@ -603,6 +646,7 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
       if (pass >= max_passes) continue;
       if (zeroed[s]) continue; /* source zeroed by this pass */
       if (strict && !proven[s]) continue;
+      if (sets > 0 && !set_on[low[l]]) continue; /* its set waits for a later pass */
       int64_t x = col_add(&R[l], &R[s], &tmp);
       if (x < 0) return ORC_ERR_ALLOC;
       st[6]++;
@@ -635,6 +679,10 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
   free(in_E);
   free(unpaired);
   free(pred);
+  free(set_n);
+  free(set_neg);
+  free(set_rows);
+  free(set_on);
   free(tmp.v);
   return status;
 }

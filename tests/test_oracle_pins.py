@@ -342,3 +342,59 @@ def test_diagram_edges_realise_diameters(orc):
             p, q = orc.realising_edge(K, j)
             d2 = int(((x[p].astype(np.int64) - x[q]) ** 2).sum())
             assert d2 == K["diam2"][j]
+
+
+# --- Phase II with p processors (Sec. 3.4) -----------------------------------------------------
+# Seven vertices and nine edges, in this filtration order. Pass 0 by hand:
+# - edges (0,1), (0,2), (0,3), (0,4) and (0,6) are left-most for their lows 1, 2, 3, 4 and 6 and
+#   become pivots in Phase I;
+# - the targets are (1,4), (2,4), (3,4) (set of row 4, |N| = 3, all with beta = -1) and (5,6)
+#   (set of row 6, |N| = 1). (5,6) is the first edge at vertex 5, so beta = 5 >= 0: it is
+#   known to be negative (Thm 5).
+# After that, every set has one target and ties go to the lower row. (5,6) + (0,6) = {0, 5}
+# has low 5 = beta and becomes a pivot in the next pass; (i,4) + (0,4) = {0, i} meets (0,i),
+# which zeroes it. So, per pass, the additions and targets are:
+#   all sets:                 adds 4, 3, 0        targets 4, 3, 0
+#   p = 1 by |N|:             adds 3, 1, 1, 1, 1, 0  targets 4, 4, 3, 2, 1, 0
+#   p = 1 negatives first:    adds 1, 3, 1, 1, 1, 0  targets 4, 3, 3, 2, 1, 0
+#   p = 2 (either order):     adds 4, 2, 1, 0     targets 4, 3, 1, 0
+BUDGET_EXAMPLE = [(v,) for v in range(7)] + [(0, 1), (0, 2), (0, 3), (0, 4), (1, 4), (2, 4),
+                                            (3, 4), (0, 6), (5, 6)]
+
+
+@pytest.mark.parametrize("sets,priority,adds,targets", [
+    (0, 0, [4, 3, 0], [4, 3, 0]),
+    (1, 0, [3, 1, 1, 1, 1, 0], [4, 4, 3, 2, 1, 0]),
+    (1, 1, [1, 3, 1, 1, 1, 0], [4, 3, 3, 2, 1, 0]),
+    (2, 0, [4, 2, 1, 0], [4, 3, 1, 0]),
+    (2, 1, [4, 2, 1, 0], [4, 3, 1, 0]),
+    (9, 1, [4, 3, 0], [4, 3, 0]),
+])
+def test_budgeted_phase2_hand_example(orc, sets, priority, adds, targets):
+    K = orc.boundary_from_simplices(BUDGET_EXAMPLE)
+    assert orc.beta(K)[15] == 5  # the edge (5, 6)
+    r = orc.reduce_pms(K, sets=sets, priority=priority)
+    assert r.converged
+    assert r.stats[:, 6].tolist() == adds
+    assert r.stats[:, 5].tolist() == targets
+    assert np.array_equal(r.low, orc.reduce_std(K)[0])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_budgeted_phase2_reaches_lowstar(orc, seed):
+    # any left-to-right additions reach the unique lowstar (Sec. 2.3), so every budget and
+    # order ends at the standard reduction's low; a budget of at least every set is Algorithm 2
+    x = pc.random_cloud(14, 3, 400 + seed)
+    K = orc.vr_build(x, 3)
+    std = orc.reduce_std(K)[0]
+    full = orc.reduce_pms(K)
+    for strict in (False, True):
+        for p, prio in ((1, 0), (1, 1), (3, 0), (5, 1), (K.m, 0)):
+            r = orc.reduce_pms(K, sets=p, priority=prio, strict=strict)
+            assert r.converged and np.array_equal(r.low, std)
+            assert np.all(r.stats[:, 6] <= r.stats[:, 5])  # additions only for targets
+            # every pass with targets acts on at least one set, so the low sum keeps falling
+            assert np.all((r.stats[:-1, 6] > 0) | (r.stats[:-1, 1] > 0) | strict)
+            if p >= K.m and not strict:
+                assert r.passes == full.passes
+                assert np.array_equal(r.stats, full.stats)
