@@ -107,6 +107,17 @@ typedef struct {
    * shrinks, so a reduction switches at most once. Results are identical either way.
    * 0 (default): 4,194,304; < 0: block chunks throughout. */
   int32_t warp_chunks_below;
+  /* Phase II with p processors (Sec. 3.4.1-3.4.2). phase2_sets = p > 0: each pass the targets
+   * fall into neighbour sets, one per low row i, holding the targets whose addition the pass
+   * may do; only the targets of the first p sets in priority order receive their addition, the
+   * others stay active unchanged (and count as targets). phase2_priority 0: larger sets first
+   * (Sec. 3.4.1); 1: sets with more targets known to be negative (beta >= 0, Thm 5) first,
+   * then larger sets (Sec. 3.4.2); ties by the smaller row. Any budget reaches the same lowstar
+   * (Sec. 2.3); passes and counters differ. The pass loop is then host-driven (use_graph is
+   * ignored). 0 (default): every set, as in Algorithm 2. ph_create rejects a priority other
+   * than 0 or 1 (PH_ERR_INVALID). */
+  int32_t phase2_sets;
+  int32_t phase2_priority;
 } ph_opts;
 
 /* Per-pass counters (rows of ph_get_pass_stats), in this order. */

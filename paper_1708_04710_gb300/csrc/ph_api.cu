@@ -280,6 +280,8 @@ void ph_default_opts(ph_opts* o) {
   o->predict_pairs = 0;
   o->dense_threshold = 0;
   o->warp_chunks_below = 0;
+  o->phase2_sets = 0;
+  o->phase2_priority = 0;
 }
 
 int ph_create(ph_ctx** out, const ph_opts* opts, const ph_allocator* alloc, void* stream) {
@@ -289,6 +291,10 @@ int ph_create(ph_ctx** out, const ph_opts* opts, const ph_allocator* alloc, void
   if (!ctx) return PH_ERR_ALLOC;
   if (opts) ctx->opts = *opts;
   else ph_default_opts(&ctx->opts);
+  if (ctx->opts.phase2_priority < 0 || ctx->opts.phase2_priority > 1) {
+    delete ctx;
+    return PH_ERR_INVALID;
+  }
   if (alloc && alloc->alloc && alloc->free) {
     ctx->alloc = *alloc;
     ctx->has_alloc = true;

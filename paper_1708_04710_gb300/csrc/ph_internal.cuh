@@ -95,6 +95,11 @@ struct ReduceState {
   uint32_t* unp_bits = nullptr;  // Corollary 10 predictions: unpaired-row bitmap
   int32_t* unp_words = nullptr;  // and its per-word prefix counts
   int32_t* pred = nullptr;       // per id: predicted lowstar, -1
+  // Phase II limited to p neighbour sets (phase2_sets > 0), per row of the boundary:
+  int32_t* set_n = nullptr;      // targets of the row's set whose addition this pass may do
+  int32_t* set_neg = nullptr;    // those of them known to be negative (beta >= 0)
+  uint8_t* set_on = nullptr;     // the set is among the p acted on
+  uint64_t* set_key = nullptr;   // [4][rows] priority sort keys, rows, and their scratch
   int64_t tiles_bytes = 0;
   void* dstate = nullptr;      // per-pass state in device memory
   void* hstate = nullptr;      // pinned host mirror of it

@@ -116,6 +116,10 @@ struct RArgs {
   int32_t* pred;      // per id: predicted lowstar (Corollary 10), -1
   int staged_max;     // merges of more rows than this run from global memory
   int force_km;       // > 0: merge-path positions per lane for every warp
+  // Phase II limited to p neighbour sets per pass (Sec. 3.4): per row of the boundary
+  int32_t* set_n;     // eligible targets of the row's set
+  int32_t* set_neg;   // those known to be negative
+  uint8_t* set_on;    // the set is acted on this pass
 };
 
 // per-pass values, read once at kernel start (no kernel changes them while others read them)
@@ -544,6 +548,67 @@ __global__ void k_mark(RArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Phase II with p processors (Sec. 3.4): the neighbour sets a pass acts on
+// ------------------------------------------------------------------------------------------
+// every active target whose addition this pass may do is counted in its set (row low(j));
+// the tests are those of the additions themselves, applied to the marks of this pass
+__global__ void k_set_count(RArgs a) {
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
+  if (!v.do_adds) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < v.n_act; e += stride) {
+    const int32_t s = a.src_e[e];
+    if (s < 0) continue;
+    const int32_t j = v.act[e];
+    const ColMeta mj = load_meta(a.meta + j);
+    if ((mj.flags & (F_PROVEN | F_FINAL)) || mj.cleared) continue;
+    const ColMeta ms = load_meta(a.meta + s);
+    if ((ms.flags & F_FINAL) || ms.cleared || (a.strict && !(ms.flags & F_PROVEN))) continue;
+    const int32_t i = a.low[j];
+    atomicAdd(a.set_n + i, 1);
+    if (a.beta[j] >= 0) atomicAdd(a.set_neg + i, 1);
+  }
+}
+
+// Sort keys of the sets: ascending key order is the priority order (priority 0: larger sets
+// first; 1: more known-negative targets first, then larger sets). The radix sort is stable and
+// the rows start in order, so equal keys keep the smaller row first; rows without a set sort
+// last. bits: enough for any count.
+__global__ void k_set_keys(RArgs a, int priority, int bits, uint64_t* key, uint64_t* row) {
+  const uint64_t top = (1ull << bits) - 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.rows_end; i += stride) {
+    const uint64_t n = (uint64_t)a.set_n[i], g = (uint64_t)a.set_neg[i];
+    key[i] = priority == 1 ? ((top - g) << bits) | (top - n) : top - n;
+    row[i] = (uint64_t)i;
+    a.set_on[i] = 0;
+  }
+}
+
+// the first p sets of the sorted order are acted on
+__global__ void k_set_select(RArgs a, int64_t p, const uint64_t* __restrict__ row) {
+  const int64_t n = p < a.rows_end ? p : a.rows_end;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += stride) {
+    const int64_t i = (int64_t)row[t];
+    if (a.set_n[i] > 0) a.set_on[i] = 1;
+  }
+}
+
+// a target outside the chosen sets keeps its collision (it counts as a target) but skips its
+// addition this pass: its slot's source becomes -2 - s
+__global__ void k_set_apply(RArgs a) {
+  if (a.ds->status != ST_RUN) return;
+  const PV v = pass_view(a.ds);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < v.n_act; e += stride) {
+    const int32_t s = a.src_e[e];
+    if (s >= 0 && !a.set_on[a.low[v.act[e]]]) a.src_e[e] = -2 - s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // what happens to an active column in Phase II
 // ------------------------------------------------------------------------------------------
 // One job by the whole warp on bitmaps: column A (rows, or a bit-packed column if dense_a) plus
@@ -621,7 +686,8 @@ __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
   // every load is issued up front: the column and its source candidate are known from the
   // active list and k_mark's per-slot source, so no load waits on another's result
   const int32_t j = v.act[e];
-  const int32_t s = a.src_e[e];
+  const int32_t se = a.src_e[e];  // -1: no collision; <= -2: a target whose set waits
+  const int32_t s = se >= 0 ? se : -1;
   const ColMeta mj = load_meta(a.meta + j);  // one 16-byte load per column
   const uint8_t f = mj.flags;
   const uint8_t cj = mj.cleared;
@@ -642,8 +708,8 @@ __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
   jb.surv = !(f & (F_PROVEN | F_FINAL)) && !cj;
   if (jb.surv) {
     jb.words = nj;
+    jb.target = se != -1;
     if (s >= 0) {
-      jb.target = true;
       if (v.do_adds && !(fs & F_FINAL) && !cs && (!a.strict || (fs & F_PROVEN))) {
         jb.src = s;
         jb.dense_b = kDense && ns < 0;
@@ -1535,6 +1601,9 @@ static RArgs make_args(ph_ctx* ctx) {
   a.staged_max = ctx->opts.staged_merge_max > 0 ? std::min(ctx->opts.staged_merge_max, kStage)
                                                  : kStage;
   a.force_km = std::max(0, std::min(ctx->opts.merge_items, 64));
+  a.set_n = rs.set_n;
+  a.set_neg = rs.set_neg;
+  a.set_on = rs.set_on;
   // bit-packed columns: per column dimension the smallest threshold over its row segments
   a.dense_mode = ctx->opts.dense_threshold;
   a.seg_start = ctx->d_seg_start;
@@ -1578,6 +1647,27 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   PH_CHECK_LAUNCH();
   if (ctx->opts.collect_stats) {
     k_ess_count<<<sms * 4, kThreads, 0, st>>>(a, ctx->m);
+    PH_CHECK_LAUNCH();
+  }
+  if (ctx->opts.phase2_sets > 0 && a.rows_end > 0) {  // host-driven loop only
+    const int64_t rows = a.rows_end;
+    int bits = 1;
+    while (bits < 31 && (int64_t(1) << bits) <= ctx->m) bits++;
+    PH_CUDA(cudaMemsetAsync(rs.set_n, 0, (size_t)rows * sizeof(int32_t), st));
+    PH_CUDA(cudaMemsetAsync(rs.set_neg, 0, (size_t)rows * sizeof(int32_t), st));
+    k_set_count<<<blocks(sms * 8, kThreads), kThreads, 0, st>>>(a);
+    PH_CHECK_LAUNCH();
+    uint64_t* key = rs.set_key;
+    uint64_t* row = rs.set_key + rows;
+    k_set_keys<<<grid_for(ctx, rows, kThreads), kThreads, 0, st>>>(
+        a, ctx->opts.phase2_priority, bits, key, row);
+    PH_CHECK_LAUNCH();
+    radix_sort_u64(ctx, key, row, rows, 0, ctx->opts.phase2_priority == 1 ? 2 * bits : bits,
+                   rs.set_key + 2 * rows, rs.set_key + 3 * rows);
+    const int64_t p = std::min<int64_t>(ctx->opts.phase2_sets, rows);
+    k_set_select<<<grid_for(ctx, p, kThreads), kThreads, 0, st>>>(a, p, row);
+    PH_CHECK_LAUNCH();
+    k_set_apply<<<blocks(sms * 8, kThreads), kThreads, 0, st>>>(a);
     PH_CHECK_LAUNCH();
   }
   if (time_add) {
@@ -1640,6 +1730,13 @@ void reduce_init(ph_ctx* ctx) {
     rs.unp_words = alloc_n<int32_t>(ctx, nwords + 1);
     rs.pred = alloc_n<int32_t>(ctx, m);
     PH_CUDA(cudaMemsetAsync(rs.pred, 0xff, (size_t)m * sizeof(int32_t), st));
+  }
+  if (ctx->opts.phase2_sets > 0) {
+    const int64_t rows = std::max<int64_t>(ctx->dimoff[ctx->max_dim], 1);
+    rs.set_n = alloc_n<int32_t>(ctx, rows);
+    rs.set_neg = alloc_n<int32_t>(ctx, rows);
+    rs.set_on = alloc_n<uint8_t>(ctx, rows);
+    rs.set_key = alloc_n<uint64_t>(ctx, 4 * rows);
   }
   rs.dstate = ctx->dalloc(sizeof(DevState));
   PH_CUDA(cudaMallocHost(&rs.hstate, sizeof(DevState)));
@@ -1786,7 +1883,8 @@ static void build_graph(ph_ctx* ctx, const RArgs& a, int variant) {
 int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   ReduceState& rs = ctx->rs;
   cudaStream_t st = ctx->stream;
-  const bool use_graph = ctx->opts.use_graph != 0;
+  // the budgeted Phase II ranks its sets with host-sized sort launches: host-driven loop
+  const bool use_graph = ctx->opts.use_graph != 0 && ctx->opts.phase2_sets <= 0;
   const bool time_add = ctx->opts.time_kernels != 0 && !use_graph;
   DevState& h = *static_cast<DevState*>(rs.hstate);
   // a resumed reduction continues after the pass that hit the previous cap
@@ -1941,7 +2039,8 @@ void free_reduce_state(ph_ctx* ctx) {
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
                   (void*)rs.first_unp, rs.tiles, rs.dstate,
                   rs.look, rs.dlist, rs.src_e, (void*)rs.unp_bits, (void*)rs.unp_words,
-                  (void*)rs.pred,
+                  (void*)rs.pred, (void*)rs.set_n, (void*)rs.set_neg, (void*)rs.set_on,
+                  (void*)rs.set_key,
                   (void*)rs.pass_stats})
     ctx->dfree(p);
   for (auto& a : rs.arena) ctx->dfree(a.p);

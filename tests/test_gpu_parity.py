@@ -417,6 +417,54 @@ def test_triangulations(ph, orc):
         assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8]), name
 
 
+@pytest.mark.parametrize("sets,priority", [(1, 0), (1, 1), (3, 0), (7, 1), (10 ** 6, 0)])
+def test_budgeted_phase2(ph, orc, sets, priority):
+    # Phase II on p neighbour sets per pass (Sec. 3.4): the sets the GPU picks each pass are
+    # the oracle's, so passes, every counter, E^l and the result agree exactly
+    from test_oracle_pins import BUDGET_EXAMPLE
+
+    K0 = orc.boundary_from_simplices(BUDGET_EXAMPLE)
+    ref = orc.reduce_pms(K0, sets=sets, priority=priority)
+    ctx = ph.Context(collect_stats=True, phase2_sets=sets, phase2_priority=priority)
+    ctx.load_boundary(K0["dim"], K0["colptr"], K0["rows"])
+    st = ctx.reduce()
+    assert st["passes"] == ref.passes
+    assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+    for x, k in ((pc.random_cloud(30, 3, 500), 2), (pc.random_cloud(12, 3, 501), 4)):
+        K = orc.vr_build(x, k)
+        for strict in (False, True):
+            ref = orc.reduce_pms(K, sets=sets, priority=priority, strict=strict)
+            ctx = _gpu(ph, x, k, phase2_sets=sets, phase2_priority=priority,
+                       strict_phase2=strict, use_graph=True)  # runs host-driven all the same
+            st = ctx.reduce()
+            assert st["passes"] == ref.passes
+            _check_reduced(orc, ctx, 0, K, strict=strict)
+            _check_counters(ctx, ref)
+
+
+def test_budgeted_phase2_batched_and_partial(ph, orc):
+    # a batch (one priority order over every cloud's sets) reaches each cloud's lowstar; an
+    # early-stopped budgeted reduction is the oracle's state after the same passes
+    sizes = [9, 20, 14]
+    clouds = [pc.random_cloud(n, 3, 510 + i) for i, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ctx = _gpu(ph, np.concatenate(clouds), 3, offsets=off, phase2_sets=2, phase2_priority=1)
+    ctx.reduce()
+    for c, xc in enumerate(clouds):
+        _check_reduced(orc, ctx, c, orc.vr_build(xc, 3))
+    x = pc.circle40()
+    K = orc.vr_build(x, 2)
+    for mp in (1, 4, 9):
+        ref = orc.reduce_pms(K, sets=5, priority=0, max_passes=mp)
+        ctx = _gpu(ph, x, 2, phase2_sets=5)
+        ctx.reduce(max_passes=mp)
+        assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+        _check_counters(ctx, ref)
+    with pytest.raises(ph.PHError):
+        ph.Context(phase2_priority=2)
+
+
 def test_invalid_arguments(ph):
     import torch
 
