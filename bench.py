@@ -359,7 +359,8 @@ def main():
 def run_early():
     """Iterations of Algorithm 2 to given levels of relative l1 error of low (Eq. rel_error),
     unreduced share and essential-estimate precision, per ensemble, for the left-most source
-    (default) and the printed rule (strict_phase2). One JSON line."""
+    (default), the printed rule (strict_phase2), and Phase II limited to 32 neighbour sets per
+    pass under both orders of Sec. 3.4. One JSON line."""
     import torch
 
     from paper_1708_04710_gb300 import build as _build
@@ -374,10 +375,15 @@ def run_early():
     for name in pc.ENSEMBLES:
         x = torch.from_numpy(pc.ensemble15(name)).cuda()
         res[name] = {}
-        for mode, strict, cor10 in (("leftmost", False, True), ("strict", True, True),
-                                    ("leftmost_no_cor10", False, False),
-                                    ("strict_no_cor10", True, False)):
-            ctx = ph.Context(collect_stats=True, strict_phase2=strict, use_cor10=cor10)
+        # the last two: p = 32 processors, the sets of Sec. 3.4.1 (largest first) against
+        # those of Sec. 3.4.2 (known-negative targets first)
+        for mode, strict, cor10, sets, prio in (
+                ("leftmost", False, True, 0, 0), ("strict", True, True, 0, 0),
+                ("leftmost_no_cor10", False, False, 0, 0), ("strict_no_cor10", True, False, 0, 0),
+                ("p32_largest_sets_first", False, False, 32, 0),
+                ("p32_negatives_first", False, False, 32, 1)):
+            ctx = ph.Context(collect_stats=True, strict_phase2=strict, use_cor10=cor10,
+                             phase2_sets=sets, phase2_priority=prio)
             ctx.build_filtration_scales(x, None, 5, step, n_scales)
             pr = early.profile(ctx)
             res[name][mode] = {

@@ -118,6 +118,11 @@ typedef struct {
    * than 0 or 1 (PH_ERR_INVALID). */
   int32_t phase2_sets;
   int32_t phase2_priority;
+  /* Initial capacity of each of the two survivor arenas, in int32 words (0, default: twice the
+   * boundary's nonzeros). A pass whose Phase I bound does not fit stops before any change, the
+   * host grows the arena and the pass runs again, so a small value trades memory for extra
+   * host round trips; results are the same. */
+  int64_t arena_words;
 } ph_opts;
 
 /* Per-pass counters (rows of ph_get_pass_stats), in this order. */

@@ -282,6 +282,7 @@ void ph_default_opts(ph_opts* o) {
   o->warp_chunks_below = 0;
   o->phase2_sets = 0;
   o->phase2_priority = 0;
+  o->arena_words = 0;
 }
 
 int ph_create(ph_ctx** out, const ph_opts* opts, const ph_allocator* alloc, void* stream) {

@@ -1753,8 +1753,10 @@ void reduce_init(ph_ctx* ctx) {
       m, L, ctx->rows0, static_cast<ColMeta*>(rs.meta), ctx->low, rs.act, rs.owner);
   PH_CHECK_LAUNCH();
   // first arenas: pass 0 needs at most the boundary matrix twice over
-  grow_store(ctx, rs.arena[0], 2 * ctx->nnz + 1);
-  grow_store(ctx, rs.arena[1], ctx->nnz + 1);
+  // passes 0 and 1 need about the same; later passes less (they grow on demand otherwise)
+  const int64_t arena0 = ctx->opts.arena_words > 0 ? ctx->opts.arena_words : 2 * ctx->nnz + 1;
+  grow_store(ctx, rs.arena[0], arena0);
+  grow_store(ctx, rs.arena[1], arena0);
   ColStore c{};
   grow_store(ctx, c, ctx->nnz / 4 + 1);
   rs.pivots.push_back(c);

@@ -33,7 +33,7 @@ class PhOpts(Structure):
                 ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32),
                 ("predict_pairs", c_int32), ("dense_threshold", c_int32),
                 ("warp_chunks_below", c_int32), ("phase2_sets", c_int32),
-                ("phase2_priority", c_int32)]
+                ("phase2_priority", c_int32), ("arena_words", c_int64)]
 
 
 class PhStats(Structure):
@@ -128,6 +128,7 @@ class Context:
                  use_graph: bool = True, time_kernels: bool = False, add_blocks_per_sm: int = 0,
                  timeout_ms: int = 0, predict_pairs: bool = False, dense_threshold: int = 0,
                  warp_chunks_below: int = 0, phase2_sets: int = 0, phase2_priority: int = 0,
+                 arena_words: int = 0,
                  stream=None):
         torch = _torch()
         self._torch = torch
@@ -149,6 +150,7 @@ class Context:
         opts.warp_chunks_below = int(warp_chunks_below)
         opts.phase2_sets = int(phase2_sets)
         opts.phase2_priority = int(phase2_priority)
+        opts.arena_words = int(arena_words)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
         dev_index = self.device.index if self.device.index is not None else 0

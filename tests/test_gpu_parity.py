@@ -465,6 +465,21 @@ def test_budgeted_phase2_batched_and_partial(ph, orc):
         ph.Context(phase2_priority=2)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_capacity_growth_between_passes(ph, orc, use_graph):
+    # one-word arenas: passes stop before any change, the host grows the arena and the pass
+    # runs again; results, passes and counters are those of an unconstrained run
+    x = pc.random_cloud(60, 3, 12)
+    K = orc.vr_build(x, 2)
+    ref = orc.reduce_pms(K)
+    for extra in ({}, {"warp_chunks_below": 1 << 30}, {"dense_threshold": 1}):
+        ctx = _gpu(ph, x, 2, use_graph=use_graph, arena_words=1, **extra)
+        st = ctx.reduce()
+        assert st["passes"] == ref.passes
+        _check_reduced(orc, ctx, 0, K)
+        _check_counters(ctx, ref)
+
+
 def test_invalid_arguments(ph):
     import torch
 
