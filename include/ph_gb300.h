@@ -65,14 +65,15 @@ typedef struct {
   /* 1 (default): zero case of Corollary 10 -- a column with beta_j = 0 whose candidate rows
    * (all rows of K_{d-1} up to low(j)) are all known to be paired is set to zero. */
   int32_t use_cor10;
-  /* threads per block of the per-column kernels (0 = library default, 256) */
+  /* reserved: the per-column kernels run 256-thread blocks (a compile-time constant of their
+   * scans); the value is ignored */
   int32_t block_threads;
   /* Phase II merges of more rows than this (target + source) run from global memory; shorter
    * ones are staged in shared memory first (0 = library default = the largest staged size,
    * 1024) */
   int32_t staged_merge_max;
   /* merge-path positions per lane in Phase II (1..64); 0 (default) picks one per warp from
-   * the mean length of its merges (4 below 32 rows, 8 below 80, 16 below 160, else 32) */
+   * the mean length of its staged merges (4 below 32 rows, 8 below 80, else 16) */
   int32_t merge_items;
   /* 1: per-pass counters are collected (column additions, XORs, pivots, ...) */
   int32_t collect_stats;
@@ -101,12 +102,16 @@ typedef struct {
    * identical either way. 0 (default): the threshold is 32 rows, so a column goes bit-packed
    * once the bitmap is its smaller form; < 0: never. */
   int32_t dense_threshold;
-  /* Phase II work shape: while the active list holds at least this many columns, a block of 4
-   * warps claims 128 columns at a time (one block scan and barrier per chunk); below it every
-   * warp claims its own 32 columns (no block barriers, 4x the queue atomics). The list only
-   * shrinks, so a reduction switches at most once. Results are identical either way.
+  /* Phase II work shape: a block of 4 warps claims 128 columns at a time (one block scan and
+   * barrier per chunk) until, at the end of some pass, fewer than this many columns are active
+   * and their jobs are long (warp_chunk_words or more arena words reserved per survivor, on
+   * average); from then on every warp claims its own 32 columns (no block barriers, 4x the
+   * queue atomics). A reduction switches at most once. Results are identical either way.
    * 0 (default): 4,194,304; < 0: block chunks throughout. */
   int32_t warp_chunks_below;
+  /* The job length that switch needs, in mean arena words per survivor. 0 (default): 40;
+   * < 0: any (then a complex of fewer than warp_chunks_below columns starts with warp chunks). */
+  int32_t warp_chunk_words;
   /* Phase II with p processors (Sec. 3.4.1-3.4.2). phase2_sets = p > 0: each pass the targets
    * fall into neighbour sets, one per low row i, holding the targets whose addition the pass
    * may do; only the targets of the first p sets in priority order receive their addition, the

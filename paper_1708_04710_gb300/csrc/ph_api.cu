@@ -280,6 +280,7 @@ void ph_default_opts(ph_opts* o) {
   o->predict_pairs = 0;
   o->dense_threshold = 0;
   o->warp_chunks_below = 0;
+  o->warp_chunk_words = 0;
   o->phase2_sets = 0;
   o->phase2_priority = 0;
   o->arena_words = 0;

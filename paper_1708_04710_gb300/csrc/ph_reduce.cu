@@ -74,11 +74,13 @@ struct DevState {
   // stops once there (ST_SWITCH) so that the host continues it with that kernel
   int32_t dense_on;
   int32_t dense_want;
-  // Phase II work shape: 128-slot chunks per block while the active list is long, 32-slot
-  // chunks per warp (no block barriers, more queue atomics) once it holds fewer than warp_below
-  // columns; the list only shrinks, so this also switches once (ST_SWITCH)
+  // Phase II work shape: 128-slot chunks per block while the active list is long or its jobs
+  // short, 32-slot chunks per warp (no block barriers, more queue atomics) once it holds fewer
+  // than warp_below columns whose survivors reserve warp_words or more arena words on
+  // average; this switches once per reduction (ST_SWITCH)
   int32_t warp_on;
   int64_t warp_below;
+  int64_t warp_words;  // the mean arena words per survivor the switch needs
 };
 
 struct RArgs {
@@ -1528,7 +1530,10 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
       ds->passes = p;
     } else {
       ds->pass = p + 1;
-      const bool to_warp = !ds->warp_on && ds->n_act < ds->warp_below;
+      // ... and only once the jobs are long (mean arena words per survivor), where warps of one
+      // block would otherwise wait on each other's merges
+      const bool to_warp = !ds->warp_on && ds->n_act < ds->warp_below &&
+                           ds->arena_used >= (unsigned long long)ds->warp_words * ds->totals[0];
       if (to_warp) ds->warp_on = 1;
       // the pass is complete, so a later call can resume from the next one
       if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
@@ -1784,7 +1789,11 @@ void reduce_init(ph_ctx* ctx) {
   h.warp_below = ctx->opts.warp_chunks_below < 0   ? 0
                  : ctx->opts.warp_chunks_below == 0 ? (int64_t)1 << 22
                                                     : ctx->opts.warp_chunks_below;
-  h.warp_on = m < h.warp_below ? 1 : 0;
+  h.warp_words = ctx->opts.warp_chunk_words < 0    ? 0
+                 : ctx->opts.warp_chunk_words == 0 ? 40
+                                                   : ctx->opts.warp_chunk_words;
+  // the first passes' jobs are short: block chunks, unless any job length will do
+  h.warp_on = h.warp_words == 0 && m < h.warp_below ? 1 : 0;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
   PH_CUDA(cudaFuncSetAttribute(k_add<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kAddSmem));

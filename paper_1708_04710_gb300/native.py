@@ -32,7 +32,8 @@ class PhOpts(Structure):
                 ("collect_stats", c_int32), ("use_graph", c_int32), ("time_kernels", c_int32),
                 ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32),
                 ("predict_pairs", c_int32), ("dense_threshold", c_int32),
-                ("warp_chunks_below", c_int32), ("phase2_sets", c_int32),
+                ("warp_chunks_below", c_int32), ("warp_chunk_words", c_int32),
+                ("phase2_sets", c_int32),
                 ("phase2_priority", c_int32), ("arena_words", c_int64)]
 
 
@@ -127,7 +128,8 @@ class Context:
                  collect_stats: bool = False, staged_merge_max: int = 0, merge_items: int = 0,
                  use_graph: bool = True, time_kernels: bool = False, add_blocks_per_sm: int = 0,
                  timeout_ms: int = 0, predict_pairs: bool = False, dense_threshold: int = 0,
-                 warp_chunks_below: int = 0, phase2_sets: int = 0, phase2_priority: int = 0,
+                 warp_chunks_below: int = 0, warp_chunk_words: int = 0, phase2_sets: int = 0,
+                 phase2_priority: int = 0,
                  arena_words: int = 0,
                  stream=None):
         torch = _torch()
@@ -148,6 +150,7 @@ class Context:
         opts.predict_pairs = int(predict_pairs)
         opts.dense_threshold = int(dense_threshold)
         opts.warp_chunks_below = int(warp_chunks_below)
+        opts.warp_chunk_words = int(warp_chunk_words)
         opts.phase2_sets = int(phase2_sets)
         opts.phase2_priority = int(phase2_priority)
         opts.arena_words = int(arena_words)

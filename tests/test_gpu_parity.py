@@ -271,11 +271,12 @@ def test_bit_packed_columns_modes_and_batches(ph, orc, strict, cor10):
 def test_chunk_shapes_agree(ph, orc, below, use_graph):
     # Phase II in 128-slot block chunks throughout (-1), 32-slot warp chunks throughout (2^30),
     # or switching from the first to the second mid-reduction (the active list drops below 20,000
-    # or 3,000 columns); a batch of clouds, and a dense-mode run, switch too
+    # or 3,000 columns); a batch of clouds, and a dense-mode run, switch too. Any job length
+    # allows the switch here (warp_chunk_words = -1), so that these short jobs take it
     x = pc.random_cloud(60, 3, 12)
     K = orc.vr_build(x, 2)
     ref = orc.reduce_pms(K)
-    ctx = _gpu(ph, x, 2, use_graph=use_graph, warp_chunks_below=below)
+    ctx = _gpu(ph, x, 2, use_graph=use_graph, warp_chunks_below=below, warp_chunk_words=-1)
     st = ctx.reduce()
     assert st["passes"] == ref.passes
     assert np.array_equal(ctx.filtration(0)["low"], ref.low)
@@ -284,14 +285,14 @@ def test_chunk_shapes_agree(ph, orc, below, use_graph):
     clouds = [pc.random_cloud(n, 3, 300 + i) for i, n in enumerate(sizes)]
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     ctx = _gpu(ph, np.concatenate(clouds), 2, offsets=off, use_graph=use_graph,
-               warp_chunks_below=below // 2 if below > 0 else below)
+               warp_chunks_below=below // 2 if below > 0 else below, warp_chunk_words=-1)
     ctx.reduce()
     for c, xc in enumerate(clouds):
         _check_reduced(orc, ctx, c, orc.vr_build(xc, 2))
     xd = pc.random_cloud(11, 3, 31)
     Kd = orc.vr_build(xd, 4)
     refd = orc.reduce_pms(Kd)
-    ctx = _gpu(ph, xd, 4, use_graph=use_graph, dense_threshold=1,
+    ctx = _gpu(ph, xd, 4, use_graph=use_graph, dense_threshold=1, warp_chunk_words=-1,
                warp_chunks_below=min(below, 2000) if below > 0 else below)
     ctx.reduce()
     assert np.array_equal(ctx.filtration(0)["low"], refd.low)
@@ -472,7 +473,8 @@ def test_capacity_growth_between_passes(ph, orc, use_graph):
     x = pc.random_cloud(60, 3, 12)
     K = orc.vr_build(x, 2)
     ref = orc.reduce_pms(K)
-    for extra in ({}, {"warp_chunks_below": 1 << 30}, {"dense_threshold": 1}):
+    for extra in ({}, {"warp_chunks_below": 1 << 30, "warp_chunk_words": -1},
+                  {"dense_threshold": 1}):
         ctx = _gpu(ph, x, 2, use_graph=use_graph, arena_words=1, **extra)
         st = ctx.reduce()
         assert st["passes"] == ref.passes
