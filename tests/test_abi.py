@@ -52,3 +52,31 @@ def test_context_fails_loudly_without_gpu(lib_path):
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         native.Context()
+
+
+@pytest.mark.parametrize("cname,pyname", [("ph_opts", "PhOpts"), ("ph_stats", "PhStats"),
+                                          ("ph_allocator", "PhAllocator")])
+def test_struct_layout_matches_binding(tmp_path, cname, pyname):
+    # the C compiler's view of the header (size and every field's offset) against ctypes'
+    import shutil
+    import subprocess
+
+    from paper_1708_04710_gb300 import native
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    py = getattr(native, pyname)
+    names = [f[0] for f in py._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ph_gb300.h"',
+             "int main(void) {", f'  printf("%zu\\n", sizeof({cname}));']
+    lines += [f'  printf("%zu\\n", offsetof({cname}, {n}));' for n in names]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = [ctypes.sizeof(py)] + [getattr(py, n).offset for n in names]
+    assert got == want, (cname, list(zip(["sizeof"] + names, got, want)))
