@@ -101,7 +101,7 @@ struct RArgs {
   int cor10;
   SegMax* tile_sm;    // [ntiles] Phase I tile aggregates (scanned in place to prefixes)
   SegMax* chunk_sm;   // [ntiles][kRItems] aggregate of each 256-entry chunk alone
-  unsigned long long* look;  // per 256-entry chunk: look-back state of the survivor count
+  unsigned long long* look;  // per Phase II chunk: look-back state of the survivor count
   int32_t* dlist;     // active slots whose column update waits for k_commit
   int32_t* src_e;     // per active slot: the colliding column's left-most column, -1 if none
   // bit-packed columns: a job's result is a bitmap over its row segment when the sum of the two
@@ -1080,15 +1080,16 @@ __device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p
   }
 }
 
-// Phase II for one 256-entry chunk of the active list. Survivors get their place in the next
-// active list from a block scan plus the look-back, and their rows a slot of the next arena
-// from a warp-aggregated atomic. New pivots are copied to the pivot store; survivors (with or
-// without an addition) are merged in registers (short columns, one thread per job) or staged
-// in shared memory and merged by a merge path over the concatenation of the batch's jobs, each
-// padded to a multiple of km positions (km chosen per warp from the mean merge length); merges
-// longer than the staging bound run from global memory. Targets and zeroed columns are updated
-// in place (no other job reads them this pass); new pivots and left-most survivors, which other
-// jobs may be reading as sources, are updated by k_commit.
+// Phase II for one chunk of the active list (128 slots of a block, or 32 of a warp). Survivors
+// get their place in the next active list from a block (or warp) scan plus the look-back, and
+// their rows a slot of the next arena from one atomic per chunk. New pivots are copied to the
+// pivot store, one run per warp; survivors (with or without an addition) are merged in
+// registers (short columns, one thread per job) or staged in shared memory and merged by a
+// merge path over the concatenation of the batch's jobs, each padded to a multiple of km
+// positions (km chosen per warp from the mean merge length); merges longer than the staging
+// bound run from global memory; bit-packed jobs run one at a time by the whole warp. Targets
+// and zeroed columns are updated in place (no other job reads them this pass); new pivots and
+// left-most survivors, which other jobs may be reading as sources, are updated by k_commit.
 enum : int {
   kCntTargets, kCntActive, kCntCleared, kCntAdds, kCntXors, kCntCopied, kCntPacked, kNumCnt
 };
@@ -1697,15 +1698,19 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   PH_CHECK_LAUNCH();
 }
 
+// the new buffer is taken before the old one goes, so a failed allocation (PH_ERR_ALLOC)
+// leaves the store, and the device state that points into it, as it was: a later call resumes
 static void grow_store(ph_ctx* ctx, ColStore& s, int64_t need_words) {
   if (need_words <= s.cap) return;
+  const int64_t cap = std::max<int64_t>(need_words + need_words / 4, 1 << 20);
+  int32_t* p = alloc_n<int32_t>(ctx, cap);
   if (s.p) ctx->dfree(s.p);
-  int64_t cap = std::max<int64_t>(need_words + need_words / 4, 1 << 20);
-  s.p = alloc_n<int32_t>(ctx, cap);
+  s.p = p;
   s.cap = cap;
 }
 
 void reduce_init(ph_ctx* ctx) {
+  free_reduce_state(ctx);  // whatever an earlier, failed initialisation left
   ReduceState& rs = ctx->rs;
   cudaStream_t st = ctx->stream;
   const int64_t m = ctx->m;

@@ -131,7 +131,7 @@ class Context:
                  warp_chunks_below: int = 0, warp_chunk_words: int = 0, phase2_sets: int = 0,
                  phase2_priority: int = 0,
                  arena_words: int = 0,
-                 stream=None):
+                 stream=None, device_alloc=None, device_free=None):
         torch = _torch()
         self._torch = torch
         self.lib = load_library()
@@ -158,14 +158,21 @@ class Context:
         self.device = self.stream.device
         dev_index = self.device.index if self.device.index is not None else 0
 
+        # device memory: torch's caching allocator, or the caller's device_alloc(nbytes, stream)
+        # -> pointer (0 / None: out of memory) and device_free(pointer)
         def _alloc(nbytes, user, stream):
             try:
+                if device_alloc is not None:
+                    return device_alloc(int(nbytes), stream or 0) or None
                 return torch.cuda.caching_allocator_alloc(int(nbytes), dev_index, stream or 0)
             except Exception:  # out of memory: the library reports PH_ERR_ALLOC
                 return None
 
         def _free(ptr, nbytes, user, stream):
-            torch.cuda.caching_allocator_delete(ptr)
+            if device_free is not None:
+                device_free(ptr)
+            else:
+                torch.cuda.caching_allocator_delete(ptr)
 
         self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))  # keep the callbacks alive
         self._allocator = PhAllocator(self._cb[0], self._cb[1], None)

@@ -482,6 +482,57 @@ def test_capacity_growth_between_passes(ph, orc, use_graph):
         _check_counters(ctx, ref)
 
 
+def test_allocation_failures_are_reported_and_resumable(ph, orc):
+    # Allocation failures injected through the binding's allocator hook. Wherever a failure
+    # hits -- the build, the reduction's set-up, or an arena grown between passes (one-word
+    # arenas) -- the call returns PH_ERR_ALLOC without touching the GPU state it cannot
+    # finish. Once allocations succeed again, the same calls resume and give the oracle's exact
+    # reduction, counters included.
+    import torch
+
+    x = pc.random_cloud(60, 3, 12)
+    K = orc.vr_build(x, 2)
+    ref = orc.reduce_pms(K)
+    xt = torch.from_numpy(x).cuda()
+
+    def run(fail_at, use_graph):
+        state = {"calls": 0, "fail": fail_at is not None, "where": None}
+
+        def alloc(nbytes, stream):
+            state["calls"] += 1
+            if state["fail"] and state["calls"] > fail_at:
+                return 0
+            return torch.cuda.caching_allocator_alloc(nbytes, 0, stream)
+
+        ctx = ph.Context(collect_stats=True, arena_words=1, use_graph=use_graph,
+                         device_alloc=alloc, device_free=torch.cuda.caching_allocator_delete)
+        for _ in range(2):
+            try:
+                if not ctx.m:
+                    ctx.build_filtration(xt, None, 2)
+                    state["built_at"] = state["calls"]
+                st = ctx.reduce()
+                state["reduced_at"] = state["calls"]
+                break
+            except ph.PHError as err:
+                assert err.code == -2 and state["where"] is None, err
+                state["where"] = "build" if not ctx.m else "reduce"
+                state["fail"] = False
+        assert st["converged"] and st["passes"] == ref.passes
+        assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+        ctx.close()
+        return state
+
+    clean = run(None, True)
+    n_build, n_all = clean["built_at"], clean["reduced_at"]
+    assert n_all > n_build + 2  # the reduction allocates, and grows its arenas
+    for use_graph in (True, False):
+        seen = [run(k, use_graph)["where"] for k in
+                (0, n_build // 2, n_build, n_build + 1, n_all - 2, n_all - 1)]
+        assert seen[:2] == ["build", "build"] and set(seen[2:]) == {"reduce"}, seen
+
+
 def test_invalid_arguments(ph):
     import torch
 
