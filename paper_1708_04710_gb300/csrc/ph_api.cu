@@ -244,9 +244,10 @@ __global__ void k_inspect(int64_t lo, int64_t hi, const int32_t* __restrict__ se
 // ---------------------------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------------------------
-#define PH_API_BEGIN \
-  if (!ctx) return PH_ERR_INVALID; \
-  ctx->err.clear();                \
+#define PH_API_BEGIN                  \
+  if (!ctx) return PH_ERR_INVALID;    \
+  ctx->err.clear();                   \
+  ph::NvtxRange nvtx_range_(__func__); \
   try {
 #define PH_API_END                                    \
   }                                                   \

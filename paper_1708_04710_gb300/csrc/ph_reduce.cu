@@ -1924,6 +1924,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
 
   for (;;) {
     const int32_t first_pass = h.pass;
+    NvtxRange nvtx_range_(use_graph ? "pass loop (graph)" : "pass");
     if (use_graph) {
       const int variant = (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0);
       if (!rs.graph_exec[variant]) build_graph(ctx, a, variant);
