@@ -285,6 +285,22 @@ int ph_get_essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* in_e, int64_t
  * Needs ph_reduce first with predict_pairs = 1. Synchronises the stream. */
 int ph_get_predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* pred, int64_t* count);
 
+/* The reduced matrix R of cloud `cloud` as the last ph_reduce left it (complete or partial),
+ * in compressed columns over the cloud's filtration indices: column f holds
+ * rows[colptr[f] .. colptr[f + 1] - 1], the filtration indices of its rows, ascending. R comes
+ * from D by left-to-right column additions (Sec. 2.3), except for columns set to zero as
+ * positive (clearing, Lemma 1; Corollary 10), which are empty. Once the reduction is complete,
+ * a negative column j holds a cycle that becomes a boundary at j: a representative of the
+ * class born at low(j) and killed by j (Lemma 1).
+ *   colptr  host int64 [count + 1], count being the cloud's number of simplices
+ *           (ph_get_filtration); always filled.
+ *   rows    host int32 [capacity], or NULL to learn *nnz first.
+ *   nnz     host, optional: total number of rows.
+ * PH_ERR_CAPACITY if rows is too small (colptr and *nnz are filled all the same). Needs
+ * ph_reduce first. Synchronises the stream. */
+int ph_get_columns(ph_ctx* ctx, int32_t cloud, int64_t* colptr, int32_t* rows, int64_t capacity,
+                   int64_t* nnz);
+
 /* Inspection of the filtration of cloud `cloud` in filtration order, for testing the build
  * against an independent implementation. Host buffers of `count` entries (any may be NULL):
  *   dim int32; diam2 int64; verts int32 [count][6] (-1 padded); beta int32 (Definition 4, as

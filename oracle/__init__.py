@@ -69,6 +69,9 @@ def _load():
         L.orc_reduce_twist.restype = ctypes.c_int
         L.orc_reduce_pms.argtypes = [i64, P, P, P, P, i32, i32, i32, i32, i32, P, P, P, P, P, P]
         L.orc_reduce_pms.restype = ctypes.c_int
+        L.orc_reduce_pms_columns.argtypes = [i64, P, P, P, P, i32, i32, i32, i32, i32, P, P, P,
+                                             i64, P]
+        L.orc_reduce_pms_columns.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -210,6 +213,28 @@ def reduce_pms(K: Complex, max_passes: int = 100000, strict: bool = False, cor10
     p = npass.value
     return PmsResult(low=low, passes=p, stats=ps[:p + 1], ess_est=ess[:m].astype(bool),
                      proven=proven[:m].astype(bool), predicted=pred[:m], converged=(rc == 0))
+
+
+def reduce_pms_columns(K: Complex, max_passes: int = 100000, strict: bool = False,
+                       cor10: bool = True, sets: int = 0, priority: int = 0):
+    """The reduced matrix R that Algorithm 2 (as reduce_pms) leaves: (colptr int64 [m + 1],
+    rows int32 [nnz]), CSC with ascending rows."""
+    L = _load()
+    m = K.m
+    b = beta(K)
+    low = np.empty(max(m, 1), np.int32)
+    cp = np.zeros(m + 1, np.int64)
+    nnz = ctypes.c_int64(0)
+    args = (m, _ptr(K["colptr"]), _ptr(K["rows"]), _ptr(K["dim"]), _ptr(b), max_passes,
+            int(strict), int(cor10), int(sets), int(priority), _ptr(low), _ptr(cp))
+    rc = L.orc_reduce_pms_columns(*args, None, 0, ctypes.byref(nnz))
+    if rc < 0:
+        raise RuntimeError(rc)
+    rows = np.zeros(max(nnz.value, 1), np.int32)
+    rc = L.orc_reduce_pms_columns(*args, _ptr(rows), nnz.value, ctypes.byref(nnz))
+    if rc < 0:
+        raise RuntimeError(rc)
+    return cp, rows[:nnz.value]
 
 
 def pairs_and_essential(low: np.ndarray, dim: np.ndarray):

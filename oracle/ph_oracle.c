@@ -506,11 +506,14 @@ static int cmp_sets(const void* a, const void* b) {
   return x < y ? -1 : (x > y);
 }
 
-int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const int32_t* dim,
+/* The reduced matrix R at the end (optional, r_colptr != NULL): CSC with m + 1 offsets and,
+ * when r_rows is given and holds r_cap entries, the rows; *r_nnz receives their number. */
+static int pms_run(int64_t m, const int64_t* colptr, const int32_t* rows, const int32_t* dim,
                    const int32_t* beta, int32_t max_passes, int32_t strict, int32_t use_cor10,
                    int32_t sets, int32_t priority, int32_t* low_out, int64_t* pass_stats,
                    int32_t* passes_out, uint8_t* ess_est_out, uint8_t* proven_out,
-                   int32_t* pred_out) {
+                   int32_t* pred_out, int64_t* r_colptr, int32_t* r_rows, int64_t r_cap,
+                   int64_t* r_nnz) {
   col_t* R = cols_from_csc(m, colptr, rows);
   int64_t M = m > 0 ? m : 1;
   int32_t* low = (int32_t*)malloc((size_t)M * sizeof(int32_t));
@@ -668,6 +671,14 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
   if (ess_est_out) memcpy(ess_est_out, in_E, (size_t)m);
   if (proven_out) memcpy(proven_out, proven, (size_t)m);
   if (pred_out) memcpy(pred_out, pred, (size_t)m * sizeof(int32_t));
+  if (r_colptr) {
+    r_colptr[0] = 0;
+    for (int64_t j = 0; j < m; j++) r_colptr[j + 1] = r_colptr[j] + R[j].n;
+    if (r_nnz) *r_nnz = r_colptr[m];
+    if (r_rows && r_colptr[m] <= r_cap)
+      for (int64_t j = 0; j < m; j++)
+        memcpy(r_rows + r_colptr[j], R[j].v, (size_t)R[j].n * sizeof(int32_t));
+  }
   cols_free(R, m);
   free(low);
   free(tab);
@@ -685,4 +696,25 @@ int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const 
   free(set_on);
   free(tmp.v);
   return status;
+}
+
+int orc_reduce_pms(int64_t m, const int64_t* colptr, const int32_t* rows, const int32_t* dim,
+                   const int32_t* beta, int32_t max_passes, int32_t strict, int32_t use_cor10,
+                   int32_t sets, int32_t priority, int32_t* low_out, int64_t* pass_stats,
+                   int32_t* passes_out, uint8_t* ess_est_out, uint8_t* proven_out,
+                   int32_t* pred_out) {
+  return pms_run(m, colptr, rows, dim, beta, max_passes, strict, use_cor10, sets, priority,
+                 low_out, pass_stats, passes_out, ess_est_out, proven_out, pred_out, NULL, NULL,
+                 0, NULL);
+}
+
+/* orc_reduce_pms that also returns the reduced matrix R (CSC, rows ascending): call with
+ * r_rows = NULL for r_colptr and *r_nnz, then with r_rows of r_cap >= *r_nnz entries. */
+int orc_reduce_pms_columns(int64_t m, const int64_t* colptr, const int32_t* rows,
+                           const int32_t* dim, const int32_t* beta, int32_t max_passes,
+                           int32_t strict, int32_t use_cor10, int32_t sets, int32_t priority,
+                           int32_t* low_out, int64_t* r_colptr, int32_t* r_rows, int64_t r_cap,
+                           int64_t* r_nnz) {
+  return pms_run(m, colptr, rows, dim, beta, max_passes, strict, use_cor10, sets, priority,
+                 low_out, NULL, NULL, NULL, NULL, NULL, r_colptr, r_rows, r_cap, r_nnz);
 }

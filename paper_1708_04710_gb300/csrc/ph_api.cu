@@ -487,6 +487,21 @@ int ph_get_essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* in_e, int64_t
   PH_API_END
 }
 
+int ph_get_columns(ph_ctx* ctx, int32_t cloud, int64_t* colptr, int32_t* rows, int64_t capacity,
+                   int64_t* nnz) {
+  PH_API_BEGIN
+  PH_REQUIRE(ctx->reduced && ctx->rs.init, PH_ERR_INVALID, "call ph_reduce first");
+  PH_REQUIRE(cloud >= 0 && cloud < ctx->n_clouds, PH_ERR_INVALID, "cloud out of range");
+  PH_REQUIRE(colptr != nullptr, PH_ERR_INVALID, "colptr is required");
+  const int nc = ctx->n_clouds;
+  int64_t n = 0;
+  for (int d = 0; d <= ctx->max_dim; d++)
+    n += ctx->seg_start[d * nc + cloud + 1] - ctx->seg_start[d * nc + cloud];
+  ph::reduced_columns(ctx, cloud, n, colptr, rows, capacity, nnz);
+  return PH_OK;
+  PH_API_END
+}
+
 int ph_get_predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* pred, int64_t* count) {
   PH_API_BEGIN
   PH_REQUIRE(ctx->reduced && ctx->rs.init, PH_ERR_INVALID, "call ph_reduce first");

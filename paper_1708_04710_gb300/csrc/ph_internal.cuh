@@ -318,6 +318,8 @@ void free_reduce_state(ph_ctx* ctx);
 void essential_estimate(ph_ctx* ctx, int32_t cloud, uint8_t* host_out, int64_t n);
 // predicted lowstar per simplex of one cloud (filtration indices, -1), into host memory
 void predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* host_out, int64_t n);
+void reduced_columns(ph_ctx* ctx, int32_t cloud, int64_t n, int64_t* colptr, int32_t* rows,
+                     int64_t capacity, int64_t* nnz_out);
 // generic device helpers (ph_scan.cu)
 void excl_scan_i64(ph_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev);
 void radix_sort_u64(ph_ctx* ctx, uint64_t* keys, uint64_t* vals, int64_t n, int lo_bit,

@@ -2046,6 +2046,109 @@ void predicted_lows(ph_ctx* ctx, int32_t cloud, int32_t* host_out, int64_t n) {
   PH_REQUIRE(bad == 0, PH_ERR_INVALID, "internal error: filtration index out of range");
 }
 
+// ------------------------------------------------------------------------------------------
+// the reduced matrix R of one cloud, CSC over its filtration indices
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int32_t col_rows(const ColMeta& mx) {
+  return mx.len >= 0 ? mx.len : mx.ptr[0];  // a bit-packed column's header holds its rows
+}
+
+__global__ void k_col_counts(int64_t lo, int64_t hi, const ColMeta* __restrict__ meta,
+                             const int64_t* __restrict__ gidx, int64_t n, int64_t* cnt,
+                             int32_t* bad) {
+  for (int64_t x = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < hi;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = gidx[x];
+    if (f < 0 || f >= n) {
+      *bad = 1;
+      continue;
+    }
+    cnt[f] = col_rows(load_meta(meta + x));
+  }
+}
+
+// rows as filtration indices of the same cloud, ascending (ids of one dimension and cloud are in
+// filtration order); a bitmap is read word by word, bit by bit
+__global__ void k_col_rows(int64_t lo, int64_t hi, const ColMeta* __restrict__ meta,
+                           const int64_t* __restrict__ gidx, const int32_t* __restrict__ seg,
+                           const int64_t* __restrict__ seg_start, int nc,
+                           const int64_t* __restrict__ off, int64_t n, int64_t nnz, int32_t* out,
+                           int32_t* bad) {
+  for (int64_t x = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < hi;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = gidx[x];
+    if (f < 0 || f >= n) {
+      *bad = 1;
+      continue;
+    }
+    const ColMeta mx = load_meta(meta + x);
+    int32_t* o = out + off[f];
+    const int64_t room = nnz - off[f];
+    int64_t k = 0;
+    if (mx.len >= 0) {
+      for (int32_t q = 0; q < mx.len && k < room; q++) o[k++] = (int32_t)gidx[mx.ptr[q]];
+    } else {
+      const int rs = seg[x] - nc;
+      const int64_t base = seg_start[rs];
+      const int64_t words = (seg_start[rs + 1] - base + 31) / 32;
+      const uint32_t* bits = reinterpret_cast<const uint32_t*>(mx.ptr + kDenseHead);
+      for (int64_t w = 0; w < words; w++)
+        for (uint32_t b = bits[w]; b && k < room; b &= b - 1)
+          o[k++] = (int32_t)gidx[base + 32 * w + (__ffs(b) - 1)];
+    }
+    if (k != col_rows(mx)) *bad = 1;
+  }
+}
+
+void reduced_columns(ph_ctx* ctx, int32_t cloud, int64_t n, int64_t* colptr, int32_t* rows,
+                     int64_t capacity, int64_t* nnz_out) {
+  ReduceState& rs = ctx->rs;
+  const int nc = ctx->n_clouds;
+  const ColMeta* meta = static_cast<const ColMeta*>(rs.meta);
+  int64_t* d_off = alloc_n<int64_t>(ctx, n + 1);
+  int32_t* d_bad = alloc_n<int32_t>(ctx, 1);
+  PH_CUDA(cudaMemsetAsync(d_off, 0, (size_t)(n + 1) * sizeof(int64_t), ctx->stream));
+  PH_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int32_t), ctx->stream));
+  for (int d = 0; d <= ctx->max_dim; d++) {
+    const int64_t lo = ctx->seg_start[d * nc + cloud], hi = ctx->seg_start[d * nc + cloud + 1];
+    if (hi <= lo) continue;
+    k_col_counts<<<grid_for(ctx, hi - lo, kThreads), kThreads, 0, ctx->stream>>>(
+        lo, hi, meta, ctx->gidx, n, d_off, d_bad);
+    PH_CHECK_LAUNCH();
+  }
+  excl_scan_i64(ctx, d_off, d_off, n + 1, nullptr);
+  PH_CUDA(cudaMemcpyAsync(colptr, d_off, (size_t)(n + 1) * sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  PH_CUDA(cudaStreamSynchronize(ctx->stream));
+  const int64_t nnz = colptr[n];
+  if (nnz_out) *nnz_out = nnz;
+  int32_t bad = 0;
+  if (rows && nnz <= capacity && nnz > 0) {
+    int32_t* d_rows = alloc_n<int32_t>(ctx, nnz);
+    for (int d = 0; d <= ctx->max_dim; d++) {
+      const int64_t lo = ctx->seg_start[d * nc + cloud], hi = ctx->seg_start[d * nc + cloud + 1];
+      if (hi <= lo) continue;
+      k_col_rows<<<grid_for(ctx, hi - lo, kThreads), kThreads, 0, ctx->stream>>>(
+          lo, hi, meta, ctx->gidx, ctx->seg, ctx->d_seg_start, nc, d_off, n, nnz, d_rows, d_bad);
+      PH_CHECK_LAUNCH();
+    }
+    PH_CUDA(cudaMemcpyAsync(rows, d_rows, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    PH_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    PH_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->dfree(d_rows);
+  } else {
+    PH_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    PH_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->dfree(d_off);
+  ctx->dfree(d_bad);
+  PH_REQUIRE(bad == 0, PH_ERR_INVALID, "internal error: column index out of range");
+  PH_REQUIRE(!rows || nnz <= capacity, PH_ERR_CAPACITY,
+             "rows holds " + std::to_string(capacity) + " entries, the columns need " +
+                 std::to_string(nnz));
+}
+
 void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
   for (int d = 0; d < 4; d++) {

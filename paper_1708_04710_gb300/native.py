@@ -80,6 +80,8 @@ SIGNATURES = {
     "ph_get_add_times": (c_int, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "ph_get_essential_estimate": (c_int, [c_void_p, c_int32, c_void_p, POINTER(c_int64)]),
     "ph_get_predicted_lows": (c_int, [c_void_p, c_int32, c_void_p, POINTER(c_int64)]),
+    "ph_get_columns": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_int64,
+                               POINTER(c_int64)]),
     "ph_kernel_launches": (c_int64, [c_void_p]),
     "ph_last_error": (c_char_p, [c_void_p]),
 }
@@ -321,6 +323,22 @@ class Context:
         out = np.zeros(n.value, np.int32)
         self._check(self.lib.ph_get_predicted_lows(self._h, int(cloud), _ptr(out), byref(n)))
         return out
+
+    def columns(self, cloud: int = 0):
+        """The reduced matrix R of the cloud as (colptr int64 [count + 1], rows int32), columns
+        and rows as filtration indices: for a negative column j of a complete reduction, the
+        rows of column j are a cycle representing the class born at low(j)."""
+        n = c_int64(0)
+        self._check(self.lib.ph_get_filtration(self._h, int(cloud), None, None, None, None,
+                                               None, byref(n)))
+        colptr = np.zeros(n.value + 1, np.int64)
+        nnz = c_int64(0)
+        self._check(self.lib.ph_get_columns(self._h, int(cloud), _ptr(colptr), None, 0,
+                                            byref(nnz)))
+        rows = np.zeros(max(nnz.value, 1), np.int32)
+        self._check(self.lib.ph_get_columns(self._h, int(cloud), _ptr(colptr), _ptr(rows),
+                                            nnz.value, byref(nnz)))
+        return colptr, rows[:nnz.value]
 
     def kernel_launches(self) -> int:
         return int(self.lib.ph_kernel_launches(self._h))

@@ -533,6 +533,49 @@ def test_allocation_failures_are_reported_and_resumable(ph, orc):
         assert seen[:2] == ["build", "build"] and set(seen[2:]) == {"reduce"}, seen
 
 
+R_OPTS = [
+    {},
+    {"dense_threshold": 1},
+    {"warp_chunks_below": 1 << 30, "warp_chunk_words": -1},
+    {"staged_merge_max": 1},
+    {"staged_merge_max": 16, "merge_items": 3},
+    {"strict_phase2": True},
+    {"use_cor10": False},
+    {"phase2_sets": 3, "phase2_priority": 1},
+]
+
+
+@pytest.mark.parametrize("opts", R_OPTS, ids=[",".join(o) or "default" for o in R_OPTS])
+def test_reduced_matrix_equals_oracle(ph, orc, opts):
+    # Every column of R, row by row, after complete and partial reductions: the column
+    # additions themselves (register networks, staged and global merge paths, bitmaps, both
+    # chunk shapes) against the oracle's sorted-array symmetric differences
+    okw = {"strict": opts.get("strict_phase2", False), "cor10": opts.get("use_cor10", True),
+           "sets": opts.get("phase2_sets", 0), "priority": opts.get("phase2_priority", 0)}
+    cases = [(pc.random_cloud(24, 3, 1), 2), (pc.random_cloud(11, 3, 31), 4), (pc.circle40(), 2),
+             (pc.random_cloud(60, 3, 12), 2)]
+    for x, k in cases:
+        K = orc.vr_build(x, k)
+        for mp in (-1, 2):
+            cp, rows = orc.reduce_pms_columns(K, **okw, **({} if mp < 0 else {"max_passes": mp}))
+            ctx = _gpu(ph, x, k, **opts)
+            ctx.reduce(max_passes=mp)
+            gcp, grows = ctx.columns(0)
+            assert np.array_equal(gcp, cp), (k, mp)
+            assert np.array_equal(grows, rows), (k, mp)
+    # a batch: each cloud's columns are those of the cloud reduced alone
+    if not opts.get("phase2_sets"):
+        sizes = [9, 20, 14]
+        clouds = [pc.random_cloud(n, 3, 700 + i) for i, n in enumerate(sizes)]
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        ctx = _gpu(ph, np.concatenate(clouds), 3, offsets=off, **opts)
+        ctx.reduce()
+        for c, xc in enumerate(clouds):
+            cp, rows = orc.reduce_pms_columns(orc.vr_build(xc, 3), **okw)
+            gcp, grows = ctx.columns(c)
+            assert np.array_equal(gcp, cp) and np.array_equal(grows, rows), c
+
+
 def test_invalid_arguments(ph):
     import torch
 

@@ -398,3 +398,40 @@ def test_budgeted_phase2_reaches_lowstar(orc, seed):
             if p >= K.m and not strict:
                 assert r.passes == full.passes
                 assert np.array_equal(r.stats, full.stats)
+
+
+@pytest.mark.parametrize("kw", [{}, {"strict": True}, {"sets": 2, "priority": 1},
+                                {"max_passes": 1}, {"max_passes": 3, "cor10": False}])
+def test_pms_reduced_matrix_spans_the_boundary_prefixes(orc, kw):
+    # The reduced matrix R that Algorithm 2 leaves comes from left-to-right additions (and
+    # zeroings of columns that are positive, Lemma 1 / Cor. 10), so for every j its first j
+    # columns span a subspace of the span of D's first j columns, with equality of ranks
+    # restricted to the columns that were not zeroed; its lows are reduce_pms's.
+    from helpers import _insert, dense_boundary
+
+    for seed, n, k in ((0, 9, 2), (1, 7, 3)):
+        K = orc.vr_build(pc.random_cloud(n, 3, 600 + seed), k)
+        cp, rows = orc.reduce_pms_columns(K, **kw)
+        ref = orc.reduce_pms(K, **kw)
+        m = K.m
+        low = np.array([rows[cp[j + 1] - 1] if cp[j + 1] > cp[j] else -1 for j in range(m)])
+        assert np.array_equal(low, ref.low)
+        if ref.converged:  # reduced: no two columns share a low
+            nz = low[low >= 0]
+            assert len(np.unique(nz)) == len(nz)
+        D = dense_boundary(K)
+        bd, bdr = {}, {}
+        for j in range(m):
+            vd = sum(1 << int(i) for i in np.nonzero(D[:, j])[0])
+            vr = sum(1 << int(i) for i in rows[cp[j]:cp[j + 1]])
+            _insert(bd, vd)
+            # column j of R lies in the span of D's first j + 1 columns
+            assert not _insert(dict(bd), vr) or vr == 0
+            _insert(bdr, vr)
+        # every column of D lies in the span of R plus the zeroed (positive) columns' D
+        zeroed = [j for j in range(m) if cp[j + 1] == cp[j]]
+        for j in zeroed:
+            _insert(bdr, sum(1 << int(i) for i in np.nonzero(D[:, j])[0]))
+        for j in range(m):
+            vd = sum(1 << int(i) for i in np.nonzero(D[:, j])[0])
+            assert not _insert(dict(bdr), vd)
