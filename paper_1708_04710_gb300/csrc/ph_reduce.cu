@@ -18,11 +18,16 @@
 //                pivot clears column low(j) (Lemma 1). Each active slot's source candidate is
 //                stored for Phase II.
 //   k_add        Phase II: every colliding column l gets column tab[low(l)] added (XOR of two
-//                sorted row lists). Sources are left-most, hence never targets, so additions
-//                are independent. Survivors take their place in the next active list by a
-//                decoupled look-back and their slot in the other arena by one atomic per chunk;
-//                new pivots move to the pivot store (their columns never change again). Blocks
-//                of 128 threads take 128-slot chunks from a device work queue.
+//                sorted row lists, or of bitmaps once a column fills in). Sources are
+//                left-most, hence never targets, so additions are independent. Survivors take
+//                their place in the next active list by a decoupled look-back and their slot in
+//                the other arena by one atomic per chunk; new pivots move to the pivot store
+//                (their columns never change again). Blocks of 128 threads take 128-slot chunks
+//                from a device work queue, or each warp 32 slots once the list is short and
+//                its jobs long. Four specialisations (row lists / bitmaps x block / warp
+//                chunks); the loop switches between them at most twice per reduction.
+//   (p sets)     With Phase II limited to p neighbour sets (Sec. 3.4), k_set_* rank the sets
+//                between k_mark and k_add and hold back the other targets.
 //   k_commit     publishes the new locations of the columns other jobs may have been reading;
 //                its last block ends the pass: the next active list, convergence (no collision
 //                left, Thm 8), the pass cap and time bound, and inside a CUDA graph the
