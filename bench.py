@@ -342,6 +342,16 @@ def main():
             "phases": {name: {"ms": t / args.steps,
                               "simplices_per_s": m_local * args.steps / (t / 1e3) if t else None}
                        for name, t in zip(("build_filtration", "reduce", "extract"), phase_ms)}}
+    # the build against the bytes a filtration must write: 16 B per simplex (diameter and
+    # vertex tuple), 4 B per boundary nonzero, 4 B of beta per simplex
+    counts = np.bincount(ctx.filtration(0)["dim"], minlength=1) if not wl.get("batched") else None
+    if counts is not None and phase_ms[0]:
+        nnz = int(sum((d + 1) * int(c) for d, c in enumerate(counts) if d > 0))
+        b_bytes = 20 * m_local + 4 * nnz
+        b_gbs = b_bytes / (phase_ms[0] / args.steps / 1e3) / 1e9
+        line["phases"]["build_filtration"]["roofline"] = {
+            "bound": "hbm", "achieved": b_gbs, "peak": peak, "unit": "GB/s", "frac": b_gbs / peak,
+            "bytes": b_bytes, "nnz": nnz}
     if world == 1 and not args.no_forms and not wl.get("batched"):
         line["forms"] = compare_forms(ph, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
