@@ -117,10 +117,10 @@ typedef struct {
    * may do; only the targets of the first p sets in priority order receive their addition, the
    * others stay active unchanged (and count as targets). phase2_priority 0: larger sets first
    * (Sec. 3.4.1); 1: sets with more targets known to be negative (beta >= 0, Thm 5) first,
-   * then larger sets (Sec. 3.4.2); ties by the smaller row. Any budget reaches the same lowstar
-   * (Sec. 2.3); passes and counters differ. The pass loop is then host-driven (use_graph is
-   * ignored). 0 (default): every set, as in Algorithm 2. ph_create rejects a priority other
-   * than 0 or 1 (PH_ERR_INVALID). */
+   * then larger sets (Sec. 3.4.2); ties by the row first in the filtration. Any budget reaches
+   * the same lowstar (Sec. 2.3); passes and counters differ. The pass loop is then host-driven
+   * (use_graph is ignored). 0 (default): every set, as in Algorithm 2. ph_create rejects a
+   * priority other than 0 or 1 (PH_ERR_INVALID). */
   int32_t phase2_sets;
   int32_t phase2_priority;
   /* Initial capacity of each of the two survivor arenas, in int32 words (0, default: twice the

@@ -578,18 +578,30 @@ __global__ void k_set_count(RArgs a) {
   }
 }
 
-// Sort keys of the sets: ascending key order is the priority order (priority 0: larger sets
-// first; 1: more known-negative targets first, then larger sets). The radix sort is stable and
-// the rows start in order, so equal keys keep the smaller row first; rows without a set sort
-// last. bits: enough for any count.
-__global__ void k_set_keys(RArgs a, int priority, int bits, uint64_t* key, uint64_t* row) {
-  const uint64_t top = (1ull << bits) - 1;
+// Ties between sets go to the row that comes first in its cloud's filtration (then to the
+// lower id): the rows are first sorted by their filtration index, and the stable sort by
+// priority below keeps that order among equal keys.
+__global__ void k_set_tiekeys(RArgs a, const int64_t* __restrict__ gidx, uint64_t* key,
+                              uint64_t* row) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.rows_end; i += stride) {
-    const uint64_t n = (uint64_t)a.set_n[i], g = (uint64_t)a.set_neg[i];
-    key[i] = priority == 1 ? ((top - g) << bits) | (top - n) : top - n;
+    key[i] = (uint64_t)gidx[i];
     row[i] = (uint64_t)i;
     a.set_on[i] = 0;
+  }
+}
+
+// Sort keys of the sets, in the current order of the rows: ascending key order is the priority
+// order (priority 0: larger sets first; 1: more known-negative targets first, then larger
+// sets); rows without a set sort last. bits: enough for any count.
+__global__ void k_set_keys(RArgs a, int priority, int bits, uint64_t* key,
+                           const uint64_t* __restrict__ row) {
+  const uint64_t top = (1ull << bits) - 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.rows_end; t += stride) {
+    const int64_t i = (int64_t)row[t];
+    const uint64_t n = (uint64_t)a.set_n[i], g = (uint64_t)a.set_neg[i];
+    key[t] = priority == 1 ? ((top - g) << bits) | (top - n) : top - n;
   }
 }
 
@@ -1670,6 +1682,9 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
     PH_CHECK_LAUNCH();
     uint64_t* key = rs.set_key;
     uint64_t* row = rs.set_key + rows;
+    k_set_tiekeys<<<grid_for(ctx, rows, kThreads), kThreads, 0, st>>>(a, ctx->gidx, key, row);
+    PH_CHECK_LAUNCH();
+    radix_sort_u64(ctx, key, row, rows, 0, bits, rs.set_key + 2 * rows, rs.set_key + 3 * rows);
     k_set_keys<<<grid_for(ctx, rows, kThreads), kThreads, 0, st>>>(
         a, ctx->opts.phase2_priority, bits, key, row);
     PH_CHECK_LAUNCH();

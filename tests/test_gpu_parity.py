@@ -710,3 +710,54 @@ def test_all_clouds_at_once(ph, orc):
     for k in ("birth", "death", "dim"):
         assert np.array_equal(allp[k].numpy(), np.concatenate([p[k].numpy() for p in parts]))
     assert np.array_equal(alle["idx"].numpy(), np.concatenate([e["idx"].numpy() for e in eparts]))
+
+
+def test_random_complexes_and_options(ph, orc):
+    # Seeded sweep: random small clouds (2-18 points, 1-4 coordinates, dimensions up to 5, with
+    # or without a diameter cut) under random combinations of the options; each run must give
+    # the oracle's lows, counters and reduced matrix, after a complete or a partial reduction
+    import torch
+
+    rng = np.random.default_rng(1708)
+    for case in range(200):
+        n = int(rng.integers(2, 19))
+        dim_cap = 5 if n <= 12 else (4 if n <= 15 else 3)
+        k = int(rng.integers(1, min(dim_cap, n - 1) + 1)) if n > 2 else 1
+        x = pc.random_cloud(n, int(rng.integers(1, 5)), 900 + case)
+        cut = -1
+        if rng.random() < 0.3:
+            d2 = ((x[:, None, :].astype(np.int64) - x[None, :, :]) ** 2).sum(-1)
+            cut = int(np.quantile(d2[np.triu_indices(n, 1)], rng.uniform(0.2, 0.9)))
+        opts = {}
+        if rng.random() < 0.3:
+            opts["dense_threshold"] = int(rng.choice([1, 8, 24]))
+        if rng.random() < 0.3:
+            opts.update(warp_chunks_below=1 << 30, warp_chunk_words=-1)
+        if rng.random() < 0.3:
+            opts["staged_merge_max"] = int(rng.choice([1, 6, 40]))
+            opts["merge_items"] = int(rng.choice([0, 2, 5, 16]))
+        if rng.random() < 0.25:
+            opts["strict_phase2"] = True
+        if rng.random() < 0.2:
+            opts["use_cor10"] = False
+        if rng.random() < 0.2:
+            opts.update(phase2_sets=int(rng.integers(1, 6)), phase2_priority=int(rng.integers(0, 2)))
+        opts["use_graph"] = bool(rng.random() < 0.6)
+        mp = -1 if rng.random() < 0.7 else int(rng.integers(0, 4))
+        okw = {"strict": opts.get("strict_phase2", False), "cor10": opts.get("use_cor10", True),
+               "sets": opts.get("phase2_sets", 0), "priority": opts.get("phase2_priority", 0)}
+        if mp >= 0:
+            okw["max_passes"] = mp
+        K = orc.vr_build(x, k, cut)
+        ref = orc.reduce_pms(K, **okw)
+        cp, rows = orc.reduce_pms_columns(K, **okw)
+        ctx = ph.Context(collect_stats=True, **opts)
+        ctx.build_filtration(torch.from_numpy(x).cuda(), None, k, cut)
+        st = ctx.reduce(max_passes=mp)
+        where = (case, n, k, cut, mp, opts)
+        assert st["passes"] == ref.passes, where
+        assert np.array_equal(ctx.filtration(0)["low"], ref.low), where
+        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8]), where
+        gcp, grows = ctx.columns(0)
+        assert np.array_equal(gcp, cp) and np.array_equal(grows, rows), where
+        ctx.close()
