@@ -761,3 +761,54 @@ def test_random_complexes_and_options(ph, orc):
         gcp, grows = ctx.columns(0)
         assert np.array_equal(gcp, cp) and np.array_equal(grows, rows), where
         ctx.close()
+
+
+def test_random_batches_grids_and_predictions(ph, orc):
+    # Seeded sweep over what the first sweep keeps fixed: batches of random clouds (each cloud
+    # against the oracle run on it alone), the scale-grid build, Corollary 10 predictions and
+    # the essential estimate of early-stopped reductions
+    import torch
+
+    rng = np.random.default_rng(4710)
+    for case in range(60):
+        nb = int(rng.integers(1, 6))
+        sizes = [int(rng.integers(1, 15)) for _ in range(nb)]
+        D = int(rng.integers(1, 4))
+        k = int(rng.integers(1, 4))
+        clouds = [pc.random_cloud(n, D, 2000 + 10 * case + i) for i, n in enumerate(sizes)]
+        opts = {"use_graph": bool(rng.random() < 0.5), "predict_pairs": bool(rng.random() < 0.5)}
+        if rng.random() < 0.3:
+            opts["dense_threshold"] = 1
+        if rng.random() < 0.3:
+            opts.update(warp_chunks_below=1 << 30, warp_chunk_words=-1)
+        if rng.random() < 0.25:
+            opts["strict_phase2"] = True
+        grid = rng.random() < 0.4
+        step, n_scales = int(rng.integers(5000, 60000)), int(rng.integers(1, 8))
+        mp = -1 if rng.random() < 0.6 else int(rng.integers(0, 4))
+        okw = {"strict": opts.get("strict_phase2", False)}
+        if mp >= 0:
+            okw["max_passes"] = mp
+        x = np.concatenate(clouds)
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        ctx = ph.Context(collect_stats=True, **opts)
+        if grid:
+            ctx.build_filtration_scales(torch.from_numpy(x).cuda(), off, k, step, n_scales)
+        else:
+            ctx.build_filtration(torch.from_numpy(x).cuda(), off, k)
+        ctx.reduce(max_passes=mp)
+        for c, xc in enumerate(clouds):
+            K = (orc.vr_build(xc, k, scale_step=step, n_scales=n_scales) if grid
+                 else orc.vr_build(xc, k))
+            ref = orc.reduce_pms(K, **okw)
+            where = (case, c, sizes, D, k, grid, mp, opts)
+            f = ctx.filtration(c)
+            assert np.array_equal(f["dim"], K["dim"]) and np.array_equal(f["low"], ref.low), where
+            cp, rows = orc.reduce_pms_columns(K, **okw)
+            gcp, grows = ctx.columns(c)
+            assert np.array_equal(gcp, cp) and np.array_equal(grows, rows), where
+            # a cloud that converged earlier than the batch is final: later passes leave it be
+            assert np.array_equal(ctx.essential_estimate(c), ref.ess_est), where
+            if opts["predict_pairs"]:
+                assert np.array_equal(ctx.predicted_lows(c), ref.predicted), where
+        ctx.close()
