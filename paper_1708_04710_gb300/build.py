@@ -1,7 +1,9 @@
 """Compiles the CUDA library ``libph_gb300.so`` in place (sm_103a only).
 
 Every translation unit is compiled in parallel with nvcc, then linked into one shared library
-that exports the C ABI of ``include/ph_gb300.h``. No GPU is needed to build.
+that exports the C ABI of ``include/ph_gb300.h``. No GPU is needed to build. ``debug=True``
+builds ``libph_gb300_debug.so`` instead, with the device-side bounds checks (``-DPH_DEBUG``);
+the binding loads it when ``PH_GB300_DEBUG=1``.
 """
 from __future__ import annotations
 
@@ -15,6 +17,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libph_gb300.so"
+BUILD_DEBUG = PKG / "_build_debug"
+LIB_DEBUG = PKG / "libph_gb300_debug.so"
 SOURCES = ["ph_scan.cu", "ph_build.cu", "ph_reduce.cu", "ph_api.cu", "ph_diff.cu",
            "ph_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -32,15 +36,18 @@ def _flags(extra=()):
             "--expt-relaxed-constexpr", *extra]
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> Path:
-    BUILD.mkdir(exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False) -> Path:
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if debug:
+        extra_flags = (*extra_flags, "-DPH_DEBUG")
+    build_dir.mkdir(exist_ok=True)
     headers = list(CSRC.glob("*.cuh")) + [PKG.parent / "include" / "ph_gb300.h"]
     newest_header = max(p.stat().st_mtime for p in headers)
     objs = []
     jobs = []
     for src in SOURCES:
         s = CSRC / src
-        o = BUILD / (Path(src).stem + ".o")
+        o = build_dir / (Path(src).stem + ".o")
         objs.append(o)
         if force or not o.exists() or o.stat().st_mtime < max(s.stat().st_mtime, newest_header):
             jobs.append([nvcc(), *_flags(extra_flags), "-c", str(s), "-o", str(o)])
@@ -54,11 +61,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> Path:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if jobs or force or not LIB.exists():
-        tmp = LIB.with_suffix(f".{os.getpid()}.tmp.so")
+    if jobs or force or not lib.exists():
+        tmp = lib.with_suffix(f".{os.getpid()}.tmp.so")
         run([nvcc(), *ARCH, "-shared", *map(str, objs), "-o", str(tmp), "-lcuda"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

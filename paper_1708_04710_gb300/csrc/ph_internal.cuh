@@ -182,6 +182,16 @@ struct ph_ctx {
 
 namespace ph {
 
+// Device-side bounds checks of the debug build (-DPH_DEBUG; the library's stand-in for a memory
+// checker): a failed check records its code in *word (the first failure wins) and yields false,
+// so that the caller skips the access; the host reports the code as an error. Without
+// PH_DEBUG every check is `true` and costs nothing.
+#ifdef PH_DEBUG
+#define PH_DCHECK(word, cond, code) ((cond) ? true : (atomicCAS((word), 0, (code)), false))
+#else
+#define PH_DCHECK(word, cond, code) true
+#endif
+
 // an NVTX range for the lifetime of the object: a profiler timeline shows every entry point and
 // pass (no cost without a profiler attached)
 struct NvtxRange {

@@ -74,6 +74,7 @@ struct DevState {
   alignas(128) unsigned int queue;             // next chunk for k_add
   alignas(128) int32_t n_deferred;             // entries of dlist
   alignas(128) int32_t fault;                  // a bounded wait ran out
+  int32_t debug_fault;  // the first failed bounds check of the debug build (PH_DCHECK), 0 if none
   // bit-packed columns: the passes after the first one that saw a target that may reach its
   // threshold run the additions kernel that handles them (and converts columns); the pass loop
   // stops once there (ST_SWITCH) so that the host continues it with that kernel
@@ -141,6 +142,8 @@ struct PV {
   int32_t* arena_next;
   int32_t* piv_base;
   int dense_on;
+  int64_t arena_next_cap;  // words of arena_next and of the pivot store's chunk (bounds checks)
+  int64_t piv_cap;
 };
 
 __device__ __forceinline__ PV pass_view(const DevState* ds) {
@@ -155,6 +158,8 @@ __device__ __forceinline__ PV pass_view(const DevState* ds) {
   v.arena_next = ds->arena[ds->pass & 1];
   v.piv_base = ds->piv_base;
   v.dense_on = ds->dense_on;
+  v.arena_next_cap = ds->arena_cap[ds->pass & 1];
+  v.piv_cap = ds->piv_cap;
   return v;
 }
 
@@ -260,7 +265,7 @@ __global__ void k_tab(RArgs a) {
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t j = v.act[i];
     int32_t l = a.low[j];
-    if (l >= 0) {
+    if (l >= 0 && PH_DCHECK(&a.ds->debug_fault, l < a.rows_end, 1)) {
       if (a.tab[l] > j) atomicMin(&a.tab[l], j);
       if (!a.meta[l].low_seen) a.meta[l].low_seen = 1;  // for the essential estimate
     }
@@ -515,6 +520,7 @@ __global__ void k_mark(RArgs a) {
     if (e < v.n_act) {
       int32_t j = v.act[e];
       int32_t l = a.low[j];
+      if (!PH_DCHECK(&a.ds->debug_fault, l < a.rows_end, 2)) continue;
       uint8_t f = a.meta[j].flags;
       const int32_t s = l >= 0 ? a.tab[l] : -1;
       a.src_e[e] = s != j ? s : -1;  // Phase II reads it in list order
@@ -641,6 +647,14 @@ __device__ __noinline__ int32_t dense_job_warp(const RArgs& a, int32_t j, const 
   int64_t base;
   int32_t W;
   row_segment(a, j, base, W);
+#ifdef PH_DEBUG
+  // the bitmap fits the slot reserved for the job (na + nb stored words)
+  if (!PH_DCHECK(&a.ds->debug_fault, W + kDenseHead <= na + nb, 6)) {
+    low = -1;
+    words = 0;
+    return 0;
+  }
+#endif
   uint32_t* bits = reinterpret_cast<uint32_t*>(T + kDenseHead);
   const uint32_t* Ab = reinterpret_cast<const uint32_t*>(A + kDenseHead);
   const uint32_t* Bb = reinterpret_cast<const uint32_t*>(B + kDenseHead);
@@ -1166,6 +1180,13 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     rank = (int)(excl >> kRankShift);
   }
 
+#ifdef PH_DEBUG
+  // the job's slot lies in the arena this pass writes (else the job is dropped and reported)
+  if (jb.surv && !PH_DCHECK(&a.ds->debug_fault, off >= 0 && off + jb.words <= v.arena_next_cap, 3)) {
+    jb.surv = false;
+    jb.newpiv = false;
+  }
+#endif
   const int32_t* A = jb.A;
   const int32_t* B = jb.B;
   const int na = jb.na, nb = jb.nb;
@@ -1182,6 +1203,11 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     unsigned long long w0 = 0;
     if (lane == 0) w0 = atomicAdd(&a.ds->piv_used, (unsigned long long)ptot);
     w0 = __shfl_sync(0xffffffffu, w0, 0) + (unsigned long long)(incl - mine);
+#ifdef PH_DEBUG
+    // the warp's run lies in the pivot store's chunk (else the warp's copies are dropped)
+    const bool in_store = PH_DCHECK(&a.ds->debug_fault, (int64_t)(w0 + mine) <= v.piv_cap, 4);
+    if (!__all_sync(0xffffffffu, in_store)) pmask = 0;
+#endif
     if (jb.newpiv) o_ptr = v.piv_base + w0;
   }
   while (pmask) {
@@ -1350,14 +1376,15 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   // ---- the survivors' places in the next active list
   if constexpr (kWarp) {
     const int64_t pre = look_back(a, pass, chunk, n_surv);
-    if (jb.surv) v.act2[pre + rank] = jb.j;
+    if (jb.surv && PH_DCHECK(&a.ds->debug_fault, pre + rank < v.n_act, 5)) v.act2[pre + rank] = jb.j;
   } else {
     if (threadIdx.x < 32) {
       const int64_t pre = look_back(a, pass, chunk, n_surv);
       if (threadIdx.x == 0) s_prefix[0] = pre;
     }
     __syncthreads();
-    if (jb.surv) v.act2[s_prefix[0] + rank] = jb.j;
+    if (jb.surv && PH_DCHECK(&a.ds->debug_fault, s_prefix[0] + rank < v.n_act, 5))
+      v.act2[s_prefix[0] + rank] = jb.j;
   }
   // ---- publish: in place for targets and zeroed columns, through k_commit for the others
   if (jb.j >= 0) {
@@ -1531,7 +1558,7 @@ __global__ void k_clock_start(DevState* ds) { ds->t_start = global_ns(); }
 // bound, and the graph's loop condition
 __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int in_graph) {
   DevState* ds = a.ds;
-  if (ds->status == ST_RUN && ds->fault) ds->status = ST_FAULT;
+  if (ds->status == ST_RUN && (ds->fault || ds->debug_fault)) ds->status = ST_FAULT;
   const bool to_dense = ds->dense_want && !ds->dense_on;
   if (to_dense) ds->dense_on = 1;
   if (ds->status == ST_RUN) {
@@ -1980,6 +2007,8 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     }
     break;
   }
+  PH_REQUIRE(h.status != ST_FAULT || h.debug_fault == 0, PH_ERR_CUDA,
+             "device bounds check " + std::to_string(h.debug_fault) + " failed (debug build)");
   PH_REQUIRE(h.status != ST_FAULT, PH_ERR_CUDA,
              "a bounded wait in the addition kernel ran out (look-back did not complete)");
   PH_REQUIRE(h.status != ST_TIMEOUT, PH_ERR_TIMEOUT,

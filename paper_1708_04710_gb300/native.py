@@ -6,6 +6,8 @@ There is no fallback: if the library is missing or no GPU is present, loading fa
 """
 from __future__ import annotations
 
+import os
+
 import ctypes
 from ctypes import (CFUNCTYPE, POINTER, Structure, byref, c_char_p, c_double, c_int, c_int32,
                     c_int64, c_size_t, c_void_p)
@@ -13,7 +15,9 @@ from pathlib import Path
 
 import numpy as np
 
-LIB_PATH = Path(__file__).resolve().parent / "libph_gb300.so"
+# PH_GB300_DEBUG=1: the build with device-side bounds checks (build.build(debug=True))
+LIB_PATH = Path(__file__).resolve().parent / (
+    "libph_gb300_debug.so" if os.environ.get("PH_GB300_DEBUG") == "1" else "libph_gb300.so")
 
 PH_OK, PH_NOT_CONVERGED = 0, 1
 PS_FIELDS = ("active", "new_pivots", "zero_final", "cor10", "cleared", "targets", "adds",

@@ -812,3 +812,47 @@ def test_random_batches_grids_and_predictions(ph, orc):
             if opts["predict_pairs"]:
                 assert np.array_equal(ctx.predicted_lows(c), ref.predicted), where
         ctx.close()
+
+
+_DEBUG_RUN = r"""
+import numpy as np, torch
+import oracle, pointclouds as pc, paper_1708_04710_gb300 as ph
+assert ph.native.LIB_PATH.name == "libph_gb300_debug.so"
+oracle.build_lib()
+cases = [(pc.circle40(), 2, {}), (pc.random_cloud(11, 3, 31), 4, {"dense_threshold": 1}),
+         (pc.random_cloud(60, 3, 12), 2, {"arena_words": 1, "warp_chunks_below": 1 << 30,
+                                          "warp_chunk_words": -1}),
+         (pc.random_cloud(30, 3, 500), 2, {"phase2_sets": 3, "phase2_priority": 1}),
+         (pc.torus400()[:120], 2, {"use_graph": False})]
+for x, k, opts in cases:
+    K = oracle.vr_build(x, k)
+    okw = {"sets": opts.get("phase2_sets", 0), "priority": opts.get("phase2_priority", 0)}
+    ref = oracle.reduce_pms(K, **okw)
+    cp, rows = oracle.reduce_pms_columns(K, **okw)
+    ctx = ph.Context(collect_stats=True, **opts)
+    ctx.build_filtration(torch.from_numpy(x).cuda(), None, k)
+    st = ctx.reduce()
+    assert st["passes"] == ref.passes
+    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+    gcp, grows = ctx.columns(0)
+    assert np.array_equal(gcp, cp) and np.array_equal(grows, rows)
+print("debug build ok")
+"""
+
+
+def test_debug_build_bounds_checks_pass(ph):
+    # The build with device-side bounds checks (every arena, pivot-store, active-list, row and
+    # bitmap access of the pass kernels checked; a failure is reported, not trapped) runs the
+    # parity cases clean and exact. It runs in its own process, which loads the debug library.
+    import os
+    import subprocess
+    import sys
+
+    from paper_1708_04710_gb300 import build
+
+    build.build(debug=True)
+    env = dict(os.environ, PH_GB300_DEBUG="1")
+    root = Path(__file__).resolve().parents[1]
+    r = subprocess.run([sys.executable, "-c", _DEBUG_RUN], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "debug build ok" in r.stdout, r.stdout + r.stderr
