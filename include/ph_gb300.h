@@ -215,12 +215,16 @@ int ph_build_filtration_f32(ph_ctx* ctx, const float* coords, const int64_t* clo
                             int64_t max_diam2, int64_t* m_out);
 
 /* Loads an explicit filtration of one complex instead of building a VR one.
- *   m             number of simplices, in a compatible order (faces before cofaces).
- *   dims          host int32 [m], dimension of each simplex (0..15).
- *   colptr        host int64 [m + 1], CSC column pointers of the boundary matrix.
- *   rows          host int32 [colptr[m]], row indices (global positions, ascending per
- *                 column, each row of dimension dims[j] - 1).
- * Squared diameters of loaded complexes are reported as 0. Synchronises the stream. */
+ *   m             number of cells, in a compatible order (faces before cofaces).
+ *   dims          host int32 [m], dimension of each cell (0..8).
+ *   colptr        host int64 [m + 1], CSC column pointers of the boundary matrix over F2.
+ *   rows          host int32 [colptr[m]], row indices (earlier positions of dimension
+ *                 dims[j] - 1, strictly ascending per column; none in dimension 0).
+ * A column may hold any number of rows: a simplicial boundary (d + 1 faces), a cubical or
+ * cellular one, or a partially reduced matrix R = D V as ph_get_columns returns it; reducing R
+ * gives the pairs of D (lowstar depends only on the spans of the column prefixes, Sec. 2.3),
+ * so R is a checkpoint of a reduction. Squared diameters of loaded complexes are reported as
+ * 0. Synchronises the stream. */
 int ph_load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* colptr,
                      const int32_t* rows);
 

@@ -52,6 +52,7 @@ void ph_ctx::free_all() {
   p_birth = p_death = p_bd2 = p_dd2 = e_idx = e_d2 = nullptr;
   p_dim = e_dim = nullptr;
   seg = low = beta = key = rows0 = nullptr;
+  col_off = nullptr;
   gidx = nullptr;
   verts = nullptr;
   d2tab = nullptr;

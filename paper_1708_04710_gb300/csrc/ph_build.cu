@@ -349,14 +349,18 @@ __device__ __forceinline__ int id_dim(const ColLayout& L, int64_t x) {
   return d;
 }
 
-__global__ void k_left(ColLayout L, const int32_t* __restrict__ rows0, int32_t* left) {
+// col_off: the columns of a loaded matrix (any length); null: d + 1 rows at a fixed stride
+__global__ void k_left(ColLayout L, const int32_t* __restrict__ rows0,
+                       const int64_t* __restrict__ col_off, int32_t* left) {
   int64_t n = L.dimoff[L.maxd + 1] - L.dimoff[1];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     int64_t j = L.dimoff[1] + t;
     int d = id_dim(L, j);
-    const int32_t* r = rows0 + L.rowbase[d] + (int64_t)(d + 1) * (j - L.dimoff[d]);
-    for (int q = 0; q <= d; q++) atomicMin(&left[r[q]], (int32_t)j);
+    const int32_t* r = col_off ? rows0 + col_off[j]
+                               : rows0 + L.rowbase[d] + (int64_t)(d + 1) * (j - L.dimoff[d]);
+    const int64_t len = col_off ? col_off[j + 1] - col_off[j] : d + 1;
+    for (int64_t q = 0; q < len; q++) atomicMin(&left[r[q]], (int32_t)j);
   }
 }
 
@@ -436,7 +440,8 @@ void compute_beta(ph_ctx* ctx) {
   ctx->beta = alloc_n<int32_t>(ctx, ctx->m);
   PH_CUDA(cudaMemsetAsync(left, 0x7f, ctx->m * sizeof(int32_t), st));  // > every id
   PH_CUDA(cudaMemsetAsync(ctx->beta, 0xff, ctx->m * sizeof(int32_t), st));
-  k_left<<<grid_for(ctx, ctx->m, kThreads), kThreads, 0, st>>>(L, ctx->rows0, left);
+  k_left<<<grid_for(ctx, ctx->m, kThreads), kThreads, 0, st>>>(L, ctx->rows0, ctx->col_off,
+                                                               left);
   PH_CHECK_LAUNCH();
   k_beta<<<grid_for(ctx, ctx->m, kThreads), kThreads, 0, st>>>(ctx->m, left, ctx->beta);
   PH_CHECK_LAUNCH();
@@ -444,7 +449,9 @@ void compute_beta(ph_ctx* ctx) {
 }
 
 // An explicit complex given in filtration order: re-index it dim-major (stable inside each
-// dimension, which keeps every order the reduction compares) and store its boundary.
+// dimension, which keeps every order the reduction compares) and store its boundary. A column
+// may hold any number of rows of the dimension below (a simplicial, cubical or cellular
+// boundary over F2, or a partially reduced matrix R = D V), so columns are kept with offsets.
 void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* colptr,
                    const int32_t* rows) {
   cudaStream_t st = ctx->stream;
@@ -459,13 +466,19 @@ void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* c
   }
   std::vector<int64_t> dimoff(maxd + 2, 0);
   for (int d = 0; d <= maxd; d++) dimoff[d + 1] = dimoff[d] + cnt[d];
-  std::vector<int64_t> rowbase(maxd + 2, 0);
-  for (int d = 0; d <= maxd; d++)
-    rowbase[d + 1] = rowbase[d] + (d > 0 ? (int64_t)(d + 1) * cnt[d] : 0);
   std::vector<int32_t> id_of(m);
   std::vector<int64_t> fill(maxd + 1, 0);
   for (int64_t j = 0; j < m; j++) id_of[j] = (int32_t)(dimoff[dims[j]] + fill[dims[j]]++);
-  const int64_t nnz = rowbase[maxd + 1];
+  PH_REQUIRE(colptr[0] == 0, PH_ERR_INVALID, "colptr[0] must be 0");
+  std::vector<int64_t> h_off(m + 1, 0);  // column offsets in id order
+  for (int64_t j = 0; j < m; j++) {
+    const int64_t n = colptr[j + 1] - colptr[j];
+    PH_REQUIRE(n >= 0 && (dims[j] > 0 || n == 0), PH_ERR_INVALID,
+               "column lengths must be >= 0, and 0 in dimension 0");
+    h_off[id_of[j] + 1] = n;
+  }
+  for (int64_t x = 0; x < m; x++) h_off[x + 1] += h_off[x];
+  const int64_t nnz = h_off[m];
   std::vector<int32_t> h_rows(std::max<int64_t>(nnz, 1)), h_seg(m), h_key(m, -1), h_low(m, -1);
   std::vector<int64_t> h_gidx(m);
   std::vector<uint64_t> h_verts(m, ~0ull);
@@ -473,9 +486,7 @@ void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* c
     int d = dims[j];
     int64_t x = id_of[j];
     int64_t n = colptr[j + 1] - colptr[j];
-    PH_REQUIRE(n == (d > 0 ? d + 1 : 0), PH_ERR_INVALID,
-               "a column of dimension d must have d + 1 rows (d > 0) or none (d = 0)");
-    int64_t base = rowbase[d] + (int64_t)(d + 1) * (x - dimoff[d]);
+    int64_t base = h_off[x];
     int32_t prev = -1;
     for (int64_t p = 0; p < n; p++) {
       int32_t r = rows[colptr[j] + p];
@@ -502,6 +513,7 @@ void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* c
   ctx->gidx = alloc_n<int64_t>(ctx, m);
   ctx->verts = alloc_n<uint64_t>(ctx, m);
   ctx->rows0 = alloc_n<int32_t>(ctx, std::max<int64_t>(nnz, 1));
+  ctx->col_off = alloc_n<int64_t>(ctx, m + 1);
   ctx->d2tab = alloc_n<int64_t>(ctx, 1);
   ctx->n_d2 = 0;
   PH_CUDA(cudaMemcpyAsync(ctx->seg, h_seg.data(), m * 4, cudaMemcpyHostToDevice, st));
@@ -511,6 +523,7 @@ void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* c
   PH_CUDA(cudaMemcpyAsync(ctx->verts, h_verts.data(), m * 8, cudaMemcpyHostToDevice, st));
   PH_CUDA(cudaMemcpyAsync(ctx->rows0, h_rows.data(), std::max<int64_t>(nnz, 1) * 4,
                           cudaMemcpyHostToDevice, st));
+  PH_CUDA(cudaMemcpyAsync(ctx->col_off, h_off.data(), (m + 1) * 8, cudaMemcpyHostToDevice, st));
   finish_layout(ctx);
   compute_beta(ctx);
   PH_CUDA(cudaStreamSynchronize(st));

@@ -162,6 +162,9 @@ struct ph_ctx {
   int64_t* d2tab = nullptr;   // dense rank -> squared diameter
   int64_t n_d2 = 0;
   int32_t* rows0 = nullptr;   // initial column storage (boundary matrix, CSC by id)
+  // loaded matrices: per id, the offset of its column in rows0 ([m + 1]); VR builds store
+  // d + 1 rows per column at a fixed stride and leave this null
+  int64_t* col_off = nullptr;
   int64_t nnz = 0;
 
   ph::ReduceState rs;

@@ -1599,22 +1599,26 @@ struct InitLayout {
 
 // the boundary matrix of a simplicial complex: a column of dimension d > 0 has d + 1 rows,
 // stored in id order from rowbase[d]
-__global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0, ColMeta* meta,
-                              int32_t* low, int32_t* act, int32_t* owner) {
+// col_off: the columns of a loaded matrix (any length); null: d + 1 rows at a fixed stride
+__global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0,
+                              const int64_t* __restrict__ col_off, ColMeta* meta, int32_t* low,
+                              int32_t* act, int32_t* owner) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < m;
        x += (int64_t)gridDim.x * blockDim.x) {
     int d = 0;
     while (d < L.maxd && x >= L.dimoff[d + 1]) d++;
-    int32_t* c = rows0 + L.rowbase[d] + (int64_t)(d > 0 ? d + 1 : 0) * (x - L.dimoff[d]);
+    int32_t* c = col_off ? rows0 + col_off[x]
+                         : rows0 + L.rowbase[d] + (int64_t)(d > 0 ? d + 1 : 0) * (x - L.dimoff[d]);
+    const int32_t n = col_off ? (int32_t)(col_off[x + 1] - col_off[x]) : (d > 0 ? d + 1 : 0);
     ColMeta mx;
     mx.ptr = c;
-    mx.len = d > 0 ? d + 1 : 0;
+    mx.len = n;
     mx.flags = 0;
     mx.cleared = 0;
     mx.low_seen = 0;
     mx.spare = 0;
     meta[x] = mx;
-    low[x] = d > 0 ? c[d] : -1;  // largest row of the unreduced column
+    low[x] = n > 0 ? c[n - 1] : -1;  // largest row of the unreduced column
     act[x] = (int32_t)x;
     owner[x] = -1;
   }
@@ -1807,7 +1811,8 @@ void reduce_init(ph_ctx* ctx) {
     rb += (d > 0 ? d + 1 : 0) * (ctx->dimoff[d + 1] - ctx->dimoff[d]);
   }
   k_reduce_init<<<grid_for(ctx, m, kThreads), kThreads, 0, st>>>(
-      m, L, ctx->rows0, static_cast<ColMeta*>(rs.meta), ctx->low, rs.act, rs.owner);
+      m, L, ctx->rows0, ctx->col_off, static_cast<ColMeta*>(rs.meta), ctx->low, rs.act,
+      rs.owner);
   PH_CHECK_LAUNCH();
   // first arenas: pass 0 needs at most the boundary matrix twice over
   // passes 0 and 1 need about the same; later passes less (they grow on demand otherwise)

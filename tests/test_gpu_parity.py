@@ -856,3 +856,50 @@ def test_debug_build_bounds_checks_pass(ph):
     r = subprocess.run([sys.executable, "-c", _DEBUG_RUN], cwd=root, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "debug build ok" in r.stdout, r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("mp", [0, 2, 5])
+def test_checkpoint_and_resume_through_the_reduced_matrix(ph, orc, mp):
+    # a partial reduction saved as its reduced matrix R (ph_get_columns), loaded into a new
+    # context (ph_load_boundary) and reduced there: the pairs of the original complex; the
+    # resumed run itself is the oracle's run on R, pass by pass
+    from oracle import Complex
+
+    for x, k in ((pc.circle40(), 2), (pc.random_cloud(12, 3, 801), 3)):
+        K = orc.vr_build(x, k)
+        ctx = _gpu(ph, x, k)
+        ctx.reduce(max_passes=mp)
+        cp, rows = ctx.columns(0)
+        dims = ctx.filtration(0)["dim"]
+        ctx2 = ph.Context(collect_stats=True)
+        ctx2.load_boundary(dims, cp, rows)
+        st = ctx2.reduce()
+        R = Complex(dim=K["dim"], diam2=K["diam2"], verts=K["verts"], colptr=cp, rows=rows)
+        ref_r = orc.reduce_pms(R)
+        assert st["passes"] == ref_r.passes
+        assert np.array_equal(ctx2.pass_stats()[:, :8], ref_r.stats[:, :8])
+        low = ctx2.filtration(0)["low"]
+        assert np.array_equal(low, orc.reduce_pms(K).low)
+
+
+def test_cubical_complex(ph, orc):
+    # columns of four rows (squares): the same lows, counters and reduced matrix as the oracle
+    from oracle import Complex
+    from test_oracle_pins import _cubical_grid
+
+    for w, h in ((3, 3), (7, 5)):
+        filled = [(x, y) for x in range(w) for y in range(h) if (x + 2 * y) % 5]
+        dims, cp0, rows0 = _cubical_grid(w, h, filled)
+        K = Complex(dim=dims, diam2=np.zeros(len(dims), np.int64),
+                    verts=np.full((len(dims), 4), -1, np.int32), colptr=cp0, rows=rows0)
+        ref = orc.reduce_pms(K)
+        for opts in ({}, {"dense_threshold": 1, "use_graph": False}):
+            ctx = ph.Context(collect_stats=True, **opts)
+            ctx.load_boundary(dims, cp0, rows0)
+            st = ctx.reduce()
+            assert st["passes"] == ref.passes
+            assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+            assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+            cp, rows = orc.reduce_pms_columns(K)
+            gcp, grows = ctx.columns(0)
+            assert np.array_equal(gcp, cp) and np.array_equal(grows, rows)

@@ -435,3 +435,63 @@ def test_pms_reduced_matrix_spans_the_boundary_prefixes(orc, kw):
         for j in range(m):
             vd = sum(1 << int(i) for i in np.nonzero(D[:, j])[0])
             assert not _insert(dict(bdr), vd)
+
+
+@pytest.mark.parametrize("kw", [{"max_passes": 0}, {"max_passes": 2}, {"max_passes": 5},
+                                {"max_passes": 2, "strict": True}])
+def test_reduced_matrix_is_a_checkpoint(orc, kw):
+    # lowstar depends only on the spans of the column prefixes, which left-to-right additions
+    # keep (Sec. 2.3): reducing a partially reduced matrix R, as a matrix of its own, gives the
+    # pairs of the original boundary matrix
+    from oracle import Complex
+
+    for seed, n, k in ((0, 14, 2), (1, 9, 3)):
+        K = orc.vr_build(pc.random_cloud(n, 3, 800 + seed), k)
+        cp, rows = orc.reduce_pms_columns(K, **kw)
+        R = Complex(dim=K["dim"], diam2=K["diam2"], verts=K["verts"], colptr=cp, rows=rows)
+        want = orc.reduce_std(K)[0]
+        assert np.array_equal(orc.reduce_std(R)[0], want)
+        assert np.array_equal(orc.reduce_pms(R).low, want)
+
+
+def _cubical_grid(w, h, filled):
+    """The cubical complex of a w x h grid of unit squares (vertices, edges, and the squares
+    listed in `filled`), in a compatible order: boundary matrix columns of any length."""
+    cells, index = [], {}
+
+    def add(key, dim, faces):
+        index[key] = len(cells)
+        cells.append((dim, sorted(index[f] for f in faces)))
+
+    for y in range(h + 1):
+        for x in range(w + 1):
+            add(("v", x, y), 0, [])
+    for y in range(h + 1):
+        for x in range(w):
+            add(("h", x, y), 1, [("v", x, y), ("v", x + 1, y)])
+    for y in range(h):
+        for x in range(w + 1):
+            add(("u", x, y), 1, [("v", x, y), ("v", x, y + 1)])
+    for (x, y) in filled:
+        add(("s", x, y), 2, [("h", x, y), ("h", x, y + 1), ("u", x, y), ("u", x + 1, y)])
+    dims = np.array([c[0] for c in cells], np.int32)
+    colptr = np.concatenate([[0], np.cumsum([len(c[1]) for c in cells])]).astype(np.int64)
+    rows = np.array([r for c in cells for r in c[1]], np.int32)
+    return dims, colptr, rows
+
+
+def test_cubical_complex_betti_numbers(orc):
+    # a non-simplicial complex (squares with four edges): a 3 x 3 grid with the middle square
+    # left out has b0 = 1, b1 = 1 (the hole), b2 = 0; the full grid has b1 = 0
+    from oracle import Complex
+
+    for filled, betti in (([(x, y) for x in range(3) for y in range(3) if (x, y) != (1, 1)],
+                           [1, 1, 0]),
+                          ([(x, y) for x in range(3) for y in range(3)], [1, 0, 0])):
+        dims, cp, rows = _cubical_grid(3, 3, filled)
+        K = Complex(dim=dims, diam2=np.zeros(len(dims), np.int64),
+                    verts=np.full((len(dims), 4), -1, np.int32), colptr=cp, rows=rows)
+        low = orc.reduce_pms(K).low
+        _, ess = orc.pairs_and_essential(low, dims)
+        assert np.bincount(dims[ess], minlength=3).tolist() == betti
+        assert np.array_equal(low, orc.reduce_std(K)[0])
