@@ -903,3 +903,70 @@ def test_cubical_complex(ph, orc):
             cp, rows = orc.reduce_pms_columns(K)
             gcp, grows = ctx.columns(0)
             assert np.array_equal(gcp, cp) and np.array_equal(grows, rows)
+
+
+def _addition_cases(seed=5):
+    """A matrix of 4096 rows (dimension 0) and columns built so that the first pass adds, per
+    group, a source column into targets with the same low: equal columns, length-1 columns,
+    disjoint and nested ones, columns longer than the staging bound, very uneven lengths, and
+    one source shared by many targets. Rows of a group lie below its own low."""
+    rng = np.random.default_rng(seed)
+    n_rows = 4096
+    cols = []
+    lows = iter(range(n_rows - 1, 0, -7))
+
+    def rand_rows(low, k):
+        return np.sort(rng.choice(low, size=min(k, low), replace=False)).tolist() + [low]
+
+    groups = []
+    low = next(lows); s = rand_rows(low, 6); groups.append((s, [list(s)]))           # equal
+    low = next(lows); groups.append(([low], [[low]]))                                  # length 1
+    low = next(lows)
+    a = rand_rows(low, 5); b = sorted(set(rand_rows(low, 5)) - set(a[:-1]))
+    groups.append((a, [b]))                                                            # disjoint
+    low = next(lows); s = rand_rows(low, 40)
+    groups.append((s, [sorted(set(s) | set(rand_rows(low, 30)))]))                    # nested
+    low = next(lows); groups.append((rand_rows(low, 60), [rand_rows(low, 70)]))       # staged
+    low = next(lows); groups.append((rand_rows(low, 900), [rand_rows(low, 1100)]))    # > staging
+    low = next(lows); groups.append((rand_rows(low, 2), [rand_rows(low, 1500)]))      # uneven
+    low = next(lows); groups.append((rand_rows(low, 1500), [rand_rows(low, 2)]))
+    low = next(lows); groups.append((rand_rows(low, 20), [rand_rows(low, int(rng.integers(1, 90)))
+                                                         for _ in range(40)]))        # 40 targets
+    for src, tgts in groups:
+        cols.append(src)
+        cols.extend(tgts)
+    # every source first (left-most for its low), then the targets in a random order
+    order = rng.permutation(len(cols))
+    src_idx = set(np.cumsum([0] + [1 + len(t) for _, t in groups[:-1]]).tolist())
+    firsts = [c for i, c in enumerate(cols) if i in src_idx]
+    rest = [cols[i] for i in order if i not in src_idx]
+    cols = firsts + rest
+    dims = np.array([0] * n_rows + [1] * len(cols), np.int32)
+    colptr = np.concatenate([[0] * (n_rows + 1), np.cumsum([len(c) for c in cols])]).astype(np.int64)
+    rows = np.array([r for c in cols for r in c], np.int32)
+    return dims, colptr, rows
+
+
+@pytest.mark.parametrize("opts", [{}, {"staged_merge_max": 1}, {"staged_merge_max": 16},
+                                  {"dense_threshold": 1},
+                                  {"warp_chunks_below": 1 << 30, "warp_chunk_words": -1},
+                                  {"use_graph": False, "merge_items": 3}],
+                         ids=["default", "global", "staged16", "bitmaps", "warp", "host_km3"])
+def test_column_additions_edge_cases(ph, orc, opts):
+    # the symmetric difference itself on crafted columns, through every merge path: the
+    # reduced matrix, lows and counters against the oracle's sorted-array additions
+    from oracle import Complex
+
+    dims, cp0, rows0 = _addition_cases()
+    K = Complex(dim=dims, diam2=np.zeros(len(dims), np.int64),
+                verts=np.full((len(dims), 4), -1, np.int32), colptr=cp0, rows=rows0)
+    ref = orc.reduce_pms(K)
+    cp, rows = orc.reduce_pms_columns(K)
+    ctx = ph.Context(collect_stats=True, **opts)
+    ctx.load_boundary(dims, cp0, rows0)
+    st = ctx.reduce()
+    assert st["passes"] == ref.passes
+    assert np.array_equal(ctx.filtration(0)["low"], ref.low)
+    assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+    gcp, grows = ctx.columns(0)
+    assert np.array_equal(gcp, cp) and np.array_equal(grows, rows)
