@@ -237,7 +237,11 @@ int ph_load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t*
  *                 every pass proves or zeroes at least one column). When it is hit the call
  *                 returns PH_NOT_CONVERGED and the state stays a valid partial reduction.
  *   out           host, optional: summary counters.
- * Synchronises the stream. May be called once per filtration. */
+ * A later call continues a reduction that stopped at its pass cap (PH_NOT_CONVERGED), at the
+ * time bound (PH_ERR_TIMEOUT) or on a failed allocation (PH_ERR_ALLOC, the state left as
+ * before the pass that needed the memory); after a complete reduction it returns the result
+ * again. The pass loop runs in a CUDA graph (use_graph) or from the host. Synchronises the
+ * stream. */
 int ph_reduce(ph_ctx* ctx, int32_t max_passes, ph_stats* out);
 
 /* Discards the reduction state (and extracted outputs) of the context; the next ph_reduce
