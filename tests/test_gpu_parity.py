@@ -970,3 +970,37 @@ def test_column_additions_edge_cases(ph, orc, opts):
     assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
     gcp, grows = ctx.columns(0)
     assert np.array_equal(gcp, cp) and np.array_equal(grows, rows)
+
+
+@pytest.mark.parametrize("world", [2, 3, 5])
+def test_sharded_batch_equals_unsharded(ph, world):
+    # the multi-GPU form of the batch shards clouds across ranks with no collective; here the
+    # shards run one after another on one GPU, and every cloud's pairs, essentials and
+    # reduced matrix equal those of the whole batch reduced together
+    import torch
+
+    from paper_1708_04710_gb300.shard import local_batch, shard_clouds
+
+    sizes = [int(s) for s in np.random.default_rng(31).integers(3, 40, 23)]
+    clouds = [pc.random_cloud(n, 3, 3000 + i) for i, n in enumerate(sizes)]
+    x = np.concatenate(clouds)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    whole = _gpu(ph, x, 2, offsets=off)
+    whole.reduce()
+    seen = []
+    for part in shard_clouds(off, world):
+        if not part:
+            continue
+        xs, offs = local_batch(x, off, part)
+        ctx = ph.Context()
+        ctx.build_filtration(torch.from_numpy(xs).cuda(), offs, 2)
+        assert ctx.reduce()["converged"]
+        for i, c in enumerate(part):
+            a, b = _gpu_pairs(ctx, i), _gpu_pairs(whole, c)
+            for k in ("birth", "death", "dim"):
+                assert np.array_equal(a[0][k], b[0][k]), (world, c, k)
+            assert np.array_equal(a[1]["idx"], b[1]["idx"]), (world, c)
+            ca, cb = ctx.columns(i), whole.columns(c)
+            assert np.array_equal(ca[0], cb[0]) and np.array_equal(ca[1], cb[1]), (world, c)
+            seen.append(c)
+    assert sorted(seen) == list(range(len(sizes)))
