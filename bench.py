@@ -265,7 +265,9 @@ def main():
     x_pin = torch.from_numpy(x).pin_memory()
     dev_buf = torch.empty_like(coords)
     e2e_times, d2h = [], 0
-    for _ in range(args.steps):
+    # two untimed steps first: the page-locked output buffers (two generations, since a step's
+    # outputs are still alive when the next is requested) come from torch's host cache after
+    for it in range(2 + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         dev_buf.copy_(x_pin, non_blocking=True)
@@ -274,7 +276,8 @@ def main():
         pr = ctx.pairs(-1, on_device=False)
         es = ctx.essential(-1, on_device=False)
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        if it >= 2:
+            e2e_times.append(time.perf_counter() - t0)
         d2h = sum(v.numel() * v.element_size() for v in list(pr.values()) + list(es.values()))
     e2e_s = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
     if dist:
