@@ -42,7 +42,8 @@ def cache_path() -> Path:
 
 
 def workload_key(gpu: str, m: int, max_dim: int, n_clouds: int) -> str:
-    return f"{gpu}|m2^{round(math.log2(max(m, 1)))}|dim{max_dim}|{'batched' if n_clouds > 1 else 'single'}"
+    kind = "batched" if n_clouds > 1 else "single"
+    return f"{gpu}|m2^{round(math.log2(max(m, 1)))}|dim{max_dim}|{kind}"
 
 
 def _time_reduce(torch, coords, offsets, max_dim, max_diam2, opts, reps=2) -> float:

@@ -142,3 +142,35 @@ def icosahedron_facets():
     adj = np.isclose(d, 2.0)
     return [t for t in itertools.combinations(range(12), 3)
             if adj[t[0], t[1]] and adj[t[0], t[2]] and adj[t[1], t[2]]]
+
+
+# Phase II with p processors: seven vertices and nine edges in filtration order (the passes
+# of this complex are derived by hand in test_oracle_pins.py)
+BUDGET_EXAMPLE = [(v,) for v in range(7)] + [(0, 1), (0, 2), (0, 3), (0, 4), (1, 4), (2, 4),
+                                            (3, 4), (0, 6), (5, 6)]
+
+
+def cubical_grid(w, h, filled):
+    """The cubical complex of a w x h grid of unit squares (vertices, edges, and the squares
+    listed in `filled`), in a compatible order: boundary matrix columns of any length."""
+    cells, index = [], {}
+
+    def add(key, dim, faces):
+        index[key] = len(cells)
+        cells.append((dim, sorted(index[f] for f in faces)))
+
+    for y in range(h + 1):
+        for x in range(w + 1):
+            add(("v", x, y), 0, [])
+    for y in range(h + 1):
+        for x in range(w):
+            add(("h", x, y), 1, [("v", x, y), ("v", x + 1, y)])
+    for y in range(h):
+        for x in range(w + 1):
+            add(("u", x, y), 1, [("v", x, y), ("v", x, y + 1)])
+    for (x, y) in filled:
+        add(("s", x, y), 2, [("h", x, y), ("h", x, y + 1), ("u", x, y), ("u", x + 1, y)])
+    dims = np.array([c[0] for c in cells], np.int32)
+    colptr = np.concatenate([[0], np.cumsum([len(c[1]) for c in cells])]).astype(np.int64)
+    rows = np.array([r for c in cells for r in c[1]], np.int32)
+    return dims, colptr, rows

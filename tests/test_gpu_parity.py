@@ -257,7 +257,8 @@ def test_bit_packed_columns_modes_and_batches(ph, orc, strict, cor10):
     xe = pc.ensemble15("sphere_product15")
     K = orc.vr_build(xe, 5, scale_step=32768, n_scales=10)
     for mp in (2, -1):
-        ref = orc.reduce_pms(K, strict=strict, cor10=cor10, **({} if mp < 0 else {"max_passes": mp}))
+        cap = {} if mp < 0 else {"max_passes": mp}
+        ref = orc.reduce_pms(K, strict=strict, cor10=cor10, **cap)
         ctx = ph.Context(collect_stats=True, strict_phase2=strict, use_cor10=cor10,
                          dense_threshold=1)
         ctx.build_filtration_scales(torch.from_numpy(xe).cuda(), None, 5, 32768, 10)
@@ -375,7 +376,8 @@ def test_corollary10_predictions(ph, orc, use_graph):
     # pass, and every prediction is a true pair of the finished reduction (Lemma 9)
     import torch
 
-    cases = [(pc.random_cloud(40, 3, 109), 2, False, -1, 0), (pc.random_cloud(40, 3, 105), 2, True, -1, 0),
+    cases = [(pc.random_cloud(40, 3, 109), 2, False, -1, 0),
+             (pc.random_cloud(40, 3, 105), 2, True, -1, 0),
              (pc.ensemble15("trefoil15"), 5, False, 32768, 10), (pc.circle40(), 2, False, -1, 0)]
     for x, k, strict, step, ns in cases:
         K = (orc.vr_build(x, k, scale_step=step, n_scales=ns) if step > 0 else orc.vr_build(x, k))
@@ -422,7 +424,7 @@ def test_triangulations(ph, orc):
 def test_budgeted_phase2(ph, orc, sets, priority):
     # Phase II on p neighbour sets per pass (Sec. 3.4): the sets the GPU picks each pass are
     # the oracle's, so passes, every counter, E^l and the result agree exactly
-    from test_oracle_pins import BUDGET_EXAMPLE
+    from helpers import BUDGET_EXAMPLE
 
     K0 = orc.boundary_from_simplices(BUDGET_EXAMPLE)
     ref = orc.reduce_pms(K0, sets=sets, priority=priority)
@@ -741,7 +743,8 @@ def test_random_complexes_and_options(ph, orc):
         if rng.random() < 0.2:
             opts["use_cor10"] = False
         if rng.random() < 0.2:
-            opts.update(phase2_sets=int(rng.integers(1, 6)), phase2_priority=int(rng.integers(0, 2)))
+            opts.update(phase2_sets=int(rng.integers(1, 6)),
+                        phase2_priority=int(rng.integers(0, 2)))
         opts["use_graph"] = bool(rng.random() < 0.6)
         mp = -1 if rng.random() < 0.7 else int(rng.integers(0, 4))
         okw = {"strict": opts.get("strict_phase2", False), "cor10": opts.get("use_cor10", True),
@@ -885,11 +888,11 @@ def test_checkpoint_and_resume_through_the_reduced_matrix(ph, orc, mp):
 def test_cubical_complex(ph, orc):
     # columns of four rows (squares): the same lows, counters and reduced matrix as the oracle
     from oracle import Complex
-    from test_oracle_pins import _cubical_grid
+    from helpers import cubical_grid
 
     for w, h in ((3, 3), (7, 5)):
         filled = [(x, y) for x in range(w) for y in range(h) if (x + 2 * y) % 5]
-        dims, cp0, rows0 = _cubical_grid(w, h, filled)
+        dims, cp0, rows0 = cubical_grid(w, h, filled)
         K = Complex(dim=dims, diam2=np.zeros(len(dims), np.int64),
                     verts=np.full((len(dims), 4), -1, np.int32), colptr=cp0, rows=rows0)
         ref = orc.reduce_pms(K)
@@ -942,7 +945,8 @@ def _addition_cases(seed=5):
     rest = [cols[i] for i in order if i not in src_idx]
     cols = firsts + rest
     dims = np.array([0] * n_rows + [1] * len(cols), np.int32)
-    colptr = np.concatenate([[0] * (n_rows + 1), np.cumsum([len(c) for c in cols])]).astype(np.int64)
+    lengths = np.cumsum([len(c) for c in cols])
+    colptr = np.concatenate([[0] * (n_rows + 1), lengths]).astype(np.int64)
     rows = np.array([r for c in cols for r in c], np.int32)
     return dims, colptr, rows
 

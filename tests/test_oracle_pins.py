@@ -17,8 +17,9 @@ import numpy as np
 import pytest
 
 import pointclouds as pc
-from helpers import (betti_by_rank, closure, dense_boundary, gf2_rank, icosahedron_facets,
-                     ordered_by_dim_lex, random_compatible_order, random_reduction, rank_pairing)
+from helpers import (BUDGET_EXAMPLE, betti_by_rank, closure, cubical_grid, dense_boundary,
+                     gf2_rank, icosahedron_facets, ordered_by_dim_lex, random_compatible_order,
+                     random_reduction, rank_pairing)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 pytestmark = pytest.mark.filterwarnings("ignore")
@@ -267,7 +268,8 @@ def test_corollary10_predictions_are_pairs(orc):
     n_pred = 0
     for x, k, strict in [(pc.random_cloud(40, 3, 109), 2, False),
                          (pc.random_cloud(40, 3, 105), 2, True),
-                         (pc.random_cloud(30, 3, 5), 3, False), (pc.ensemble15("gaussian15"), 5, False)]:
+                         (pc.random_cloud(30, 3, 5), 3, False),
+                         (pc.ensemble15("gaussian15"), 5, False)]:
         K = orc.vr_build(x, k)
         lowstar = orc.reduce_std(K)[0]
         full = orc.reduce_pms(K, strict=strict)
@@ -358,9 +360,6 @@ def test_diagram_edges_realise_diameters(orc):
 #   p = 1 by |N|:             adds 3, 1, 1, 1, 1, 0  targets 4, 4, 3, 2, 1, 0
 #   p = 1 negatives first:    adds 1, 3, 1, 1, 1, 0  targets 4, 3, 3, 2, 1, 0
 #   p = 2 (either order):     adds 4, 2, 1, 0     targets 4, 3, 1, 0
-BUDGET_EXAMPLE = [(v,) for v in range(7)] + [(0, 1), (0, 2), (0, 3), (0, 4), (1, 4), (2, 4),
-                                            (3, 4), (0, 6), (5, 6)]
-
 
 @pytest.mark.parametrize("sets,priority,adds,targets", [
     (0, 0, [4, 3, 0], [4, 3, 0]),
@@ -454,32 +453,6 @@ def test_reduced_matrix_is_a_checkpoint(orc, kw):
         assert np.array_equal(orc.reduce_pms(R).low, want)
 
 
-def _cubical_grid(w, h, filled):
-    """The cubical complex of a w x h grid of unit squares (vertices, edges, and the squares
-    listed in `filled`), in a compatible order: boundary matrix columns of any length."""
-    cells, index = [], {}
-
-    def add(key, dim, faces):
-        index[key] = len(cells)
-        cells.append((dim, sorted(index[f] for f in faces)))
-
-    for y in range(h + 1):
-        for x in range(w + 1):
-            add(("v", x, y), 0, [])
-    for y in range(h + 1):
-        for x in range(w):
-            add(("h", x, y), 1, [("v", x, y), ("v", x + 1, y)])
-    for y in range(h):
-        for x in range(w + 1):
-            add(("u", x, y), 1, [("v", x, y), ("v", x, y + 1)])
-    for (x, y) in filled:
-        add(("s", x, y), 2, [("h", x, y), ("h", x, y + 1), ("u", x, y), ("u", x + 1, y)])
-    dims = np.array([c[0] for c in cells], np.int32)
-    colptr = np.concatenate([[0], np.cumsum([len(c[1]) for c in cells])]).astype(np.int64)
-    rows = np.array([r for c in cells for r in c[1]], np.int32)
-    return dims, colptr, rows
-
-
 def test_cubical_complex_betti_numbers(orc):
     # a non-simplicial complex (squares with four edges): a 3 x 3 grid with the middle square
     # left out has b0 = 1, b1 = 1 (the hole), b2 = 0; the full grid has b1 = 0
@@ -488,7 +461,7 @@ def test_cubical_complex_betti_numbers(orc):
     for filled, betti in (([(x, y) for x in range(3) for y in range(3) if (x, y) != (1, 1)],
                            [1, 1, 0]),
                           ([(x, y) for x in range(3) for y in range(3)], [1, 0, 0])):
-        dims, cp, rows = _cubical_grid(3, 3, filled)
+        dims, cp, rows = cubical_grid(3, 3, filled)
         K = Complex(dim=dims, diam2=np.zeros(len(dims), np.int64),
                     verts=np.full((len(dims), 4), -1, np.int32), colptr=cp, rows=rows)
         low = orc.reduce_pms(K).low
