@@ -2,8 +2,8 @@
 
 Filtrations of different clouds are independent problems, so clouds are split across ranks
 with no collective on the data path: longest-processing-time-first on an estimate of each
-cloud's work (the number of top-dimensional simplices, C(n, max_dim + 1)), each cloud to the
-currently lightest rank. Every rank computes the same assignment from the offsets alone.
+cloud's work (the number of simplices of dimension 0..max_dim, the sum of C(n, d + 1)), each
+cloud to the currently lightest rank. Every rank computes the same assignment from the offsets alone.
 """
 from __future__ import annotations
 
