@@ -2,6 +2,7 @@
 
 * Betti numbers of known triangulations (Sec. 2.1) and of complete skeleta (closed form).
 * The pairing lemma through GF(2) ranks, on every tiny complex (no column operations).
+* Homology/cohomology duality: the anti-transposed matrix reduces to the mirrored pairs.
 * Order independence of lowstar (Sec. 2.3): Algorithms 1, 2 and 3 and random valid reductions.
 * R = D V with V upper-unitriangular and R reduced.
 * Theorem 5 (beta bounds), Lemma 11 (essential estimate), Theorem 8 (progress each pass).
@@ -468,3 +469,43 @@ def test_cubical_complex_betti_numbers(orc):
         _, ess = orc.pairs_and_essential(low, dims)
         assert np.bincount(dims[ess], minlength=3).tolist() == betti
         assert np.array_equal(low, orc.reduce_std(K)[0])
+
+
+def _anti_transpose(orc, K):
+    """J D^T J of the boundary matrix D (J reverses the index order): the coboundary matrix of
+    the reversed filtration. It squares to zero and is graded by dim' = d_max - dim."""
+    m = K.m
+    cols = [[] for _ in range(m)]
+    cp, rows = K["colptr"], K["rows"]
+    for j in range(m):
+        for i in rows[cp[j]:cp[j + 1]]:
+            cols[m - 1 - int(i)].append(m - 1 - j)
+    colptr = np.zeros(m + 1, np.int64)
+    colptr[1:] = np.cumsum([len(c) for c in cols])
+    flat = np.array([r for c in cols for r in sorted(c)], np.int32)
+    dim = (int(K["dim"].max()) - K["dim"][::-1]).astype(np.int32)
+    return orc.Complex(dim=np.ascontiguousarray(dim), diam2=np.zeros(m, np.int64),
+                       verts=np.full((m, 4), -1, np.int32), colptr=colptr, rows=flat)
+
+
+def test_cohomology_duality_of_pairs(orc):
+    # Reducing the coboundary matrix of the reversed filtration gives the same pairs, mirrored:
+    # low(j) = i  <=>  low'(m-1-i) = m-1-j, and the unpaired indices mirror too. The ranks of the
+    # lower-left submatrices that fix the pairing are unchanged by the anti-transpose.
+    for name, K in _tiny_complexes(orc):
+        m = K.m
+        Kc = _anti_transpose(orc, K)
+        Dc = dense_boundary(Kc).astype(np.int64)
+        assert not ((Dc @ Dc) % 2).any(), name
+        low = orc.reduce_std(K)[0]
+        mirror = np.full(m, -1, np.int32)
+        for j in np.nonzero(low >= 0)[0]:
+            mirror[m - 1 - low[j]] = m - 1 - j
+        assert np.array_equal(rank_pairing(dense_boundary(Kc)), mirror), name
+        assert np.array_equal(orc.reduce_std(Kc)[0], mirror), name
+        assert np.array_equal(orc.reduce_twist(Kc)[0], mirror), name
+        assert np.array_equal(orc.reduce_pms(Kc).low, mirror), name
+        assert np.array_equal(orc.reduce_pms(Kc, strict=True).low, mirror), name
+        _, ess = orc.pairs_and_essential(low, K["dim"])
+        _, ess_c = orc.pairs_and_essential(mirror, Kc["dim"])
+        assert sorted(m - 1 - ess) == sorted(ess_c.tolist()), name
