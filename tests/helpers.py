@@ -28,6 +28,22 @@ def dense_boundary(K) -> np.ndarray:
     return D
 
 
+def anti_transpose(K):
+    """J D^T J of the boundary matrix D of K, J reversing the index order: the coboundary matrix
+    of the reversed filtration, as (dim, colptr, rows). It squares to zero and is graded by
+    dim' = d_max - dim, so it is a boundary matrix in its own right."""
+    dim, cp, rows = K["dim"], np.asarray(K["colptr"], np.int64), np.asarray(K["rows"], np.int64)
+    m = len(dim)
+    col = np.repeat(np.arange(m, dtype=np.int64), np.diff(cp))
+    new_col, new_row = m - 1 - rows, m - 1 - col
+    order = np.lexsort((new_row, new_col))
+    colptr = np.zeros(m + 1, np.int64)
+    colptr[1:] = np.cumsum(np.bincount(new_col, minlength=m))
+    new_dim = (int(dim.max()) - np.asarray(dim)[::-1]).astype(np.int32)
+    return (np.ascontiguousarray(new_dim), colptr,
+            np.ascontiguousarray(new_row[order].astype(np.int32)))
+
+
 def _insert(basis: dict, v: int) -> bool:
     while v:
         h = v.bit_length() - 1

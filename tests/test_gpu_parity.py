@@ -420,6 +420,38 @@ def test_triangulations(ph, orc):
         assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8]), name
 
 
+@pytest.mark.parametrize("kw", [{}, {"strict_phase2": True}, {"dense_threshold": 1},
+                                {"warp_chunk_words": -1},
+                                {"use_graph": False, "dense_threshold": -1,
+                                 "warp_chunks_below": -1}])
+def test_coboundary_matrix(ph, orc, kw):
+    # The anti-transposed boundary matrix (the coboundary of the reversed filtration) loaded as
+    # a general boundary: columns of up to n - 1 rows and an empty top-dimensional block. The
+    # GPU reduces it to the oracle's lowstar pass by pass, and that lowstar mirrors the pairs
+    # of the filtration itself (duality of persistent homology and cohomology).
+    from helpers import anti_transpose
+
+    for x, k in ((pc.random_cloud(40, 3, 600), 2), (pc.random_cloud(18, 3, 601), 4)):
+        K = orc.vr_build(x, k)
+        m = K.m
+        dim, cp, rows = anti_transpose(K)
+        Kc = orc.Complex(dim=dim, diam2=np.zeros(m, np.int64),
+                         verts=np.full((m, 4), -1, np.int32), colptr=cp, rows=rows)
+        ref = orc.reduce_pms(Kc, strict=kw.get("strict_phase2", False))
+        ctx = ph.Context(collect_stats=True, **kw)
+        ctx.load_boundary(dim, cp, rows)
+        st = ctx.reduce()
+        assert st["converged"] and st["passes"] == ref.passes
+        low = ctx.filtration(0)["low"]
+        assert np.array_equal(low, ref.low)
+        assert np.array_equal(ctx.pass_stats()[:, :8], ref.stats[:, :8])
+        low_k = orc.reduce_twist(K)[0]
+        nz = np.nonzero(low >= 0)[0]
+        mirror = np.full(m, -1, np.int32)
+        mirror[m - 1 - low[nz]] = m - 1 - nz
+        assert np.array_equal(mirror, low_k)
+
+
 @pytest.mark.parametrize("sets,priority", [(1, 0), (1, 1), (3, 0), (7, 1), (10 ** 6, 0)])
 def test_budgeted_phase2(ph, orc, sets, priority):
     # Phase II on p neighbour sets per pass (Sec. 3.4): the sets the GPU picks each pass are

@@ -18,9 +18,9 @@ import numpy as np
 import pytest
 
 import pointclouds as pc
-from helpers import (BUDGET_EXAMPLE, betti_by_rank, closure, cubical_grid, dense_boundary,
-                     gf2_rank, icosahedron_facets, ordered_by_dim_lex, random_compatible_order,
-                     random_reduction, rank_pairing)
+from helpers import (BUDGET_EXAMPLE, anti_transpose, betti_by_rank, closure, cubical_grid,
+                     dense_boundary, gf2_rank, icosahedron_facets, ordered_by_dim_lex,
+                     random_compatible_order, random_reduction, rank_pairing)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 pytestmark = pytest.mark.filterwarnings("ignore")
@@ -471,30 +471,15 @@ def test_cubical_complex_betti_numbers(orc):
         assert np.array_equal(low, orc.reduce_std(K)[0])
 
 
-def _anti_transpose(orc, K):
-    """J D^T J of the boundary matrix D (J reverses the index order): the coboundary matrix of
-    the reversed filtration. It squares to zero and is graded by dim' = d_max - dim."""
-    m = K.m
-    cols = [[] for _ in range(m)]
-    cp, rows = K["colptr"], K["rows"]
-    for j in range(m):
-        for i in rows[cp[j]:cp[j + 1]]:
-            cols[m - 1 - int(i)].append(m - 1 - j)
-    colptr = np.zeros(m + 1, np.int64)
-    colptr[1:] = np.cumsum([len(c) for c in cols])
-    flat = np.array([r for c in cols for r in sorted(c)], np.int32)
-    dim = (int(K["dim"].max()) - K["dim"][::-1]).astype(np.int32)
-    return orc.Complex(dim=np.ascontiguousarray(dim), diam2=np.zeros(m, np.int64),
-                       verts=np.full((m, 4), -1, np.int32), colptr=colptr, rows=flat)
-
-
 def test_cohomology_duality_of_pairs(orc):
     # Reducing the coboundary matrix of the reversed filtration gives the same pairs, mirrored:
     # low(j) = i  <=>  low'(m-1-i) = m-1-j, and the unpaired indices mirror too. The ranks of the
     # lower-left submatrices that fix the pairing are unchanged by the anti-transpose.
     for name, K in _tiny_complexes(orc):
         m = K.m
-        Kc = _anti_transpose(orc, K)
+        dim_c, cp_c, rows_c = anti_transpose(K)
+        Kc = orc.Complex(dim=dim_c, diam2=np.zeros(m, np.int64),
+                         verts=np.full((m, 4), -1, np.int32), colptr=cp_c, rows=rows_c)
         Dc = dense_boundary(Kc).astype(np.int64)
         assert not ((Dc @ Dc) % 2).any(), name
         low = orc.reduce_std(K)[0]
