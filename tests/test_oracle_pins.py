@@ -3,6 +3,7 @@
 * Betti numbers of known triangulations (Sec. 2.1) and of complete skeleta (closed form).
 * The pairing lemma through GF(2) ranks, on every tiny complex (no column operations).
 * Homology/cohomology duality: the anti-transposed matrix reduces to the mirrored pairs.
+* A seeded sweep of 100 random complexes: every reduction and option mix reaches the rank pairing.
 * Order independence of lowstar (Sec. 2.3): Algorithms 1, 2 and 3 and random valid reductions.
 * R = D V with V upper-unitriangular and R reduced.
 * Theorem 5 (beta bounds), Lemma 11 (essential estimate), Theorem 8 (progress each pass).
@@ -494,3 +495,33 @@ def test_cohomology_duality_of_pairs(orc):
         _, ess = orc.pairs_and_essential(low, K["dim"])
         _, ess_c = orc.pairs_and_essential(mirror, Kc["dim"])
         assert sorted(m - 1 - ess) == sorted(ess_c.tolist()), name
+
+
+def _random_complex(orc, seed):
+    # closure of a few random facets of dimensions 1-3 on at most 8 vertices, in a random order
+    # compatible with the face relation (a filtration of a complex that is not a VR complex)
+    rng = np.random.default_rng(seed)
+    nv = int(rng.integers(4, 9))
+    facets = [tuple(rng.choice(nv, size=int(rng.integers(2, 5)), replace=False))
+              for _ in range(int(rng.integers(2, 7)))]
+    return orc.boundary_from_simplices(random_compatible_order(closure(facets), seed))
+
+
+@pytest.mark.parametrize("block", range(4))
+def test_random_complexes_all_modes_reach_rank_pairing(orc, block):
+    # every reduction of the oracle, in every option mix, ends at the pairing that the ranks of
+    # the lower-left submatrices fix (pairing lemma); none of them may take a wrong addition
+    modes = [{}, {"strict": True}, {"cor10": False}, {"sets": 1, "priority": 0},
+             {"sets": 2, "priority": 1}, {"strict": True, "sets": 1, "priority": 1}]
+    for seed in range(block * 25, block * 25 + 25):
+        K = _random_complex(orc, seed)
+        D = dense_boundary(K)
+        expect = rank_pairing(D)
+        assert np.array_equal(orc.reduce_std(K)[0], expect), seed
+        assert np.array_equal(orc.reduce_twist(K)[0], expect), seed
+        for kw in modes:
+            r = orc.reduce_pms(K, **kw)
+            assert r.converged and np.array_equal(r.low, expect), (seed, kw)
+        Dv = D.astype(np.int64)
+        _, _, R, V = orc.reduce_std(K, track_v=True)
+        assert np.array_equal((Dv @ V.astype(np.int64)) % 2, R.astype(np.int64)), seed
