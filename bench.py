@@ -307,23 +307,15 @@ def main():
     # graph's conditional body), with per-pass counters for its algorithmic bytes
     prof = ph.Context(**dict(tuned, use_graph=False, collect_stats=True, time_kernels=True))
     step(coords, prof)
-    pst = [step(coords, prof) for _ in range(2)]
     peak, peak_kind = _peak_hbm()
-    add_bytes = sum(s["add_bytes"] for s in pst)
-    add_ms = sum(s["ms_add"] for s in pst)
-    add_launches = sum(s["add_launches"] for s in pst)
-    achieved = (add_bytes / add_launches) / (add_ms / add_launches / 1e3) / 1e9 if add_ms else None
-    traffic = _profile_traffic("k_add", args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None,
-                "traffic": traffic, "kernel": "k_add (Phase II column additions)",
-                "peak_kind": peak_kind,
-                "bytes_per_launch": add_bytes / max(add_launches, 1),
-                "ms_per_launch": add_ms / max(add_launches, 1),
-                "launches_per_step": add_launches / len(pst),
-                "share_of_step": (add_ms / len(pst)) / (total_ms / args.steps),
-                "timing": "CUDA events around each k_add launch, host-driven pass loop, "
-                          "same workload, 2 steps after 1 warm-up"}
+    roofline = kadd_roofline(ph, prof, lambda: step(coords, prof), peak, peak_kind)
+    roofline["traffic"] = _profile_traffic("k_add", args.workload)
+    roofline["share_of_step"] = roofline.pop("_ms_per_reduction") / (total_ms / args.steps)
+    # the same reduction through the timed graph loop and through the host-driven loop (whose
+    # k_add launches the events above time), each reduction alone, after a warm-up
+    roofline["reduce_ms_graph_loop"] = _reduce_ms(torch, ph, tuned, coords, offsets, wl, True)
+    roofline["reduce_ms_host_loop"] = _reduce_ms(torch, ph, tuned, coords, offsets, wl, False)
+    pst = [roofline.pop("_last_stats")]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -357,16 +349,196 @@ def main():
             "bytes": b_bytes, "nnz": nnz}
     if world == 1 and not args.no_forms and not wl.get("batched"):
         line["forms"] = compare_forms(ph, torch, dev)
+        line["configs"] = other_configs(ph, torch, dev, peak, peak_kind)
+        line["early"] = early_summary(ph, torch)
     if world == 1 and not args.no_cpu_baseline:
         n_sample = 250
         ms, secs = cpu_oracle_sample(n_sample)
-        line["cpu_baseline"] = {
-            "value": ms / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n_sample} of the 400 torus points: complete VR <= dim 2, m={ms}; "
-                      f"oracle VR build + Algorithm 3 (twist), {secs:.1f} s on one core"}
+        live = {"value": ms / secs, "unit": UNIT, "cores": 1,
+                "sample": f"first {n_sample} of the 400 torus points: complete VR <= dim 2, "
+                          f"m={ms}; oracle VR build + Algorithm 3 (twist), {secs:.1f} s on one "
+                          "core of this host, timed in this run"}
+        host, cached = cached_oracle_times()
+        full = (cached or {}).get("workloads", {}).get(args.workload)
+        if full:
+            line["cpu_baseline"] = {
+                "value": full["simplices_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the whole {args.workload} workload (m={full['m']}): oracle VR build "
+                          f"({full['build_s']} s) + Algorithm 3 (twist, {full['reduce_s']} s) "
+                          f"on one core of a GB300 box's host ({cached['cpu']}, {host}), timed "
+                          "once by tests/golden/time_oracle.py and stored",
+                "reduce_only_simplices_per_s": full["reduce_simplices_per_s"],
+                "live_subsample": live}
+        else:
+            line["cpu_baseline"] = dict(live, kind="oracle")
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# algorithmic bytes of the additions kernel, per the method's minimum traffic: 8 B per nontrivial
+# XOR (4 * (|src| + |tgt| + |out|) = 8 * |src union tgt|) and 26 B per active column per pass
+# (column header and low read 4, low write 4, table atomic 4, table read 4, flags 1, active list
+# read and write 8 -- charged to k_add, which dominates the pass)
+BYTES_PER_XOR = 8
+BYTES_PER_ACTIVE = 26
+
+
+def kadd_roofline(ph, prof, run_step, peak, peak_kind, reps=2):
+    """k_add's achieved algorithmic bandwidth: CUDA events around every k_add launch of `reps`
+    host-driven reductions (library stream), bytes from the same reductions' per-pass counters
+    (active columns and XORs; the rows copied without an addition are reported apart)."""
+    xors = active = copied = launches = 0
+    ms = 0.0
+    st = None
+    for _ in range(reps):
+        st = run_step()
+        ps = prof.pass_stats()
+        xors += int(ps[:, ph.PS_FIELDS.index("xors")].sum())
+        active += int(ps[:, ph.PS_FIELDS.index("active")].sum())
+        copied += int(ps[:, ph.PS_FIELDS.index("copied")].sum())
+        launches += st["add_launches"]
+        ms += st["ms_add"]
+    nbytes = BYTES_PER_XOR * xors + BYTES_PER_ACTIVE * active
+    per_launch_ms = ms / max(launches, 1)
+    achieved = nbytes / max(launches, 1) / (per_launch_ms / 1e3) / 1e9 if ms else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "kernel": "k_add (Phase II column additions)", "peak_kind": peak_kind,
+            "bytes_per_launch": nbytes / max(launches, 1),
+            "bytes_model": f"{BYTES_PER_XOR} B per nontrivial XOR + {BYTES_PER_ACTIVE} B per "
+                           "active column per pass (counters below, per reduction)",
+            "xors_per_reduction": xors // reps, "active_column_passes_per_reduction": active // reps,
+            "copied_rows_per_reduction": copied // reps,
+            "copied_row_bytes_per_launch": 8 * copied / max(launches, 1),
+            "ms_per_launch": per_launch_ms, "launches_per_step": launches / reps,
+            "timing": f"CUDA events around each k_add launch, host-driven pass loop, same "
+                      f"workload, {reps} reductions after 1 warm-up",
+            "_ms_per_reduction": ms / reps, "_last_stats": st}
+
+
+def _reduce_ms(torch, ph, tuned, coords, offsets, wl, graph, reps=3):
+    """Median CUDA-event time of ph_reduce alone on a freshly built filtration."""
+    ctx = ph.Context(**dict(tuned, use_graph=graph))
+    stream = torch.cuda.current_stream()
+    times = []
+    for it in range(reps + 1):
+        ctx.build_filtration(coords, offsets, wl["max_dim"], wl["max_diam2"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.reduce()
+        e1.record(stream)
+        e1.synchronize()
+        if it:
+            times.append(e0.elapsed_time(e1))
+    ctx.close()
+    return statistics.median(times)
+
+
+def _golden(name):
+    p = ROOT / "tests" / "golden" / f"{name}.json"
+    return json.loads(p.read_text()) if p.exists() else None
+
+
+def _canon_sha(pr, es):
+    """SHA-256 of the canonical pairs (sorted by death, then birth) and essential indices."""
+    b, d = pr["birth"].cpu().numpy(), pr["death"].cpu().numpy()
+    o = np.lexsort((b, d))
+    p = np.stack([b[o], d[o]], 1).astype(np.int64)
+    e = np.sort(es["idx"].cpu().numpy()).astype(np.int64)
+    return (hashlib.sha256(p.tobytes()).hexdigest(), hashlib.sha256(e.tobytes()).hexdigest(),
+            p, e)
+
+
+def other_configs(ph, torch, dev, peak, peak_kind):
+    """The single-filtration configurations besides the headline one (circle40, gauss8_120):
+    the same step (build + reduce + extract, CUDA events, L2 flushed before each), passes,
+    bit-exactness against the oracle's stored result, and k_add's roofline fraction."""
+    from paper_1708_04710_gb300 import autotune
+
+    out = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    for name in ("circle40", "gauss8_120"):
+        wl = WORKLOADS[name]
+        coords = torch.from_numpy(wl["gen"]()).to(dev)
+        tuned = autotune.tune(coords, None, wl["max_dim"], wl["max_diam2"])
+        ctx = ph.Context(**tuned)
+        times = []
+        for it in range(3 + 10):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.build_filtration(coords, None, wl["max_dim"], wl["max_diam2"])
+            st = ctx.reduce()
+            pr = ctx.pairs(0, on_device=True)
+            es = ctx.essential(0, on_device=True)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= 3:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        g = _golden(name)
+        ps, es_sha, _, _ = _canon_sha(pr, es)
+        exact = (g is not None and ps == g["pairs_sha"] and es_sha == g["ess_sha"]
+                 and st["passes"] == g["passes"])
+        prof = ph.Context(**dict(tuned, use_graph=False, collect_stats=True, time_kernels=True))
+
+        def run(prof=prof, coords=coords, wl=wl):
+            prof.build_filtration(coords, None, wl["max_dim"], wl["max_diam2"])
+            return prof.reduce()
+
+        run()
+        rl = kadd_roofline(ph, prof, run, peak, peak_kind)
+        rl.pop("_last_stats")
+        rl.pop("_ms_per_reduction")
+        out[name] = {"desc": wl["desc"], "m": ctx.m, "ms_per_step": ms,
+                     "simplices_per_s": ctx.m / (ms / 1e3), "passes": st["passes"],
+                     "bit_exact_vs_oracle": exact, "autotuned": tuned,
+                     "k_add": {k: rl[k] for k in ("achieved", "frac", "bytes_per_launch",
+                                                   "ms_per_launch", "launches_per_step")}}
+        ctx.close()
+        prof.close()
+    return out
+
+
+def early_summary(ph, torch):
+    """Early stopping on the four 15-point stand-in ensembles (complete VR to dimension 5 on the
+    paper's scale grid): passes, additions, and the iterations Algorithm 2 needs to reach an
+    l1 error of 0.01 and an essential-estimate precision of 0.95 and 1.0 (Sec. 4.2-4.3), for
+    the default rule and for the paper's rule without Corollary 10's zero case."""
+    from paper_1708_04710_gb300 import early
+
+    step, n_scales = pc.GRID_SCALE // 2, 10
+    res = {}
+    for name in pc.ENSEMBLES:
+        x = torch.from_numpy(pc.ensemble15(name)).cuda()
+        res[name] = {}
+        for mode, strict, cor10 in (("default", False, True), ("paper_rule", True, False)):
+            ctx = ph.Context(collect_stats=True, strict_phase2=strict, use_cor10=cor10)
+            ctx.build_filtration_scales(x, None, 5, step, n_scales)
+            pr = early.profile(ctx)
+            res[name][mode] = {
+                "m": pr["m"], "passes": pr["passes"], "adds": pr["adds"][-1],
+                "to_l1_0.01": early.iterations_to(pr["l1_error"], [0.01])[0.01],
+                "to_precision_0.95": early.iterations_to(pr["precision"], [0.95],
+                                                         below=False)[0.95],
+                "to_precision_1.0": early.iterations_to(pr["precision"], [1.0],
+                                                        below=False)[1.0]}
+            ctx.close()
+    return res
+
+
+def cached_oracle_times():
+    """The oracle's full-size times stored by tests/golden/time_oracle.py (GPU machine host first)."""
+    p = ROOT / "tests" / "golden" / "oracle_times.json"
+    if not p.exists():
+        return None, None
+    data = json.loads(p.read_text())
+    for key in ("aarch64", "x86_64"):
+        if key in data:
+            return key, data[key]
+    return None, None
 
 
 def run_early():
@@ -447,11 +619,21 @@ def compare_forms(ph, torch, dev):
 
     tb = _timed(torch, batched)
     mb = ctx.m
+    # every cloud's pairs and essentials against the oracle's stored digest of all of them
+    batched()
+    h = hashlib.sha256()
+    for c in range(len(off) - 1):
+        _, _, p_c, e_c = _canon_sha(ctx.pairs(c, on_device=False),
+                                    ctx.essential(c, on_device=False))
+        h.update(p_c.tobytes())
+        h.update(e_c.tobytes())
+    gb = _golden("batch512")
     tl = _timed(torch, looped, reps=1)
     out["batched"] = {"workload": "batch512: 512 clouds, n ~ U{20..120}, sphere/torus/N(0,I3), "
                                   "complete VR <= dim 2", "m": mb,
                       "batched_simplices_per_s": mb / tb, "looped_plain_simplices_per_s": mb / tl,
-                      "batched_ms": 1e3 * tb, "looped_plain_ms": 1e3 * tl}
+                      "batched_ms": 1e3 * tb, "looped_plain_ms": 1e3 * tl,
+                      "bit_exact_vs_oracle": gb is not None and h.hexdigest() == gb["all_sha"]}
     # differentiable: loss + gradient over 256 clouds vs the plain build + reduce of the same
     from paper_1708_04710_gb300.diff import diagram_loss
 
@@ -469,12 +651,25 @@ def compare_forms(ph, torch, dev):
 
     tf = _timed(torch, fwd_bwd)
     tp = _timed(torch, plain)
+    # every cloud's pairing and loss against the oracle's stored values
+    gd = _golden("diff256")
+    lossd = diagram_loss(cd, offd, 1, dctx).detach().cpu().numpy()
+    exact = gd is not None
+    loss_rel = 0.0
+    for c in range(len(offd) - 1) if gd is not None else ():
+        ps, es_sha, _, _ = _canon_sha(dctx.pairs(c, on_device=False),
+                                      dctx.essential(c, on_device=False))
+        gc = gd["clouds"][c]
+        exact &= ps == gc["pairs_sha"] and es_sha == gc["ess_sha"]
+        loss_rel = max(loss_rel, abs(float(lossd[c]) - gc["loss"]) / gc["loss"])
     out["differentiable"] = {"workload": "diff256: 256 clouds x 64 points on S^2 + noise, "
                                          "complete VR <= dim 2, loss over H1 pairs",
                              "m": dctx.m, "forward_backward_ms": 1e3 * tf,
                              "plain_build_reduce_ms": 1e3 * tp,
                              "forward_backward_simplices_per_s": dctx.m / tf,
-                             "plain_simplices_per_s": dctx.m / tp}
+                             "plain_simplices_per_s": dctx.m / tp,
+                             "bit_exact_vs_oracle": bool(exact),
+                             "max_loss_rel_err_vs_oracle_fp64": loss_rel}
     return out
 
 

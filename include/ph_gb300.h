@@ -324,7 +324,10 @@ int ph_get_filtration(ph_ctx* ctx, int32_t cloud, int32_t* dim, int64_t* diam2, 
  * diameter; a simplex's realising edge is itself for an edge, else the realising edge of its
  * last face in the filtration), and loss = sum (d - b)^2 per cloud. The pairing is exact and
  * piecewise constant, so only b and d carry gradient.
- *   coords   device float [N][D], the coordinates the filtration was built from.
+ *   coords   device float [N][D], the coordinates the filtration was built from: N and D of
+ *            that build (n_points * D floats). The kernels read coords at the build's point
+ *            rows, so a smaller array is read out of bounds; the library cannot see its size.
+ *   D        must equal the build's D (PH_ERR_INVALID otherwise, before any launch).
  *   loss     device float [n_clouds + 1]: per-cloud losses, then their sum.
  *   n_pairs  host, optional: number of pairs summed.
  * Needs ph_reduce first and dim + 1 <= max_dim. Synchronises the stream. */
@@ -334,6 +337,8 @@ int ph_diagram_loss(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim, fl
 /* Gradient of the per-cloud losses of ph_diagram_loss with respect to the coordinates:
  * grad_coords (device float [N][D]) += sum over clouds of grad_loss[c] * d loss_c / d coords,
  * scattered to the two points of each realising edge (a zero-length edge contributes nothing).
+ *   coords, grad_coords  device float, n_points * D each, N and D of the build (as above).
+ *   D          must equal the build's D (PH_ERR_INVALID otherwise, before any launch).
  *   grad_loss  device float [n_clouds]. Asynchronous. */
 int ph_diagram_backward(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim,
                         const float* grad_loss, float* grad_coords);
@@ -352,7 +357,9 @@ int ph_diagram_backward(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim
  *   stream        cudaStream_t as void*.
  * Allocates nothing (no cudaMalloc, cudaFree or allocator call). The first call on a device
  * looks up the scratch's device address with cudaGetSymbolAddress; make that first call before
- * any stream capture on that device. Every call shares the one scratch array, which it resets
+ * any stream capture on that device. The address is kept for the process: after a
+ * cudaDeviceReset of that device the scratch is gone, so do not call this entry point on it
+ * again in the same process. Every call shares the one scratch array, which it resets
  * at its start: calls that overlap on the GPU (other streams or threads) race and give wrong
  * results. Rows outside [0, n_rows) are skipped and make the call return PH_ERR_INVALID.
  * Synchronises `stream`. */

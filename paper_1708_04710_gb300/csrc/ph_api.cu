@@ -58,6 +58,8 @@ void ph_ctx::free_all() {
   d2tab = nullptr;
   d_seg_start = nullptr;
   m = nnz = 0;
+  D = 0;
+  n_points = 0;
 }
 
 namespace ph {

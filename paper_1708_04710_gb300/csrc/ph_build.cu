@@ -569,6 +569,8 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   ctx->max_dim = max_dim;
   ctx->vbits = vbits;
   ctx->pt_off = off;
+  ctx->D = D;
+  ctx->n_points = n_points;
 
   // device copies of the small tables: off, mo, cand[2..kVrSlots]
   const int ntab = 2 + (kVrSlots - 1);

@@ -219,6 +219,9 @@ int ph_diagram_loss(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim, fl
   PH_REQUIRE(coords && loss, PH_ERR_INVALID, "NULL argument");
   PH_REQUIRE(dim >= 0 && dim + 1 <= ctx->max_dim, PH_ERR_INVALID,
              "dim + 1 must not exceed the filtration's max_dim");
+  // the kernels index coords by the build's point rows: any other shape reads out of bounds
+  PH_REQUIRE(D == ctx->D, PH_ERR_INVALID,
+             "D must equal the D of the build (" + std::to_string(ctx->D) + ")");
   const ph::DiagLayout L = ph::layout_of(ctx);
   unsigned long long* cnt = ph::alloc_n<unsigned long long>(ctx, 1);
   int64_t* d_pt = ph::alloc_n<int64_t>(ctx, ctx->n_clouds + 1);
@@ -248,6 +251,8 @@ int ph_diagram_backward(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim
   PH_REQUIRE(coords && grad_loss && grad_coords, PH_ERR_INVALID, "NULL argument");
   PH_REQUIRE(dim >= 0 && dim + 1 <= ctx->max_dim, PH_ERR_INVALID,
              "dim + 1 must not exceed the filtration's max_dim");
+  PH_REQUIRE(D == ctx->D, PH_ERR_INVALID,
+             "D must equal the D of the build (" + std::to_string(ctx->D) + ")");
   const ph::DiagLayout L = ph::layout_of(ctx);
   int64_t* d_pt = ph::alloc_n<int64_t>(ctx, ctx->n_clouds + 1);
   PH_CUDA(cudaMemcpyAsync(d_pt, ctx->pt_off.data(), (ctx->n_clouds + 1) * sizeof(int64_t),

@@ -145,6 +145,8 @@ struct ph_ctx {
   bool built = false;
   bool reduced = false;
   bool is_vr = false;  // built from points (vertex tuples known)
+  int32_t D = 0;          // coordinates per point of a VR build (0: none)
+  int64_t n_points = 0;   // points of a VR build: coordinate arrays hold n_points * D values
   int32_t n_clouds = 0;
   int32_t max_dim = 0;
   int64_t m = 0;

@@ -1023,8 +1023,13 @@ __device__ __forceinline__ void lane_merge_regs(const int32_t* __restrict__ sA, 
 // job's running count plus the count of the job's earlier lanes in the round. KM > 0: the piece
 // is merged once into registers and the rows that are not one of an equal pair are written;
 // KM = 0 (a forced piece size without a register form): counted first, then merged again.
+#ifndef PH_STAGED_INLINE
+#define PH_STAGED_ATTR __noinline__
+#else
+#define PH_STAGED_ATTR __forceinline__
+#endif
 template <int KM>
-__device__ __noinline__ void staged_rounds(WarpStage& S, int c, int c_end, int p0, int nch,
+__device__ PH_STAGED_ATTR void staged_rounds(WarpStage& S, int c, int c_end, int p0, int nch,
                                               int km) {
   const int lane = lane_id();
   const int in_c = S.in_off[c];
@@ -1439,8 +1444,11 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
 // kDense: the pass may meet bit-packed columns or convert some; the row-list variant carries none
 // of it. kWarp: chunks of 32 slots claimed by single warps. The host picks the variant from
 // DevState::dense_on and warp_on (a separate graph for each).
+#ifndef PH_ADD_MIN_BLOCKS
+#define PH_ADD_MIN_BLOCKS 8
+#endif
 template <bool kDense, bool kWarp>
-__global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
+__global__ void __launch_bounds__(kAddThreads, PH_ADD_MIN_BLOCKS) k_add(RArgs a) {
   __shared__ int64_t sh[kAddWarps + 1];
   __shared__ int64_t s_chunk;
   __shared__ int64_t s_prefix[2];

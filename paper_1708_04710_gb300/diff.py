@@ -24,11 +24,17 @@ class DiagramLoss(torch.autograd.Function):
         ctx.save_for_backward(coords)
         ctx.dim = dim
         ctx.context = context
+        ctx.build = context.builds  # the filtration this loss was computed on
         return loss[:-1].clone()
 
     @staticmethod
     def backward(ctx, grad_loss):
         (coords,) = ctx.saved_tensors
+        if ctx.context.builds != ctx.build:
+            # the gradient scatters through the context's current pairing: after another
+            # build it would belong to a different filtration
+            raise RuntimeError("the context was rebuilt between this loss's forward and backward;"
+                               " give each loss its own Context")
         grad = ctx.context.diagram_backward(coords.detach(), grad_loss, ctx.dim)
         return grad, None, None, None
 

@@ -188,6 +188,8 @@ class Context:
                                            c_void_p(self.stream.cuda_stream)))
         self.n_clouds = 0
         self.m = 0
+        self.builds = 0        # filtrations built or loaded so far
+        self._points = None    # (N, D) of the current VR build from float32 coordinates
 
     # -- helpers --------------------------------------------------------------------------
     def _check(self, rc: int) -> int:
@@ -223,10 +225,12 @@ class Context:
             offs = np.ascontiguousarray(np.asarray(cloud_offsets, dtype=np.int64))
             nc = len(offs) - 1
         m = c_int64(0)
+        self._points = None
         self._check(self.lib.ph_build_filtration(self._h, _ptr(coords), _ptr(offs), nc, N, D,
                                                  max_dim, int(max_diam2), byref(m)))
         self.n_clouds = nc
         self.m = m.value
+        self.builds += 1
         return self.m
 
     def build_filtration_scales(self, coords, cloud_offsets=None, max_dim: int = 2,
@@ -242,11 +246,13 @@ class Context:
             np.asarray(cloud_offsets, dtype=np.int64))
         nc = 1 if offs is None else len(offs) - 1
         m = c_int64(0)
+        self._points = None
         self._check(self.lib.ph_build_filtration_scales(self._h, _ptr(coords), _ptr(offs), nc, N,
                                                         D, max_dim, int(scale_step),
                                                         int(n_scales), byref(m)))
         self.n_clouds = nc
         self.m = m.value
+        self.builds += 1
         return self.m
 
     def build_filtration_f32(self, coords, cloud_offsets=None, max_dim: int = 2,
@@ -260,15 +266,29 @@ class Context:
             np.asarray(cloud_offsets, dtype=np.int64))
         nc = 1 if offs is None else len(offs) - 1
         m = c_int64(0)
+        self._points = None
         self._check(self.lib.ph_build_filtration_f32(self._h, _ptr(coords), _ptr(offs), nc, N, D,
                                                      max_dim, int(max_diam2), byref(m)))
+        self._points = (int(N), int(D))
         self.n_clouds = nc
         self.m = m.value
+        self.builds += 1
         return self.m
+
+    def _check_points(self, coords):
+        """The diagram kernels index coords by the build's point rows: the tensor must be the
+        float32 (N, D) CUDA array of the last build_filtration_f32."""
+        if self._points is None:
+            raise PHError(-1, "diagram losses need a filtration built by build_filtration_f32")
+        if (not coords.is_cuda or coords.dtype != self._torch.float32
+                or tuple(coords.shape) != self._points):
+            raise PHError(-1, f"coords must be a float32 CUDA tensor of shape {self._points} "
+                              f"(got {coords.dtype} {tuple(coords.shape)})")
 
     def diagram_loss(self, coords, dim: int = 1):
         """Per-cloud losses followed by their sum (float32 tensor, n_clouds + 1)."""
         torch = self._torch
+        self._check_points(coords)
         coords = coords.contiguous()
         out = torch.empty(self.n_clouds + 1, dtype=torch.float32, device=coords.device)
         n = c_int64(0)
@@ -279,10 +299,16 @@ class Context:
 
     def diagram_backward(self, coords, grad_loss, dim: int = 1, grad=None):
         torch = self._torch
+        self._check_points(coords)
         coords = coords.contiguous()
         if grad is None:
             grad = torch.zeros_like(coords)
+        elif (tuple(grad.shape) != tuple(coords.shape) or grad.dtype != torch.float32
+              or not grad.is_contiguous() or grad.device != coords.device):
+            raise PHError(-1, "grad must be a contiguous float32 tensor shaped like coords")
         g = grad_loss.contiguous().to(torch.float32)
+        if g.numel() != self.n_clouds or not g.is_cuda:
+            raise PHError(-1, f"grad_loss must hold one CUDA value per cloud ({self.n_clouds})")
         self._check(self.lib.ph_diagram_backward(self._h, _ptr(coords), coords.shape[1], dim,
                                                  _ptr(g), _ptr(grad)))
         return grad
@@ -291,10 +317,12 @@ class Context:
         dims = np.ascontiguousarray(dims, np.int32)
         colptr = np.ascontiguousarray(colptr, np.int64)
         rows = np.ascontiguousarray(rows, np.int32)
+        self._points = None
         self._check(self.lib.ph_load_boundary(self._h, len(dims), _ptr(dims), _ptr(colptr),
                                               _ptr(rows)))
         self.n_clouds = 1
         self.m = len(dims)
+        self.builds += 1
 
     def reduce(self, max_passes: int = -1) -> dict:
         st = PhStats()

@@ -5,8 +5,11 @@ generator drift from a kernel bug), the number of simplices per dimension, the p
 and essential simplices (as SHA-256 of canonical int64 arrays, plus counts per dimension), and
 the per-pass counters of the oracle's pass-by-pass Algorithm 2 (default rule: left-most source,
 Corollary 10 on). Pairs are checked against Algorithm 3 (twist) before anything is written.
+For the differentiable workload (diff256): per cloud, the pairs and essentials as above (from
+Algorithm 3 on the grid copy), the fp64 diagram loss over the H1 pairs and the max-abs and l1
+norms of its fp64 gradient.
 
-    python tests/golden/make_golden.py [circle40 torus400 gauss8_120 batch512]
+    python tests/golden/make_golden.py [circle40 torus400 gauss8_120 batch512 diff256]
 
 Takes minutes (torus400 alone: about 3 minutes on one core).
 """
@@ -90,6 +93,25 @@ def main(names):
                      all_sha=h.hexdigest(), passes=int(max(c["passes"] for c in clouds)),
                      pass_stats=agg.tolist(), clouds=clouds)
             g["offsets_sha"] = sha(off)
+        elif name == "diff256":
+            # the differentiable form: fp32 clouds, pairing from the grid copy, loss over the
+            # H1 pairs with fp64 Euclidean lengths of the realising edges
+            x, off = pc.diff256()
+            clouds = []
+            for c in range(len(off) - 1):
+                x64 = x[off[c]:off[c + 1]].astype(np.float64)
+                K = oracle.vr_build(pc.to_grid(x64), 2)
+                low, _ = oracle.reduce_twist(K)
+                pairs, ess = canonical(low, K["dim"])
+                edges = oracle.diagram_edges(K, low, 1)
+                loss, grad = oracle.diagram_loss_grad(x64, edges)
+                clouds.append(dict(m=int(K.m), n_pairs=int(len(pairs)), n_h1=int(len(edges)),
+                                   pairs_sha=sha(pairs), ess_sha=sha(ess), loss=float(loss),
+                                   grad_maxabs=float(np.abs(grad).max()),
+                                   grad_l1=float(np.abs(grad).sum())))
+            g = dict(m=int(sum(c["m"] for c in clouds)), n_clouds=len(clouds), dim=1,
+                     loss_total=float(sum(c["loss"] for c in clouds)), clouds=clouds,
+                     offsets_sha=sha(off))
         else:
             raise SystemExit(f"unknown workload {name}")
         g["coords_sha"] = sha(x)
@@ -100,4 +122,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["circle40", "torus400", "gauss8_120", "batch512"])
+    main(sys.argv[1:] or ["circle40", "torus400", "gauss8_120", "batch512", "diff256"])

@@ -80,3 +80,18 @@ def test_struct_layout_matches_binding(tmp_path, cname, pyname):
                                           text=True).stdout.split()]
     want = [ctypes.sizeof(py)] + [getattr(py, n).offset for n in names]
     assert got == want, (cname, list(zip(["sizeof"] + names, got, want)))
+
+
+def test_no_alloc_entry_point_source_allocates_nothing():
+    """ph_beta_static's translation unit calls no allocation routine: no cudaMalloc* /
+    cudaFree* (runtime or driver), no library context and none of its allocator hooks."""
+    src = (ROOT / "paper_1708_04710_gb300" / "csrc" / "ph_noalloc.cu").read_text()
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", src, flags=re.S))
+    banned = [r"\bcu(da)?Malloc\w*", r"\bcu(da)?Free\w*", r"\bcu(da)?MemAlloc\w*",
+              r"\bcuMemCreate\b", r"\bdalloc\b", r"\bdfree\b", r"\balloc_n\b", r"\bph_ctx\b",
+              r"\bnew\s+[A-Za-z_]", r"\bmalloc\s*\("]
+    for pat in banned:
+        assert not re.search(pat, code), f"ph_noalloc.cu matches {pat}"
+    # the scratch is a file-scope device array, and host code passes its looked-up address
+    assert re.search(r"__device__\s+__align__\(256\)\s+int32_t\s+g_left_scratch\[", code)
+    assert "cudaGetSymbolAddress" in code

@@ -1,11 +1,22 @@
 """Differentiable diagrams on the GPU against the FP64 oracle, through the C ABI.
 
 The pairing is integer work and must match exactly (same pairs, hence the same realising
-edges); losses and gradients are FP32 on the GPU and FP64 in the oracle, compared normwise at
-relative tolerance 1e-4: max |g_gpu - g_ref| <= 1e-4 * max |g_ref|. The oracle's gradient is
-itself pinned by FP64 central differences in test_oracle_pins.py.
+edges); losses and gradients are FP32 on the GPU and FP64 in the oracle, compared at relative
+tolerance 1e-4, normwise (max |g_gpu - g_ref| <= 1e-4 * max |g_ref|) and element by element:
+
+    |g_gpu - g_ref| <= 1e-4 * |g_ref| + 16 u * max |g_ref|   (per cloud, u = 2^-24).
+
+The second term is for components near zero, where a relative bound means nothing: each
+gradient component is an FP32 sum, in atomic (arbitrary) order, of about 125 pair terms whose
+magnitudes exceed the result, so its rounding error is a few units in the last place of the
+cloud's largest component (an FP32 emulation of the kernel's arithmetic, in random order,
+stays below 4.4 u * max |g_ref| on diff256), not a fraction of the component itself. The
+oracle's gradient is itself pinned by FP64 central differences in test_oracle_pins.py.
 """
+import hashlib
+import json
 import math
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -14,6 +25,15 @@ import pointclouds as pc
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-4
+ULP_FLOOR = 16 * 2.0 ** -24  # times the cloud's largest gradient component
+GOLDEN = Path(__file__).resolve().parent / "golden" / "diff256.json"
+
+
+def _elementwise_ok(got, ref):
+    """The element-wise rule of the module docstring; returns (ok, worst ratio to the bound)."""
+    bound = RTOL * np.abs(ref) + ULP_FLOOR * np.abs(ref).max()
+    ratio = float((np.abs(got - ref) / bound).max()) if ref.size else 0.0
+    return ratio <= 1.0, ratio
 
 
 @pytest.fixture(scope="module")
@@ -56,6 +76,7 @@ def test_single_cloud_loss_and_gradient(env, dim):
     assert abs(loss[0] - ref_loss) <= RTOL * abs(ref_loss)
     assert loss[1] == loss[0]
     assert np.abs(grad - ref_grad).max() <= RTOL * np.abs(ref_grad).max()
+    assert _elementwise_ok(grad, ref_grad)[0]
 
 
 def test_batched_autograd_matches_oracle(env):
@@ -76,32 +97,56 @@ def test_batched_autograd_matches_oracle(env):
         assert npairs == math.comb(64, 2) - 63  # complete 2-skeleton: every cycle dies
         assert abs(got_loss[c] - loss) <= RTOL * loss
         ref_grad[a:b] = w[c].item() * g
+        assert _elementwise_ok(got_grad[a:b], ref_grad[a:b])[0], c
     assert np.abs(got_grad - ref_grad).max() <= RTOL * np.abs(ref_grad).max()
 
 
-def test_full_diff256_properties_and_samples(env):
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def test_full_diff256_every_cloud(env):
+    """The full differentiable workload (256 clouds x 64 points, 11.2M simplices): every
+    cloud's pairs and essentials bit-exact against the oracle's stored SHA-256, every cloud's
+    loss against the stored FP64 loss, and every gradient component against the oracle's FP64
+    gradient (element-wise rule above), the oracle run live on all 256 clouds."""
     torch, ph, orc = env
+    g = json.loads(GOLDEN.read_text())
     x, off = pc.diff256()
+    assert _sha(off) == g["offsets_sha"] and _sha(x) == g["coords_sha"], "generator drift"
     xt = torch.from_numpy(x).cuda()
     ctx = ph.Context()
     ctx.build_filtration_f32(xt, off, 2)
-    assert ctx.m == 256 * (64 + math.comb(64, 2) + math.comb(64, 3))
+    assert ctx.m == 256 * (64 + math.comb(64, 2) + math.comb(64, 3)) == g["m"]
     assert ctx.reduce()["converged"]
     loss = ctx.diagram_loss(xt, 1)
     assert ctx.last_pairs == 256 * (math.comb(64, 2) - 63)
     grad = ctx.diagram_backward(xt, torch.ones(256, device="cuda"), 1).cpu().numpy()
     lc = loss.cpu().numpy()
-    assert abs(lc[-1] - lc[:-1].astype(np.float64).sum()) <= 1e-5 * lc[-1]
-    # translation invariance: every cloud's gradient sums to zero
+    assert abs(lc[-1] - g["loss_total"]) <= RTOL * g["loss_total"]
+    worst = 0.0
     for c in range(256):
-        gsum = grad[off[c]:off[c + 1]].sum(0)
-        assert np.abs(gsum).max() <= 1e-4 * np.abs(grad[off[c]:off[c + 1]]).max()
-    # sampled clouds against the oracle
-    for c in (0, 77, 255):
-        a, b = off[c], off[c + 1]
-        ref_loss, ref_grad, _ = _oracle(orc, x[a:b], 1)
-        assert abs(lc[c] - ref_loss) <= RTOL * ref_loss
-        assert np.abs(grad[a:b] - ref_grad).max() <= RTOL * np.abs(ref_grad).max()
+        gc = g["clouds"][c]
+        pr = ctx.pairs(c, on_device=False)
+        es = ctx.essential(c, on_device=False)
+        b, d = pr["birth"].numpy(), pr["death"].numpy()
+        o = np.lexsort((b, d))
+        pairs = np.stack([b[o], d[o]], 1).astype(np.int64)
+        assert _sha(pairs) == gc["pairs_sha"], f"cloud {c}: pairs differ from the oracle"
+        assert _sha(np.sort(es["idx"].numpy()).astype(np.int64)) == gc["ess_sha"], c
+        assert abs(lc[c] - gc["loss"]) <= RTOL * gc["loss"], c
+        a, e = off[c], off[c + 1]
+        ref_loss, ref_grad, n_h1 = _oracle(orc, x[a:e], 1)
+        # the live oracle is the one that wrote the golden values
+        assert n_h1 == gc["n_h1"] and abs(ref_loss - gc["loss"]) <= 1e-9 * gc["loss"], c
+        assert abs(np.abs(ref_grad).max() - gc["grad_maxabs"]) <= 1e-9 * gc["grad_maxabs"], c
+        ok, ratio = _elementwise_ok(grad[a:e], ref_grad)
+        worst = max(worst, ratio)
+        assert ok, f"cloud {c}: gradient off by {ratio:.2f} of the element-wise bound"
+        assert np.abs(grad[a:e] - ref_grad).max() <= RTOL * np.abs(ref_grad).max(), c
+        # translation invariance: each cloud's gradient sums to zero
+        assert np.abs(grad[a:e].sum(0)).max() <= 1e-4 * np.abs(grad[a:e]).max(), c
+    print(f"diff256: worst gradient error {worst:.3f} of the element-wise bound")
 
 
 def test_rejects_bad_input(env):

@@ -44,6 +44,29 @@ def _local_rows(K, d):
     return pos[rows].astype(np.int32), cols, pos
 
 
+def _pool_used(torch):
+    """Bytes in use in the device's default memory pool (what cudaMallocAsync draws from), or
+    None where the CUDA runtime library cannot be opened from Python."""
+    import ctypes.util
+
+    for name in ("libcudart.so", "libcudart.so.13", ctypes.util.find_library("cudart")):
+        try:
+            rt = ctypes.CDLL(name or "libcudart.so")
+            break
+        except OSError:
+            rt = None
+    if rt is None:
+        return None
+    pool = ctypes.c_void_p()
+    if rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) != 0:
+        return None
+    used = ctypes.c_uint64()
+    attr_used_mem_current = 7  # cudaMemPoolAttrUsedMemCurrent
+    if rt.cudaMemPoolGetAttribute(pool, attr_used_mem_current, ctypes.byref(used)) != 0:
+        return None
+    return used.value
+
+
 def test_beta_static_matches_allocating_path(env):
     torch, ph, oracle = env
     lib = ph.load_library()
@@ -56,12 +79,19 @@ def test_beta_static_matches_allocating_path(env):
     beta_orc = oracle.beta(K)
     assert np.array_equal(beta_ctx, beta_orc)
     stream = torch.cuda.current_stream()
+    inputs = {}
+    for d in (1, 2, 3):  # every buffer the calls use exists before the first call
+        rows, cols, pos = _local_rows(K, d)
+        inputs[d] = (rows, cols, pos, torch.from_numpy(rows).cuda(),
+                     torch.full((len(cols),), -7, dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    torch_allocs = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    pool0 = _pool_used(torch)
     # several calls in a row, large then small then large again: leftovers must not leak
     for d in (3, 1, 2, 3, 1):
-        rows, cols, pos = _local_rows(K, d)
+        rows, cols, pos, r_dev, out = inputs[d]
         n_rows = int((K["dim"] == d - 1).sum())
-        r_dev = torch.from_numpy(rows).cuda()
-        out = torch.full((len(cols),), -7, dtype=torch.int32, device="cuda")
+        out.fill_(-7)
         rc = lib.ph_beta_static(ctypes.c_void_p(r_dev.data_ptr()), len(cols), d + 1, n_rows,
                                 ctypes.c_void_p(out.data_ptr()),
                                 ctypes.c_void_p(stream.cuda_stream))
@@ -69,6 +99,12 @@ def test_beta_static_matches_allocating_path(env):
         got = out.cpu().numpy()
         expect = np.where(beta_ctx[cols] >= 0, pos[np.maximum(beta_ctx[cols], 0)], -1)
         assert np.array_equal(got, expect), d
+    # nothing was allocated on the device meanwhile: not through torch's allocator, and not
+    # from the default memory pool (the GPU is shared, so device-wide free memory says nothing)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == torch_allocs
+    if pool0 is not None:
+        assert _pool_used(torch) == pool0
 
 
 def test_beta_static_rejects_oversize_and_bad_rows(env):
