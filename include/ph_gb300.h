@@ -48,8 +48,10 @@ enum {
 typedef struct ph_ctx ph_ctx;
 
 /* Device memory provider. alloc returns device memory of at least `bytes` bytes usable on
- * `stream`, or NULL on failure; free releases it. Both are called from the thread that calls
- * the library. With a NULL provider the library uses cudaMallocAsync / cudaFreeAsync. */
+ * `stream`, aligned to 256 bytes (as cudaMalloc's is), or NULL on failure; free releases it.
+ * Both are called from the thread that calls the library. A misaligned block is given back and
+ * the call fails with PH_ERR_ALLOC. With a NULL provider the library uses cudaMallocAsync /
+ * cudaFreeAsync. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* user, void* stream);
   void (*free)(void* ptr, size_t bytes, void* user, void* stream);

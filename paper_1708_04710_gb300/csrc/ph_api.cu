@@ -22,6 +22,12 @@ void* ph_ctx::dalloc(size_t bytes) {
     err = "device allocation of " + std::to_string(bytes) + " bytes failed";
     throw ph::Fail{PH_ERR_ALLOC};
   }
+  if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {  // the kernels copy in 16-byte units
+    if (has_alloc) alloc.free(p, bytes, alloc.user, (void*)stream);
+    else cudaFreeAsync(p, stream);
+    err = "the device allocator returned memory that is not 256-byte aligned";
+    throw ph::Fail{PH_ERR_ALLOC};
+  }
   blocks.push_back({p, bytes});
   return p;
 }

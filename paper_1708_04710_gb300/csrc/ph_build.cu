@@ -512,7 +512,7 @@ void load_boundary(ph_ctx* ctx, int64_t m, const int32_t* dims, const int64_t* c
   ctx->low = alloc_n<int32_t>(ctx, m);
   ctx->gidx = alloc_n<int64_t>(ctx, m);
   ctx->verts = alloc_n<uint64_t>(ctx, m);
-  ctx->rows0 = alloc_n<int32_t>(ctx, std::max<int64_t>(nnz, 1));
+  ctx->rows0 = alloc_n<int32_t>(ctx, std::max<int64_t>(nnz, 1) + kColSlack);
   ctx->col_off = alloc_n<int64_t>(ctx, m + 1);
   ctx->d2tab = alloc_n<int64_t>(ctx, 1);
   ctx->n_d2 = 0;
@@ -662,7 +662,7 @@ void build_vr(ph_ctx* ctx, const int32_t* coords, const int64_t* cloud_offsets, 
   ctx->key = alloc_n<int32_t>(ctx, m_bound);
   ctx->low = alloc_n<int32_t>(ctx, m_bound);
   ctx->verts = alloc_n<uint64_t>(ctx, m_bound);
-  ctx->rows0 = alloc_n<int32_t>(ctx, nnz_bound);
+  ctx->rows0 = alloc_n<int32_t>(ctx, nnz_bound + kColSlack);
   IdOut o{ctx->seg, ctx->key, ctx->low, ctx->verts, ctx->rows0};
 
   k_vertex_init<<<grid_for(ctx, N, kThreads), kThreads, 0, st>>>(ct, N, o);

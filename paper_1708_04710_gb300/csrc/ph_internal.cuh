@@ -74,6 +74,12 @@ __device__ __forceinline__ bool in_essential_estimate(const ColMeta& mx, int32_t
   return !(mx.flags & F_PROVEN) && beta_x < 0 && owner_x < 0 && !mx.low_seen;
 }
 
+// Every buffer that holds columns (boundary matrix, arenas, pivot store) is allocated with this
+// many words past its capacity: the additions kernel stages a column by 16-byte copies that
+// round its start down and its end up to 16 bytes, so they may read up to 4 words past the last
+// column, and those words must lie inside the allocation.
+constexpr int64_t kColSlack = 8;
+
 struct ColStore {  // a device buffer that holds column storage (int32 rows)
   int32_t* p = nullptr;
   int64_t cap = 0;  // words

@@ -834,18 +834,28 @@ __device__ __forceinline__ int warp_symdiff(const int32_t* __restrict__ A, int n
   return out;
 }
 
-// Per-warp shared staging: the columns (A then B) of a batch of the warp's jobs, stored back
-// to back, and per-job bookkeeping. kStage rows per warp bound a staged merge.
-constexpr int kStage = 1024;
-struct WarpStage {
-  int32_t in[kStage];
-  int32_t* jout[32];    // output slot of the job (its reserved words in the next arena)
+// Per-warp shared staging of a batch of the warp's jobs, and per-job bookkeeping (indexed by
+// the job's ordinal among the warp's staged jobs). Each staged list (a job's column A, its source
+// B) has a span that starts on a 16-byte boundary: its first row lands at the span's start plus
+// the list's misalignment in global memory (0-3 words), so whole 16-byte chunks copy it, and the
+// word after its last row holds a sentinel (INT32_MAX), so a merge needs no bounds checks. A
+// batch fills at most kStage words; kStageSlack more absorb a merge's reads past the last
+// sentinel (at most KM + 1 words, KM <= 16).
+#ifndef PH_KSTAGE
+#define PH_KSTAGE 1024
+#endif
+constexpr int kStage = PH_KSTAGE;
+constexpr int kStageSlack = 32;
+struct __align__(16) WarpStage {
+  int32_t in[kStage + kStageSlack];
+  int32_t* jout[32];  // output slot of the job (its reserved words in the next arena)
+  int32_t ia[32];     // index in `in` of the job's first row of A (current batch)
+  int32_t ib[32];     // index in `in` of the job's first row of B
   int32_t na[32];
-  int32_t nin[32];      // rows staged for the job (na + nb), 0 if not staged
-  int32_t in_off[33];   // exclusive prefix of nin over the warp's lanes
-  int32_t pad_off[33];  // exclusive prefix of nin rounded up to km
-  int32_t jcnt[32];     // output rows of the job so far
-  int32_t jlow[32];     // largest output row (new low), -1 if none
+  int32_t nb[32];
+  int32_t pc[33];     // first merge piece of the job: exclusive prefix of pieces over the jobs
+  int32_t jcnt[32];   // output rows of the job so far
+  int32_t jlow[32];   // largest output row (new low), -1 if none
 };
 // Phase II blocks: 128 threads, so a block's barriers wait on 4 warps rather than 8
 constexpr int kAddThreads = 128;
@@ -982,136 +992,138 @@ __device__ __forceinline__ int64_t look_back(const RArgs& a, int32_t pass, int64
   return prefix;
 }
 
-// 4-byte asynchronous copy global -> shared (no register staging); completed by
-// cp_async_wait_all, which waits for all of this thread's copies.
-__device__ __forceinline__ void cp_async4(int32_t* smem_dst, const int32_t* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
+// waits for all of this thread's asynchronous copies (cp_async16)
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Branch-free merge of one lane's merge-path range A[x0..x1), B[y0..y1) (at most KM + 1 rows,
-// since a split moves an equal pair to one side) into registers: step t takes the smaller head,
-// ties from A first, so the two copies of a row common to both columns come out adjacent.
-template <int KM>
-__device__ __forceinline__ void lane_merge_regs(const int32_t* __restrict__ sA, int x0, int x1,
-                                                const int32_t* __restrict__ sB, int y0, int y1,
-                                                int32_t (&m)[KM + 1]) {
-  int i = x0, j = y0;
-  int32_t va = i < x1 ? sA[i] : INT32_MAX;
-  int32_t vb = j < y1 ? sB[j] : INT32_MAX;
-#pragma unroll
-  for (int t = 0; t <= KM; t++) {
-    const bool ta = va <= vb;
-    m[t] = ta ? va : vb;
-    if (t < KM) {
-      const int nx = ta ? i + 1 : j + 1;
-      const bool ok = ta ? nx < x1 : nx < y1;
-      const int32_t nv = ok ? (ta ? sA : sB)[nx] : INT32_MAX;
-      i = ta ? nx : i;
-      j = ta ? j : nx;
-      va = ta ? nv : va;
-      vb = ta ? vb : nv;
-    }
-  }
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned), cached in L2 only
+__device__ __forceinline__ void cp_async16(int32_t* smem_dst, const int32_t* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
 }
 
-// One batch of staged jobs (c..c_end) of a warp, merged by rounds: a lane takes one
-// km-position piece of the padded concatenation per round. Outputs go to the job's slot at the
-// job's running count plus the count of the job's earlier lanes in the round. KM > 0: the piece
-// is merged once into registers and the rows that are not one of an equal pair are written;
-// KM = 0 (a forced piece size without a register form): counted first, then merged again.
-#ifndef PH_STAGED_INLINE
-#define PH_STAGED_ATTR __noinline__
-#else
-#define PH_STAGED_ATTR __forceinline__
-#endif
+// merge-path split of the staged lists A = in[ia..ia+na), B = in[ib..ib+nb) on diagonal d, ties
+// taken from A first; an equal pair A[x-1] == B[y] is kept on the same side of the split, so that
+// cancellations never straddle two pieces
+__device__ __forceinline__ void split_staged(const int32_t* __restrict__ in, int ia, int na,
+                                             int ib, int nb, int d, int& x, int& y) {
+  int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (in[ia + mid] <= in[ib + d - 1 - mid]) lo = mid + 1; else hi = mid;
+  }
+  x = lo;
+  y = d - lo;
+  if (x > 0 && y < nb && in[ia + x - 1] == in[ib + y]) y++;
+}
+
+// Merge rounds over the pieces [P0, P1) of one batch: a job of N staged rows is cut into
+// ceil(N / KM) pieces of KM merge-path positions, and in each round lane l takes piece h0 + l.
+// A piece's job is found from a bitmask of the pieces that start a job (each lane of the batch
+// owns one job, with its first piece p_first); its end split comes from a binary search, its
+// start split from the previous lane (or the previous round). KM > 0: the piece is merged once,
+// branch-free, into registers (the sentinels end each list), rows that are not one of an equal
+// pair are kept, and kept rows go to the job's slot after the kept rows of its earlier pieces.
+// KM = 0 (a forced piece size km without a register form): counted first, then merged again.
 template <int KM>
-__device__ PH_STAGED_ATTR void staged_rounds(WarpStage& S, int c, int c_end, int p0, int nch,
-                                              int km) {
+__device__ __forceinline__ void staged_rounds(WarpStage& S, int P0, int P1, int o0, bool in_batch,
+                                              int p_first, int km) {
   const int lane = lane_id();
-  const int in_c = S.in_off[c];
-  int cx = 0, cy = 0;  // the end split of the previous round's last piece
-  for (int h0 = 0; h0 < nch; h0 += 32) {
+  const int32_t* __restrict__ in = S.in;
+  int cx = 0, cy = 0;    // end split of the previous round's last piece
+  int kprev = o0 - 1;    // job of the piece before the round
+  for (int h0 = P0; h0 < P1; h0 += 32) {
+    const unsigned start_bit =
+        in_batch && p_first >= h0 && p_first < h0 + 32 ? 1u << (p_first - h0) : 0u;
+    const unsigned heads = __reduce_or_sync(0xffffffffu, start_bit);
     const int h = h0 + lane;
-    int cnt = 0, k = -1, x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-    const int32_t* sA = S.in;
-    const int32_t* sB = S.in;
-    int32_t m[KM + 1];
-    uint32_t keep = 0;
-    int d = 0, nk = 0, ka = 0;
-    if (h < nch) {  // every piece starts inside its job: d < nk
-      const int gp = p0 + h * km;
-      int lo = c, hi = c_end - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (S.pad_off[mid] <= gp) lo = mid; else hi = mid - 1;
-      }
-      k = lo;
-      d = gp - S.pad_off[k];
-      nk = S.nin[k];
-      ka = S.na[k];
-      sA = S.in + (S.in_off[k] - in_c);
-      sB = sA + ka;
-      // each lane finds where its piece ends; a piece starts where the previous one ends
-      if (d + km >= nk) {
-        x1 = ka;
-        y1 = nk - ka;
+    const bool valid = h < P1;
+    const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
+    const int o = kprev + __popc(heads & upto);        // this piece's job
+    kprev = __shfl_sync(0xffffffffu, o, 31);
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0, d0 = 0, ia = 0, ib = 0, na = 0, nb = 0;
+    if (valid) {
+      na = S.na[o];
+      nb = S.nb[o];
+      ia = S.ia[o];
+      ib = S.ib[o];
+      d0 = (h - S.pc[o]) * km;
+      const int n = na + nb;
+      const int d1 = d0 + km < n ? d0 + km : n;
+      if (d1 == n) {
+        x1 = na;
+        y1 = nb;
       } else {
-        merge_split(sA, ka, sB, nk - ka, d + km, x1, y1);
+        split_staged(in, ia, na, ib, nb, d1, x1, y1);
       }
     }
     const int px = __shfl_up_sync(0xffffffffu, x1, 1);
     const int py = __shfl_up_sync(0xffffffffu, y1, 1);
-    if (k >= 0 && d > 0) {  // not a job's first piece: the previous piece is the same job's
+    if (valid && d0 > 0) {  // not a job's first piece: the previous piece is the same job's
       x0 = lane > 0 ? px : cx;
       y0 = lane > 0 ? py : cy;
     }
     cx = __shfl_sync(0xffffffffu, x1, 31);
     cy = __shfl_sync(0xffffffffu, y1, 31);
-    if (k >= 0) {
-      if constexpr (KM > 0) {
-        lane_merge_regs<KM>(sA, x0, x1, sB, y0, y1, m);
+    const int cnt = valid ? (x1 - x0) + (y1 - y0) : 0;
+    unsigned keep = 0;
+    int32_t m[KM > 0 ? KM + 1 : 1];
+    int kept = 0;
+    if constexpr (KM > 0) {
+      if (valid) {
+        int i = ia + x0, j = ib + y0;
+        int32_t va = in[i], vb = in[j];
 #pragma unroll
         for (int t = 0; t <= KM; t++) {
-          const bool dup = (t > 0 && m[t - 1] == m[t]) || (t < KM && m[t + 1] == m[t]);
-          if (m[t] != INT32_MAX && !dup) keep |= 1u << t;
-        }
-        cnt = __popc(keep);
-      } else {
-        cnt = lane_symdiff<false>(sA, x0, x1, sB, y0, y1, nullptr, nullptr);
-      }
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, k);
-    const int first_peer = __ffs(peers) - 1, last_peer = 31 - __clz(peers);
-    const int incl = warp_incl_sum(cnt);
-    const int seg_ex = (incl - cnt) - __shfl_sync(0xffffffffu, incl - cnt, first_peer);
-    const int seg_tot = __shfl_sync(0xffffffffu, incl, last_peer) -
-                        __shfl_sync(0xffffffffu, incl - cnt, first_peer);
-    const int base = k >= 0 ? S.jcnt[k] : 0;
-    __syncwarp();
-    if (k >= 0) {
-      if (cnt) {
-        int32_t* dst = S.jout[k] + base + seg_ex;
-        int32_t lastv = -1;
-        if constexpr (KM > 0) {
-          int q = 0;
-#pragma unroll
-          for (int t = 0; t <= KM; t++) {
-            if (keep & (1u << t)) {
-              dst[q++] = m[t];
-              lastv = m[t];
-            }
+          const bool ta = va <= vb;
+          m[t] = ta ? va : vb;
+          if (t < KM) {
+            i += ta ? 1 : 0;
+            j += ta ? 0 : 1;
+            const int32_t nv = in[ta ? i : j];
+            va = ta ? nv : va;
+            vb = ta ? vb : nv;
           }
-        } else {
-          lane_symdiff<true>(sA, x0, x1, sB, y0, y1, dst, &lastv);
         }
-        atomicMax(&S.jlow[k], lastv);
+#pragma unroll
+        for (int t = 0; t <= KM; t++) {
+          const bool dup = (t > 0 && m[t - 1] == m[t]) || (t < KM && t + 1 < cnt && m[t + 1] == m[t]);
+          if (t < cnt && !dup) keep |= 1u << t;
+        }
+        kept = __popc(keep);
       }
-      if (lane == last_peer) S.jcnt[k] = base + seg_tot;
+    } else {
+      if (valid) kept = lane_symdiff<false>(in + ia, x0, x1, in + ib, y0, y1, nullptr, nullptr);
     }
+    // this piece's place among the kept rows of its job: a scan over the round, restarted at the
+    // pieces that start a job (and at lane 0, which continues the previous round's job)
+    const unsigned run_heads = __ballot_sync(0xffffffffu, valid && (d0 == 0 || lane == 0));
+    const int incl = warp_incl_sum(kept);
+    const int rs = 31 - __clz(run_heads & upto);
+    const int run_base = __shfl_sync(0xffffffffu, incl - kept, rs);
+    const int jc = valid ? S.jcnt[o] : 0;
+    const bool run_last =
+        valid && (lane == 31 || ((run_heads >> (lane + 1)) & 1u) || h + 1 >= P1);
+    __syncwarp();  // every lane has read its job's count before the run's last lane moves it
+    if (kept) {
+      int32_t* dst = S.jout[o] + jc + (incl - kept - run_base);
+      int32_t lastv = -1;
+      if constexpr (KM > 0) {
+        int q = 0;
+#pragma unroll
+        for (int t = 0; t <= KM; t++) {
+          if (keep & (1u << t)) {
+            dst[q++] = m[t];
+            lastv = m[t];
+          }
+        }
+      } else {
+        lane_symdiff<true>(in + ia, x0, x1, in + ib, y0, y1, dst, &lastv);
+      }
+      atomicMax(&S.jlow[o], lastv);
+    }
+    if (run_last) S.jcnt[o] = jc + (incl - run_base);
     __syncwarp();
   }
 }
@@ -1254,75 +1266,92 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   }
   const unsigned smask = __ballot_sync(0xffffffffu, cls == 3);
   if (smask) {
-    // longer merges: staged in shared memory, merge path over the concatenated jobs
-    const bool big = cls == 3 && N > a.staged_max;
-    const int nin = (cls == 3 && !big) ? N : 0;
-    const int in_ex = warp_incl_sum(nin) - nin;
-    const int small_total = __shfl_sync(0xffffffffu, in_ex + nin, 31);
-    const int n_staged = __popc(__ballot_sync(0xffffffffu, nin > 0));
-    const int mean = n_staged ? small_total / n_staged : 0;
+    // longer merges: staged in shared memory, merge path over the concatenated jobs. Each list
+    // takes a 16-byte aligned span (its misalignment, its rows, a sentinel, rounded up to 4 words)
+    const int ra = (int)(((uintptr_t)A >> 2) & 3u);
+    const int rb = B ? (int)(((uintptr_t)B >> 2) & 3u) : 0;
+    const int span_a = (ra + na + 1 + 3) & ~3;
+    const int span_b = (rb + nb + 1 + 3) & ~3;
+    const bool staged = cls == 3 && N <= a.staged_max && span_a + span_b <= kStage;
+    const bool big = cls == 3 && !staged;
+    const unsigned stmask = __ballot_sync(0xffffffffu, staged);
+    const int ord = __popc(stmask & ((1u << lane) - 1u));  // ordinal among the staged jobs
+    const int words = staged ? span_a + span_b : 0;
+    const int w_ex = warp_incl_sum(words) - words;
+    const int n_staged = __popc(stmask);
+    const int mean = n_staged ? __reduce_add_sync(0xffffffffu, staged ? (unsigned)N : 0u) / n_staged
+                              : 0;
     const int km = a.force_km > 0 ? a.force_km
                                   : (mean >= 80 ? 16 : (mean >= 32 ? 8 : 4));
-    const int npad = (nin + km - 1) / km * km;
-    const int pad_ex = warp_incl_sum(npad) - npad;
-    S.jout[lane] = slot;
-    S.na[lane] = na;
-    S.nin[lane] = nin;
-    S.in_off[lane] = in_ex;
-    S.pad_off[lane] = pad_ex;
-    S.jcnt[lane] = 0;
-    S.jlow[lane] = -1;
-    if (lane == 31) {
-      S.in_off[32] = in_ex + nin;
-      S.pad_off[32] = pad_ex + npad;
+    const int npc = staged ? (N + km - 1) / km : 0;  // merge pieces of the job
+    const int p_first = warp_incl_sum(npc) - npc;
+    if (staged) {
+      S.jout[ord] = slot;
+      S.na[ord] = na;
+      S.nb[ord] = nb;
+      S.pc[ord] = p_first;
+      S.jcnt[ord] = 0;
+      S.jlow[ord] = -1;
     }
     __syncwarp();
-    int c = 0;
-    while (c < 32) {
-      // batch: jobs c.. whose staged rows fit together
-      const int in_c = S.in_off[c];
-      const bool fits = lane >= c && S.in_off[lane] + S.nin[lane] - in_c <= kStage;
-      const int c_end = c + __popc(__ballot_sync(0xffffffffu, fits));
-      const int nch = (S.pad_off[c_end] - S.pad_off[c]) / km;
-      const bool mine = lane >= c && lane < c_end && nin > 0;
-      if (__ballot_sync(0xffffffffu, mine)) {
-        // stage: columns of 32+ rows by the whole warp (coalesced), shorter ones by their lane;
-        // asynchronous copies, so the loads of all of the batch's jobs are in flight together
-        unsigned lmask = __ballot_sync(0xffffffffu, mine && nin >= 32);
-        while (lmask) {
-          const int src = __ffs(lmask) - 1;
-          lmask &= lmask - 1;
-          const int32_t* wA = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)A, src);
-          const int32_t* wB = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)B, src);
-          const int wna = __shfl_sync(0xffffffffu, na, src);
-          const int wn = __shfl_sync(0xffffffffu, nin, src);
-          int32_t* d = S.in + (__shfl_sync(0xffffffffu, in_ex, src) - in_c);
-          for (int q = lane; q < wn; q += 32) cp_async4(d + q, q < wna ? wA + q : wB + (q - wna));
-        }
-        if (mine && nin < 32) {
-          int32_t* d = S.in + (in_ex - in_c);
-          for (int q = 0; q < na; q++) cp_async4(d + q, A + q);
-          for (int r = 0; r < nb; r++) cp_async4(d + na + r, B + r);
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        const int p0 = S.pad_off[c];
-        switch (km) {
-          case 4: staged_rounds<4>(S, c, c_end, p0, nch, km); break;
-          case 8: staged_rounds<8>(S, c, c_end, p0, nch, km); break;
-          case 16: staged_rounds<16>(S, c, c_end, p0, nch, km); break;
-          default: staged_rounds<0>(S, c, c_end, p0, nch, km); break;
-        }
+    unsigned rest = stmask;
+    while (rest) {
+      // batch: the staged jobs from lane c on whose spans fit together
+      const int c = __ffs(rest) - 1;
+      const int w0 = __shfl_sync(0xffffffffu, w_ex, c);
+      const bool mine = staged && lane >= c && w_ex + words - w0 <= kStage;
+      const unsigned bmask = __ballot_sync(0xffffffffu, mine);
+      rest &= ~bmask;
+      const int o0 = __popc(stmask & ((1u << c) - 1u));
+      const int base = w_ex - w0;  // this job's spans in `in`
+      if (mine) {
+        S.ia[ord] = base + ra;
+        S.ib[ord] = base + span_a + rb;
+      }
+      // stage: 16-byte chunks from the lists' aligned starts (the column stores carry slack
+      // after their last column for the rounding); jobs of 16+ chunks by the whole warp,
+      // shorter ones by their lane; all copies of the batch are in flight together
+      const int ch_a = span_a >> 2;
+      const int ch_n = ch_a + (B ? span_b >> 2 : 0);
+      const int32_t* ga = A - ra;
+      const int32_t* gb = B ? B - rb : nullptr;
+      unsigned lmask = __ballot_sync(0xffffffffu, mine && ch_n >= 16);
+      while (lmask) {
+        const int src = __ffs(lmask) - 1;
+        lmask &= lmask - 1;
+        const int32_t* wa = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)ga, src);
+        const int32_t* wb = (const int32_t*)__shfl_sync(0xffffffffu, (unsigned long long)gb, src);
+        const int wca = __shfl_sync(0xffffffffu, ch_a, src);
+        const int wcn = __shfl_sync(0xffffffffu, ch_n, src);
+        int32_t* d = S.in + __shfl_sync(0xffffffffu, base, src);
+        for (int q = lane; q < wcn; q += 32)
+          cp_async16(d + 4 * q, q < wca ? wa + 4 * q : wb + 4 * (q - wca));
+      }
+      if (mine && ch_n < 16) {
+        int32_t* d = S.in + base;
+        for (int q = 0; q < ch_n; q++) cp_async16(d + 4 * q, q < ch_a ? ga + 4 * q : gb + 4 * (q - ch_a));
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      if (mine) {  // the sentinels go after the copies, which may have covered their words
+        S.in[base + ra + na] = INT32_MAX;
+        S.in[base + span_a + rb + nb] = INT32_MAX;
       }
       __syncwarp();
-      c = c_end;
+      const int P0 = __shfl_sync(0xffffffffu, p_first, c);
+      const int P1 = P0 + (int)__reduce_add_sync(0xffffffffu, mine ? (unsigned)npc : 0u);
+      switch (km) {
+        case 4: staged_rounds<4>(S, P0, P1, o0, mine, p_first, km); break;
+        case 8: staged_rounds<8>(S, P0, P1, o0, mine, p_first, km); break;
+        case 16: staged_rounds<16>(S, P0, P1, o0, mine, p_first, km); break;
+        default: staged_rounds<0>(S, P0, P1, o0, mine, p_first, km); break;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    if (cls == 3 && !big) {
-      const int len = S.jcnt[lane];
+    if (staged) {
       o_ptr = slot;
-      o_len = len;
-      if (B) a.low[jb.j] = S.jlow[lane];
+      o_len = S.jcnt[ord];
+      if (B) a.low[jb.j] = S.jlow[ord];
     }
     // merges too long to stage: straight from global memory into their slot
     unsigned bmask = __ballot_sync(0xffffffffu, big);
@@ -1762,7 +1791,7 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
 static void grow_store(ph_ctx* ctx, ColStore& s, int64_t need_words) {
   if (need_words <= s.cap) return;
   const int64_t cap = std::max<int64_t>(need_words + need_words / 4, 1 << 20);
-  int32_t* p = alloc_n<int32_t>(ctx, cap);
+  int32_t* p = alloc_n<int32_t>(ctx, cap + kColSlack);
   if (s.p) ctx->dfree(s.p);
   s.p = p;
   s.cap = cap;

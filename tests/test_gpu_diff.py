@@ -160,3 +160,56 @@ def test_rejects_bad_input(env):
     ctx.reduce()
     with pytest.raises(ph.PHError):  # a loaded complex has no coordinates
         ctx.diagram_loss(torch.zeros((2, 2), device="cuda"), 0)
+
+
+def test_diagram_calls_reject_wrong_shapes_before_any_launch(env):
+    """The diagram kernels index the coordinates by the build's point rows, so a wrong D or a
+    coordinate array of another shape must be refused before anything is launched."""
+    import ctypes
+
+    torch, ph, _ = env
+    x, off = pc.diff256(n_clouds=2)
+    xt = torch.from_numpy(x).cuda()
+    ctx = ph.Context()
+    ctx.build_filtration_f32(xt, off, 2)
+    assert ctx.reduce()["converged"]
+    lib = ph.load_library()
+    loss = torch.zeros(3, device="cuda")
+    grad = torch.zeros_like(xt)
+    gl = torch.ones(2, device="cuda")
+    n = ctypes.c_int64(0)
+    before = ctx.kernel_launches()
+    rc = lib.ph_diagram_loss(ctx._h, ctypes.c_void_p(xt.data_ptr()), 2, 1,
+                             ctypes.c_void_p(loss.data_ptr()), ctypes.byref(n))
+    assert rc == -1 and b"D must equal" in lib.ph_last_error(ctx._h)  # PH_ERR_INVALID
+    rc = lib.ph_diagram_backward(ctx._h, ctypes.c_void_p(xt.data_ptr()), 4, 1,
+                                 ctypes.c_void_p(gl.data_ptr()), ctypes.c_void_p(grad.data_ptr()))
+    assert rc == -1
+    assert ctx.kernel_launches() == before
+    # the binding checks the whole shape (it knows N): fewer points, or another D
+    for bad in (xt[:-1], xt[:, :2], xt.double()):
+        with pytest.raises(ph.PHError):
+            ctx.diagram_loss(bad, 1)
+        with pytest.raises(ph.PHError):
+            ctx.diagram_backward(bad, gl, 1)
+    with pytest.raises(ph.PHError):  # one upstream value per cloud
+        ctx.diagram_backward(xt, torch.ones(3, device="cuda"), 1)
+    assert ctx.kernel_launches() == before
+    assert torch.isfinite(ctx.diagram_loss(xt, 1)).all()
+
+
+def test_autograd_refuses_a_rebuilt_context(env):
+    """Two losses on one context: the first loss's backward would scatter through the second
+    filtration's pairing, so it raises instead."""
+    torch, ph, _ = env
+    from paper_1708_04710_gb300.diff import diagram_loss
+
+    x, off = pc.diff256(n_clouds=2)
+    shared = ph.Context()
+    xa = torch.from_numpy(x).cuda().requires_grad_(True)
+    xb = (torch.from_numpy(x).cuda() * 1.01).requires_grad_(True)
+    la = diagram_loss(xa, off, 1, shared).sum()
+    lb = diagram_loss(xb, off, 1, shared).sum()
+    lb.backward()  # the context's current filtration: fine
+    with pytest.raises(RuntimeError, match="rebuilt"):
+        la.backward()
