@@ -27,7 +27,7 @@ from .native import Context
 
 KNOBS = {
     "staged_merge_max": (1024, 512, 256),
-    "merge_items": (0, 4, 8, 16),
+    "merge_items": (0, 8, 16),
     "add_blocks_per_sm": (4, 3, 2),
     "dense_threshold": (0, -1, 128, 1024),
     "warp_chunks_below": (0, -1, 1 << 20, 1 << 24),
@@ -98,8 +98,10 @@ def tune(coords, offsets=None, max_dim: int = 2, max_diam2: int = -1, use_cache:
             cache = json.loads(path.read_text())
         except Exception:
             cache = {}
-        if key in cache:
-            return dict(cache[key]["options"])
+        # an entry tuned over other knob values (an older library) is tuned again
+        opts = cache.get(key, {}).get("options")
+        if opts and all(opts.get(k) in vals for k, vals in KNOBS.items()):
+            return dict(opts)
     best, best_t, trials = coordinate_descent(
         lambda o: _time_reduce(torch, coords, offsets, max_dim, max_diam2, o), KNOBS, DEFAULTS,
         verbose)

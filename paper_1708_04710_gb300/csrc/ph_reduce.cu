@@ -841,10 +841,7 @@ __device__ __forceinline__ int warp_symdiff(const int32_t* __restrict__ A, int n
 // word after its last row holds a sentinel (INT32_MAX), so a merge needs no bounds checks. A
 // batch fills at most kStage words; kStageSlack more absorb a merge's reads past the last
 // sentinel (at most KM + 1 words, KM <= 16).
-#ifndef PH_KSTAGE
-#define PH_KSTAGE 1024
-#endif
-constexpr int kStage = PH_KSTAGE;
+constexpr int kStage = 1024;
 constexpr int kStageSlack = 32;
 struct __align__(16) WarpStage {
   int32_t in[kStage + kStageSlack];
@@ -1019,18 +1016,21 @@ __device__ __forceinline__ void split_staged(const int32_t* __restrict__ in, int
 }
 
 // Merge rounds over the pieces [P0, P1) of one batch: a job of N staged rows is cut into
-// ceil(N / KM) pieces of KM merge-path positions, and in each round lane l takes piece h0 + l.
+// ceil(N / km) pieces of km merge-path positions, and in each round lane l takes piece h0 + l.
 // A piece's job is found from a bitmask of the pieces that start a job (each lane of the batch
 // owns one job, with its first piece p_first); its end split comes from a binary search, its
-// start split from the previous lane (or the previous round). KM > 0: the piece is merged once,
-// branch-free, into registers (the sentinels end each list), rows that are not one of an equal
-// pair are kept, and kept rows go to the job's slot after the kept rows of its earlier pieces.
-// KM = 0 (a forced piece size km without a register form): counted first, then merged again.
+// start split from the previous lane (or the previous round). A piece holds at most km + 1 rows
+// (a split moves an equal pair to one side). KM > 0 (km = KM): a branch-free merge into
+// registers, one shared load per row, the sentinels ending each list; the two copies of a row
+// common to both columns come out adjacent and cancel. KM = 0 (any other km): merged
+// sequentially, counted first and then merged again to write. Kept rows go to the job's slot
+// after the kept rows of its earlier pieces.
 template <int KM>
-__device__ __forceinline__ void staged_rounds(WarpStage& S, int P0, int P1, int o0, bool in_batch,
+__device__ __forceinline__ void staged_rounds(WarpStage& S_, int P0, int P1, int o0, bool in_batch,
                                               int p_first, int km) {
+  constexpr int S = KM > 0 ? KM + 1 : 0;  // register slots: the most rows a piece holds
   const int lane = lane_id();
-  const int32_t* __restrict__ in = S.in;
+  const int32_t* __restrict__ in = S_.in;
   int cx = 0, cy = 0;    // end split of the previous round's last piece
   int kprev = o0 - 1;    // job of the piece before the round
   for (int h0 = P0; h0 < P1; h0 += 32) {
@@ -1044,11 +1044,11 @@ __device__ __forceinline__ void staged_rounds(WarpStage& S, int P0, int P1, int 
     kprev = __shfl_sync(0xffffffffu, o, 31);
     int x0 = 0, y0 = 0, x1 = 0, y1 = 0, d0 = 0, ia = 0, ib = 0, na = 0, nb = 0;
     if (valid) {
-      na = S.na[o];
-      nb = S.nb[o];
-      ia = S.ia[o];
-      ib = S.ib[o];
-      d0 = (h - S.pc[o]) * km;
+      na = S_.na[o];
+      nb = S_.nb[o];
+      ia = S_.ia[o];
+      ib = S_.ib[o];
+      d0 = (h - S_.pc[o]) * km;
       const int n = na + nb;
       const int d1 = d0 + km < n ? d0 + km : n;
       if (d1 == n) {
@@ -1068,17 +1068,17 @@ __device__ __forceinline__ void staged_rounds(WarpStage& S, int P0, int P1, int 
     cy = __shfl_sync(0xffffffffu, y1, 31);
     const int cnt = valid ? (x1 - x0) + (y1 - y0) : 0;
     unsigned keep = 0;
-    int32_t m[KM > 0 ? KM + 1 : 1];
+    int32_t c[S > 0 ? S : 1];
     int kept = 0;
-    if constexpr (KM > 0) {
-      if (valid) {
+    if constexpr (S > 0) {
+      if (valid) {  // branch-free sequential merge; the sentinels end each list
         int i = ia + x0, j = ib + y0;
         int32_t va = in[i], vb = in[j];
 #pragma unroll
-        for (int t = 0; t <= KM; t++) {
+        for (int t = 0; t < S; t++) {
           const bool ta = va <= vb;
-          m[t] = ta ? va : vb;
-          if (t < KM) {
+          c[t] = ta ? va : vb;
+          if (t + 1 < S) {
             i += ta ? 1 : 0;
             j += ta ? 0 : 1;
             const int32_t nv = in[ta ? i : j];
@@ -1087,8 +1087,8 @@ __device__ __forceinline__ void staged_rounds(WarpStage& S, int P0, int P1, int 
           }
         }
 #pragma unroll
-        for (int t = 0; t <= KM; t++) {
-          const bool dup = (t > 0 && m[t - 1] == m[t]) || (t < KM && t + 1 < cnt && m[t + 1] == m[t]);
+        for (int t = 0; t < S; t++) {
+          const bool dup = (t > 0 && c[t - 1] == c[t]) || (t + 1 < cnt && c[t + 1] == c[t]);
           if (t < cnt && !dup) keep |= 1u << t;
         }
         kept = __popc(keep);
@@ -1102,28 +1102,28 @@ __device__ __forceinline__ void staged_rounds(WarpStage& S, int P0, int P1, int 
     const int incl = warp_incl_sum(kept);
     const int rs = 31 - __clz(run_heads & upto);
     const int run_base = __shfl_sync(0xffffffffu, incl - kept, rs);
-    const int jc = valid ? S.jcnt[o] : 0;
+    const int jc = valid ? S_.jcnt[o] : 0;
     const bool run_last =
         valid && (lane == 31 || ((run_heads >> (lane + 1)) & 1u) || h + 1 >= P1);
     __syncwarp();  // every lane has read its job's count before the run's last lane moves it
     if (kept) {
-      int32_t* dst = S.jout[o] + jc + (incl - kept - run_base);
+      int32_t* dst = S_.jout[o] + jc + (incl - kept - run_base);
       int32_t lastv = -1;
-      if constexpr (KM > 0) {
+      if constexpr (S > 0) {
         int q = 0;
 #pragma unroll
-        for (int t = 0; t <= KM; t++) {
+        for (int t = 0; t < S; t++) {
           if (keep & (1u << t)) {
-            dst[q++] = m[t];
-            lastv = m[t];
+            dst[q++] = c[t];
+            lastv = c[t];
           }
         }
       } else {
         lane_symdiff<true>(in + ia, x0, x1, in + ib, y0, y1, dst, &lastv);
       }
-      atomicMax(&S.jlow[o], lastv);
+      atomicMax(&S_.jlow[o], lastv);
     }
-    if (run_last) S.jcnt[o] = jc + (incl - run_base);
+    if (run_last) S_.jcnt[o] = jc + (incl - run_base);
     __syncwarp();
   }
 }
@@ -1281,8 +1281,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     const int n_staged = __popc(stmask);
     const int mean = n_staged ? __reduce_add_sync(0xffffffffu, staged ? (unsigned)N : 0u) / n_staged
                               : 0;
-    const int km = a.force_km > 0 ? a.force_km
-                                  : (mean >= 80 ? 16 : (mean >= 32 ? 8 : 4));
+    const int km = a.force_km > 0 ? a.force_km : (mean >= 80 ? 16 : 8);
     const int npc = staged ? (N + km - 1) / km : 0;  // merge pieces of the job
     const int p_first = warp_incl_sum(npc) - npc;
     if (staged) {
@@ -1341,7 +1340,6 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       const int P0 = __shfl_sync(0xffffffffu, p_first, c);
       const int P1 = P0 + (int)__reduce_add_sync(0xffffffffu, mine ? (unsigned)npc : 0u);
       switch (km) {
-        case 4: staged_rounds<4>(S, P0, P1, o0, mine, p_first, km); break;
         case 8: staged_rounds<8>(S, P0, P1, o0, mine, p_first, km); break;
         case 16: staged_rounds<16>(S, P0, P1, o0, mine, p_first, km); break;
         default: staged_rounds<0>(S, P0, P1, o0, mine, p_first, km); break;
@@ -1473,11 +1471,8 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
 // kDense: the pass may meet bit-packed columns or convert some; the row-list variant carries none
 // of it. kWarp: chunks of 32 slots claimed by single warps. The host picks the variant from
 // DevState::dense_on and warp_on (a separate graph for each).
-#ifndef PH_ADD_MIN_BLOCKS
-#define PH_ADD_MIN_BLOCKS 8
-#endif
 template <bool kDense, bool kWarp>
-__global__ void __launch_bounds__(kAddThreads, PH_ADD_MIN_BLOCKS) k_add(RArgs a) {
+__global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   __shared__ int64_t sh[kAddWarps + 1];
   __shared__ int64_t s_chunk;
   __shared__ int64_t s_prefix[2];
