@@ -67,9 +67,12 @@ typedef struct {
   /* 1 (default): zero case of Corollary 10 -- a column with beta_j = 0 whose candidate rows
    * (all rows of K_{d-1} up to low(j)) are all known to be paired is set to zero. */
   int32_t use_cor10;
-  /* reserved: the per-column kernels run 256-thread blocks (a compile-time constant of their
-   * scans); the value is ignored */
-  int32_t block_threads;
+  /* Phase II starts by merging each job in its own lane (sequentially, from shared memory),
+   * which suits short columns, and switches once, for the rest of the reduction, to merge
+   * pieces spread over the lanes when the mean job (target + source rows reserved per
+   * surviving column) reaches this many rows; 0 = library default (24), -1 = pieces from the
+   * first pass */
+  int32_t lane_merge_words;
   /* Phase II merges of more rows than this (target + source) run from global memory; shorter
    * ones are staged in shared memory first (0 = library default = the largest staged size,
    * 1024) */

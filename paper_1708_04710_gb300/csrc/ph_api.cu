@@ -279,7 +279,7 @@ void ph_default_opts(ph_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->strict_phase2 = 0;
   o->use_cor10 = 1;
-  o->block_threads = 256;
+  o->lane_merge_words = 0;
   o->staged_merge_max = 0;
   o->merge_items = 0;
   o->collect_stats = 0;

@@ -24,8 +24,10 @@
 //                the other arena by one atomic per chunk; new pivots move to the pivot store
 //                (their columns never change again). Blocks of 128 threads take 128-slot chunks
 //                from a device work queue, or each warp 32 slots once the list is short and
-//                its jobs long. Four specialisations (row lists / bitmaps x block / warp
-//                chunks); the loop switches between them at most twice per reduction.
+//                its jobs long. While jobs are short each lane merges its own job; later the
+//                lanes share every job's merge-path pieces. Eight specialisations (row lists /
+//                bitmaps x block / warp chunks x lane / piece merges); the loop switches
+//                between them at most three times per reduction.
 //   (p sets)     With Phase II limited to p neighbour sets (Sec. 3.4), k_set_* rank the sets
 //                between k_mark and k_add and hold back the other targets.
 //   k_commit     publishes the new locations of the columns other jobs may have been reading;
@@ -87,6 +89,11 @@ struct DevState {
   int32_t warp_on;
   int64_t warp_below;
   int64_t warp_words;  // the mean arena words per survivor the switch needs
+  // Phase II merges each job in its own lane while jobs are short (lane_on), and merge pieces
+  // spread over the lanes once the mean arena words per survivor reach lane_words; this
+  // switches once per reduction (ST_SWITCH)
+  int32_t lane_on;
+  int64_t lane_words;
 };
 
 struct RArgs {
@@ -1128,6 +1135,43 @@ __device__ __forceinline__ void staged_rounds(WarpStage& S_, int P0, int P1, int
   }
 }
 
+// One job merged by its own lane, sequentially from the staged lists (the sentinels end each
+// list), straight into its slot: a row equal to the one before it cancels that one, so the two
+// copies of a row common to both columns never reach the slot. Returns the output length; the
+// last row written (the new low) goes to *last, -1 if none.
+__device__ __forceinline__ int lane_merge_job(const int32_t* __restrict__ in, int ia, int ib, int n,
+                                              int32_t* __restrict__ dst, int32_t* last) {
+  int i = ia, j = ib, q = 0;
+  int32_t va = in[i], vb = in[j];
+  int32_t p = -1, w = -1;
+  bool held = false;  // p is a merged row not written yet (it may still cancel)
+  for (int t = 0; t < n; t++) {
+    const bool ta = va <= vb;
+    const int32_t v = ta ? va : vb;
+    i += ta ? 1 : 0;
+    j += ta ? 0 : 1;
+    const int32_t nv = in[ta ? i : j];
+    va = ta ? nv : va;
+    vb = ta ? vb : nv;
+    if (held && v == p) {
+      held = false;
+    } else {
+      if (held) {
+        dst[q++] = p;
+        w = p;
+      }
+      p = v;
+      held = true;
+    }
+  }
+  if (held) {
+    dst[q++] = p;
+    w = p;
+  }
+  *last = w;
+  return q;
+}
+
 // Phase II for one chunk of the active list (128 slots of a block, or 32 of a warp). Survivors
 // get their place in the next active list from a block (or warp) scan plus the look-back, and
 // their rows a slot of the next arena from one atomic per chunk. New pivots are copied to the
@@ -1150,7 +1194,7 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
 
 // kWarp: the chunk is 32 slots of one warp (warp scan, no block barrier); otherwise 128 slots of
 // the whole block
-template <bool kDense, bool kWarp>
+template <bool kDense, bool kWarp, bool kLane>
 __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
                                           WarpStage& S, int64_t* sh, int64_t* s_prefix,
                                           unsigned long long* s_cnt) {
@@ -1337,12 +1381,21 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
         S.in[base + span_a + rb + nb] = INT32_MAX;
       }
       __syncwarp();
-      const int P0 = __shfl_sync(0xffffffffu, p_first, c);
-      const int P1 = P0 + (int)__reduce_add_sync(0xffffffffu, mine ? (unsigned)npc : 0u);
-      switch (km) {
-        case 8: staged_rounds<8>(S, P0, P1, o0, mine, p_first, km); break;
-        case 16: staged_rounds<16>(S, P0, P1, o0, mine, p_first, km); break;
-        default: staged_rounds<0>(S, P0, P1, o0, mine, p_first, km); break;
+      if constexpr (kLane) {  // each job by its own lane
+        if (mine) {
+          int32_t lastv;
+          const int len = lane_merge_job(S.in, base + ra, base + span_a + rb, N, slot, &lastv);
+          S.jcnt[ord] = len;
+          S.jlow[ord] = lastv;
+        }
+      } else {  // pieces of every job spread over the lanes
+        const int P0 = __shfl_sync(0xffffffffu, p_first, c);
+        const int P1 = P0 + (int)__reduce_add_sync(0xffffffffu, mine ? (unsigned)npc : 0u);
+        switch (km) {
+          case 8: staged_rounds<8>(S, P0, P1, o0, mine, p_first, km); break;
+          case 16: staged_rounds<16>(S, P0, P1, o0, mine, p_first, km); break;
+          default: staged_rounds<0>(S, P0, P1, o0, mine, p_first, km); break;
+        }
       }
       __syncwarp();
     }
@@ -1469,9 +1522,10 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
 }
 
 // kDense: the pass may meet bit-packed columns or convert some; the row-list variant carries none
-// of it. kWarp: chunks of 32 slots claimed by single warps. The host picks the variant from
-// DevState::dense_on and warp_on (a separate graph for each).
-template <bool kDense, bool kWarp>
+// of it. kWarp: chunks of 32 slots claimed by single warps. kLane: each staged job merged by its
+// own lane (short columns), else merge pieces spread over the lanes. The host picks the variant
+// from DevState::dense_on, warp_on and lane_on (a separate graph for each).
+template <bool kDense, bool kWarp, bool kLane>
 __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   __shared__ int64_t sh[kAddWarps + 1];
   __shared__ int64_t s_chunk;
@@ -1492,7 +1546,7 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
       if (lane_id() == 0) chunk = atomicAdd(&a.ds->queue, 1u);
       chunk = __shfl_sync(0xffffffffu, chunk, 0);
       if ((int64_t)chunk >= nchunks) break;
-      add_chunk<kDense, true>(a, v, chunk, S, sh, s_prefix, s_cnt);
+      add_chunk<kDense, true, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
     }
     __syncthreads();
   } else {
@@ -1503,7 +1557,7 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
       const int64_t nchunks = (v.n_act + kAddThreads - 1) / kAddThreads;
       __syncthreads();
       if (chunk >= nchunks) break;
-      add_chunk<kDense, false>(a, v, chunk, S, sh, s_prefix, s_cnt);
+      add_chunk<kDense, false, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
     }
   }
   if (threadIdx.x == 0 && s_cnt[kCntTargets]) atomicAdd(&a.ds->totals[1], s_cnt[kCntTargets]);
@@ -1612,9 +1666,13 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
       const bool to_warp = !ds->warp_on && ds->n_act < ds->warp_below &&
                            ds->arena_used >= (unsigned long long)ds->warp_words * ds->totals[0];
       if (to_warp) ds->warp_on = 1;
+      // merge pieces over the lanes once the jobs are long enough to share them out
+      const bool to_pieces =
+          ds->lane_on && ds->arena_used >= (unsigned long long)ds->lane_words * ds->totals[0];
+      if (to_pieces) ds->lane_on = 0;
       // the pass is complete, so a later call can resume from the next one
       if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
-      else if (to_dense || to_warp) ds->status = ST_SWITCH;  // continued with the other kernel
+      else if (to_dense || to_warp || to_pieces) ds->status = ST_SWITCH;  // another kernel
     }
   }
   if (in_graph) cudaGraphSetConditional(cond, ds->status == ST_RUN ? 1u : 0u);
@@ -1712,7 +1770,7 @@ static RArgs make_args(ph_ctx* ctx) {
 
 // the kernels of one pass, in order; grids are fixed (persistent blocks loop over the work)
 // variant: the additions kernel, 1 = handles bit-packed columns (DevState::dense_on) + 2 = one
-// chunk per warp (DevState::warp_on)
+// chunk per warp (DevState::warp_on) + 4 = each job merged by its own lane (DevState::lane_on)
 static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
                         bool in_graph, int variant, bool time_add, cudaStream_t st) {
   ReduceState& rs = ctx->rs;
@@ -1770,10 +1828,14 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   const int add_bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
   const unsigned add_grid = blocks(sms * add_bps * (kThreads / kAddThreads), kAddThreads);
   switch (variant) {
-    case 0: k_add<false, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 1: k_add<true, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 2: k_add<false, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    default: k_add<true, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 0: k_add<false, false, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 1: k_add<true, false, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 2: k_add<false, true, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 3: k_add<true, true, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 4: k_add<false, false, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 5: k_add<true, false, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    case 6: k_add<false, true, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
+    default: k_add<true, true, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
   }
   PH_CHECK_LAUNCH();
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
@@ -1883,15 +1945,16 @@ void reduce_init(ph_ctx* ctx) {
                                                    : ctx->opts.warp_chunk_words;
   // the first passes' jobs are short: block chunks, unless any job length will do
   h.warp_on = h.warp_words == 0 && m < h.warp_below ? 1 : 0;
+  h.lane_words = ctx->opts.lane_merge_words == 0 ? 24 : ctx->opts.lane_merge_words;
+  h.lane_on = ctx->opts.lane_merge_words < 0 ? 0 : 1;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  PH_CUDA(cudaFuncSetAttribute(k_add<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kAddSmem));
-  PH_CUDA(cudaFuncSetAttribute(k_add<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kAddSmem));
-  PH_CUDA(cudaFuncSetAttribute(k_add<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kAddSmem));
-  PH_CUDA(cudaFuncSetAttribute(k_add<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kAddSmem));
+  const void* add_kernels[8] = {
+      (const void*)k_add<false, false, false>, (const void*)k_add<true, false, false>,
+      (const void*)k_add<false, true, false>,  (const void*)k_add<true, true, false>,
+      (const void*)k_add<false, false, true>,  (const void*)k_add<true, false, true>,
+      (const void*)k_add<false, true, true>,   (const void*)k_add<true, true, true>};
+  for (const void* f : add_kernels)
+    PH_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAddSmem));
   rs.passes = 0;
   rs.init = true;
   rs.done = false;
@@ -2010,11 +2073,12 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     const int32_t first_pass = h.pass;
     NvtxRange nvtx_range_(use_graph ? "pass loop (graph)" : "pass");
     if (use_graph) {
-      const int variant = (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0);
+      const int variant = (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0) + (h.lane_on ? 4 : 0);
       if (!rs.graph_exec[variant]) build_graph(ctx, a, variant);
       PH_CUDA(cudaGraphLaunch(rs.graph_exec[variant], st));
     } else {
-      launch_pass(ctx, a, 0, false, (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0), time_add, st);
+      launch_pass(ctx, a, 0, false,
+                  (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0) + (h.lane_on ? 4 : 0), time_add, st);
       if (time_add) rs.add_launches++;
     }
     PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
@@ -2237,7 +2301,7 @@ void reduced_columns(ph_ctx* ctx, int32_t cloud, int64_t n, int64_t* colptr, int
 
 void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
-  for (int d = 0; d < 4; d++) {
+  for (int d = 0; d < 8; d++) {
     if (rs.graph_exec[d]) cudaGraphExecDestroy(rs.graph_exec[d]);
     if (rs.graph[d]) cudaGraphDestroy(rs.graph[d]);
   }

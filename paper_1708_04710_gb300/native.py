@@ -31,7 +31,7 @@ class PHError(RuntimeError):
 
 
 class PhOpts(Structure):
-    _fields_ = [("strict_phase2", c_int32), ("use_cor10", c_int32), ("block_threads", c_int32),
+    _fields_ = [("strict_phase2", c_int32), ("use_cor10", c_int32), ("lane_merge_words", c_int32),
                 ("staged_merge_max", c_int32), ("merge_items", c_int32),
                 ("collect_stats", c_int32), ("use_graph", c_int32), ("time_kernels", c_int32),
                 ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32),
@@ -134,7 +134,8 @@ class Context:
                  collect_stats: bool = False, staged_merge_max: int = 0, merge_items: int = 0,
                  use_graph: bool = True, time_kernels: bool = False, add_blocks_per_sm: int = 0,
                  timeout_ms: int = 0, predict_pairs: bool = False, dense_threshold: int = 0,
-                 warp_chunks_below: int = 0, warp_chunk_words: int = 0, phase2_sets: int = 0,
+                 warp_chunks_below: int = 0, warp_chunk_words: int = 0, lane_merge_words: int = 0,
+                 phase2_sets: int = 0,
                  phase2_priority: int = 0,
                  arena_words: int = 0,
                  stream=None, device_alloc=None, device_free=None):
@@ -157,6 +158,7 @@ class Context:
         opts.dense_threshold = int(dense_threshold)
         opts.warp_chunks_below = int(warp_chunks_below)
         opts.warp_chunk_words = int(warp_chunk_words)
+        opts.lane_merge_words = int(lane_merge_words)
         opts.phase2_sets = int(phase2_sets)
         opts.phase2_priority = int(phase2_priority)
         opts.arena_words = int(arena_words)
