@@ -1093,11 +1093,14 @@ __device__ __forceinline__ void staged_rounds(WarpStage& S_, int P0, int P1, int
             vb = ta ? vb : nv;
           }
         }
+        // bit t of eq: row t equals row t + 1 (an equal pair, which cancels); rows past the
+        // piece's cnt are masked off, so a pair never reaches past the piece
+        const unsigned in_piece = cnt >= 32 ? 0xffffffffu : (1u << cnt) - 1u;
+        unsigned eq = 0;
 #pragma unroll
-        for (int t = 0; t < S; t++) {
-          const bool dup = (t > 0 && c[t - 1] == c[t]) || (t + 1 < cnt && c[t + 1] == c[t]);
-          if (t < cnt && !dup) keep |= 1u << t;
-        }
+        for (int t = 0; t + 1 < S; t++) eq |= (c[t] == c[t + 1] ? 1u : 0u) << t;
+        eq &= in_piece >> 1;
+        keep = in_piece & ~(eq | (eq << 1));
         kept = __popc(keep);
       }
     } else {
@@ -1847,7 +1850,7 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
 // leaves the store, and the device state that points into it, as it was: a later call resumes
 static void grow_store(ph_ctx* ctx, ColStore& s, int64_t need_words) {
   if (need_words <= s.cap) return;
-  const int64_t cap = std::max<int64_t>(need_words + need_words / 4, 1 << 20);
+  const int64_t cap = std::max<int64_t>(2 * need_words, 1 << 20);  // doubling: few regrowth stops
   int32_t* p = alloc_n<int32_t>(ctx, cap + kColSlack);
   if (s.p) ctx->dfree(s.p);
   s.p = p;
