@@ -77,10 +77,9 @@ typedef struct {
    * ones are staged in shared memory first (0 = library default = the largest staged size,
    * 1024) */
   int32_t staged_merge_max;
-  /* merge-path positions per lane in Phase II (1..64); 0 (default) picks one per warp from
-   * the mean length of its staged merges (8 below 80 rows, else 16). With 8 and 16 a lane
+  /* merge-path positions per lane in Phase II (1..64); 0 = library default (8). With 8 a lane
    * merges its piece into registers; any other value merges it from shared memory twice
-   * (count, then write) */
+   * (count, then write), which is slower and kept for testing the merge path */
   int32_t merge_items;
   /* 1: per-pass counters are collected (column additions, XORs, pivots, ...) */
   int32_t collect_stats;

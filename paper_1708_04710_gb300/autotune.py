@@ -1,9 +1,8 @@
 """Autotuner for the Phase II addition kernel.
 
-Six knobs shape the hot loop:
+Five knobs shape the hot loop:
 - ``staged_merge_max``: the longest merge that is still staged in shared memory (the threshold
   between the staged and the straight-from-memory merge);
-- ``merge_items``: merge-path positions per lane (0 = chosen per warp);
 - ``add_blocks_per_sm``: persistent blocks per SM (the grid shape);
 - ``dense_threshold``: when a column's addition goes bit-packed (0 = as soon as the bitmap is
   the smaller form and the sum exceeds 32 rows, -1 = never, t > 0 = beyond max(bitmap words + 1,
@@ -29,13 +28,12 @@ from .native import Context
 
 KNOBS = {
     "staged_merge_max": (1024, 512, 256),
-    "merge_items": (0, 8, 16),
     "add_blocks_per_sm": (4, 3, 2),
     "dense_threshold": (0, -1, 128, 1024),
     "warp_chunks_below": (0, -1, 1 << 20, 1 << 24),
     "lane_merge_words": (0, -1, 16, 40),
 }
-DEFAULTS = {"staged_merge_max": 1024, "merge_items": 0, "add_blocks_per_sm": 4,
+DEFAULTS = {"staged_merge_max": 1024, "add_blocks_per_sm": 4,
             "dense_threshold": 0, "warp_chunks_below": 0, "lane_merge_words": 0}
 
 
@@ -103,7 +101,7 @@ def tune(coords, offsets=None, max_dim: int = 2, max_diam2: int = -1, use_cache:
             cache = {}
         # an entry tuned over other knob values (an older library) is tuned again
         opts = cache.get(key, {}).get("options")
-        if opts and all(opts.get(k) in vals for k, vals in KNOBS.items()):
+        if opts and set(opts) == set(KNOBS) and all(opts[k] in v for k, v in KNOBS.items()):
             return dict(opts)
     best, best_t, trials = coordinate_descent(
         lambda o: _time_reduce(torch, coords, offsets, max_dim, max_diam2, o), KNOBS, DEFAULTS,

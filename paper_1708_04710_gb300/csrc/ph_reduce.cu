@@ -1179,9 +1179,9 @@ __device__ __forceinline__ int lane_merge_job(const int32_t* __restrict__ in, in
 // get their place in the next active list from a block (or warp) scan plus the look-back, and
 // their rows a slot of the next arena from one atomic per chunk. New pivots are copied to the
 // pivot store, one run per warp; survivors (with or without an addition) are merged in
-// registers (short columns, one thread per job) or staged in shared memory and merged by a
-// merge path over the concatenation of the batch's jobs, each padded to a multiple of km
-// positions (km chosen per warp from the mean merge length); merges longer than the staging
+// registers (short columns, one thread per job) or staged in shared memory and merged, each job
+// by its own lane (short jobs) or by a merge path over the batch's jobs cut into pieces of km
+// positions (8 unless ph_opts.merge_items says otherwise); merges longer than the staging
 // bound run from global memory; bit-packed jobs run one at a time by the whole warp. Targets
 // and zeroed columns are updated in place (no other job reads them this pass); new pivots and
 // left-most survivors, which other jobs may be reading as sources, are updated by k_commit.
@@ -1299,14 +1299,23 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   const bool dense_job =
       kDense && jb.surv &&
       (jb.dense_a || (B != nullptr && (jb.dense_b || goes_dense(a, jb.j, N))));
-  int cls = !jb.surv ? 0 : (dense_job ? 4 : (need <= 16 ? 1 : 3));
+  // the register network for jobs of up to kRegMax rows per column; the piece kernels keep it
+  // small (8), their registers go to the merge pieces
+  constexpr int kRegMax = kLane ? 16 : 8;
+  int cls = !jb.surv ? 0 : (dense_job ? 4 : (need <= kRegMax ? 1 : 3));
   if (__popc(__ballot_sync(0xffffffffu, cls == 1)) < 12 && cls == 1) cls = 3;
   const unsigned wneed = __reduce_max_sync(0xffffffffu, cls == 1 ? (unsigned)need : 0u);
   if (cls == 1) {
     int32_t last;
-    const int len = wneed <= 4   ? reg_symdiff<4>(A, na, B, nb, slot, last)
-                    : wneed <= 8 ? reg_symdiff<8>(A, na, B, nb, slot, last)
-                                 : reg_symdiff<16>(A, na, B, nb, slot, last);
+    int len;
+    if constexpr (kRegMax == 16) {
+      len = wneed <= 4   ? reg_symdiff<4>(A, na, B, nb, slot, last)
+            : wneed <= 8 ? reg_symdiff<8>(A, na, B, nb, slot, last)
+                         : reg_symdiff<16>(A, na, B, nb, slot, last);
+    } else {
+      len = wneed <= 4 ? reg_symdiff<4>(A, na, B, nb, slot, last)
+                       : reg_symdiff<8>(A, na, B, nb, slot, last);
+    }
     o_ptr = slot;
     o_len = len;
     if (B) a.low[jb.j] = last;
@@ -1325,10 +1334,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     const int ord = __popc(stmask & ((1u << lane) - 1u));  // ordinal among the staged jobs
     const int words = staged ? span_a + span_b : 0;
     const int w_ex = warp_incl_sum(words) - words;
-    const int n_staged = __popc(stmask);
-    const int mean = n_staged ? __reduce_add_sync(0xffffffffu, staged ? (unsigned)N : 0u) / n_staged
-                              : 0;
-    const int km = a.force_km > 0 ? a.force_km : (mean >= 80 ? 16 : 8);
+    const int km = a.force_km > 0 ? a.force_km : 8;
     const int npc = staged ? (N + km - 1) / km : 0;  // merge pieces of the job
     const int p_first = warp_incl_sum(npc) - npc;
     if (staged) {
@@ -1396,7 +1402,6 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
         const int P1 = P0 + (int)__reduce_add_sync(0xffffffffu, mine ? (unsigned)npc : 0u);
         switch (km) {
           case 8: staged_rounds<8>(S, P0, P1, o0, mine, p_first, km); break;
-          case 16: staged_rounds<16>(S, P0, P1, o0, mine, p_first, km); break;
           default: staged_rounds<0>(S, P0, P1, o0, mine, p_first, km); break;
         }
       }

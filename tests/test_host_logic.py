@@ -11,7 +11,7 @@ import pointclouds as pc
 def test_coordinate_descent_finds_separable_optimum():
     from paper_1708_04710_gb300.autotune import DEFAULTS, KNOBS, coordinate_descent
 
-    target = {"staged_merge_max": 512, "merge_items": 8, "add_blocks_per_sm": 3,
+    target = {"staged_merge_max": 512, "add_blocks_per_sm": 3,
               "dense_threshold": -1, "warp_chunks_below": 1 << 20, "lane_merge_words": 16}
 
     def timer(o):  # separable cost with its minimum at `target`
