@@ -70,7 +70,7 @@ typedef struct {
   /* Phase II starts by merging each job in its own lane (sequentially, from shared memory),
    * which suits short columns, and switches once, for the rest of the reduction, to merge
    * pieces spread over the lanes when the mean job (target + source rows reserved per
-   * surviving column) reaches this many rows; 0 = library default (24), -1 = pieces from the
+   * surviving column) reaches this many rows; 0 = library default (20), -1 = pieces from the
    * first pass */
   int32_t lane_merge_words;
   /* Phase II merges of more rows than this (target + source) run from global memory; shorter

@@ -10,7 +10,7 @@ Five knobs shape the hot loop:
 - ``warp_chunks_below``: the active-list length below which a warp, not a block, claims a chunk
   of the work queue (0 = 4,194,304, -1 = never), the block shape of the work queue;
 - ``lane_merge_words``: the mean job length (target + source rows) up to which each lane merges
-  its own job, before the lanes share every job's merge pieces (0 = 24, -1 = pieces throughout).
+  its own job, before the lanes share every job's merge pieces (0 = 20, -1 = pieces throughout).
 The tuner times full reductions of the caller's own filtration, one knob at a time (coordinate
 descent from the library defaults), and caches the winner per GPU model and workload class in a
 JSON file (``$PH_GB300_CACHE`` or ``~/.cache/ph_gb300/autotune.json``). Every option gives the

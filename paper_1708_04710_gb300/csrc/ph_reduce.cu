@@ -1953,7 +1953,7 @@ void reduce_init(ph_ctx* ctx) {
                                                    : ctx->opts.warp_chunk_words;
   // the first passes' jobs are short: block chunks, unless any job length will do
   h.warp_on = h.warp_words == 0 && m < h.warp_below ? 1 : 0;
-  h.lane_words = ctx->opts.lane_merge_words == 0 ? 24 : ctx->opts.lane_merge_words;
+  h.lane_words = ctx->opts.lane_merge_words == 0 ? 20 : ctx->opts.lane_merge_words;
   h.lane_on = ctx->opts.lane_merge_words < 0 ? 0 : 1;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
   const void* add_kernels[8] = {
