@@ -381,19 +381,32 @@ __device__ __forceinline__ SegMax block_scan_segmax(SegMax v, SegMax carry, SegM
 }
 
 
-// scan of the tile aggregates to tile prefixes, by one block
+// scan of the tile aggregates to tile prefixes, by one block; each thread takes kTopItems
+// consecutive tiles, so a pass of 10M columns (5,200 tiles) needs three block scans
+constexpr int kTopItems = 8;
 __device__ __forceinline__ void p1_top(const RArgs& a, const PV& v, SegMax* sh) {
   SegMax carry{-1, -1};
-  for (int64_t base = 0; base < v.ntiles; base += kThreads) {
-    int64_t i = base + threadIdx.x;
-    SegMax val{INT32_MAX, -1};
-    if (i < v.ntiles) {  // written by other blocks of this grid: read from L2
-      const int2 t = __ldcg(reinterpret_cast<const int2*>(a.tile_sm + i));
-      val = SegMax{t.x, t.y};
+  for (int64_t base = 0; base < v.ntiles; base += (int64_t)kThreads * kTopItems) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kTopItems;
+    SegMax x[kTopItems];
+#pragma unroll
+    for (int k = 0; k < kTopItems; k++) {
+      x[k] = SegMax{INT32_MAX, -1};
+      if (i0 + k < v.ntiles) {  // written by other blocks of this grid: read from L2
+        const int2 t = __ldcg(reinterpret_cast<const int2*>(a.tile_sm + i0 + k));
+        x[k] = SegMax{t.x, t.y};
+      }
     }
+    SegMax agg = x[0];
+#pragma unroll
+    for (int k = 1; k < kTopItems; k++) agg = segmax_combine(agg, x[k]);
     SegMax tot;
-    SegMax ex = block_scan_segmax(val, carry, sh, tot);
-    if (i < v.ntiles) a.tile_sm[i] = ex;
+    SegMax run = block_scan_segmax(agg, carry, sh, tot);
+#pragma unroll
+    for (int k = 0; k < kTopItems; k++) {
+      if (i0 + k < v.ntiles) a.tile_sm[i0 + k] = run;
+      run = segmax_combine(run, x[k]);
+    }
     carry = tot;
   }
 }
