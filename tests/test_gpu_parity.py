@@ -573,6 +573,8 @@ R_OPTS = [
     {"warp_chunks_below": 1 << 30, "warp_chunk_words": -1},
     {"staged_merge_max": 1},
     {"staged_merge_max": 16, "merge_items": 3},
+    {"lane_merge_words": -1},
+    {"lane_merge_words": 1 << 30},
     {"strict_phase2": True},
     {"use_cor10": False},
     {"phase2_sets": 3, "phase2_priority": 1},
@@ -770,6 +772,8 @@ def test_random_complexes_and_options(ph, orc):
         if rng.random() < 0.3:
             opts["staged_merge_max"] = int(rng.choice([1, 6, 40]))
             opts["merge_items"] = int(rng.choice([0, 2, 5, 16]))
+        if rng.random() < 0.4:
+            opts["lane_merge_words"] = int(rng.choice([-1, 4, 12, 1 << 30]))
         if rng.random() < 0.25:
             opts["strict_phase2"] = True
         if rng.random() < 0.2:
@@ -986,8 +990,13 @@ def _addition_cases(seed=5):
 @pytest.mark.parametrize("opts", [{}, {"staged_merge_max": 1}, {"staged_merge_max": 16},
                                   {"dense_threshold": 1},
                                   {"warp_chunks_below": 1 << 30, "warp_chunk_words": -1},
-                                  {"use_graph": False, "merge_items": 3}],
-                         ids=["default", "global", "staged16", "bitmaps", "warp", "host_km3"])
+                                  {"use_graph": False, "merge_items": 3},
+                                  {"lane_merge_words": -1},
+                                  {"lane_merge_words": 1 << 30},
+                                  {"lane_merge_words": -1, "warp_chunks_below": 1 << 30,
+                                   "warp_chunk_words": -1}],
+                         ids=["default", "global", "staged16", "bitmaps", "warp", "host_km3",
+                              "pieces", "lanes", "pieces_warp"])
 def test_column_additions_edge_cases(ph, orc, opts):
     # the symmetric difference itself on crafted columns, through every merge path: the
     # reduced matrix, lows and counters against the oracle's sorted-array additions
