@@ -70,7 +70,7 @@ struct DevState {
   unsigned int blocks_done;       // blocks of the current grid that have finished (last-block)
   unsigned long long t_start;     // global timer (ns) when this ph_reduce's loop began
   unsigned long long t_limit;     // ns the loop may run before it stops with ST_TIMEOUT
-  alignas(128) unsigned long long totals[2];  // survivors and targets of the current pass
+  alignas(128) unsigned long long totals[2];  // [1]: targets of the current pass ([0] unused)
   unsigned long long bound_words, bound_piv;
   alignas(128) unsigned long long arena_used;  // words taken in the arena of the current pass
   alignas(128) unsigned int queue;             // next chunk for k_add
@@ -94,6 +94,7 @@ struct DevState {
   // switches once per reduction (ST_SWITCH)
   int32_t lane_on;
   int64_t lane_words;
+  int32_t chunk_slots;  // slots per chunk of this pass's additions kernel (32 or 128)
 };
 
 struct RArgs {
@@ -265,16 +266,26 @@ __device__ __forceinline__ int32_t predicted_low(const RArgs& a, int32_t b, int3
   return (int32_t)(lo * 32 + __ffs(bits) - 1);
 }
 
+// kTI consecutive slots per thread and iteration, their loads issued together
+constexpr int kTabItems = 4;
 __global__ void k_tab(RArgs a) {
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v.n_act;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t j = v.act[i];
-    int32_t l = a.low[j];
-    if (l >= 0 && PH_DCHECK(&a.ds->debug_fault, l < a.rows_end, 1)) {
-      if (a.tab[l] > j) atomicMin(&a.tab[l], j);
-      if (!a.meta[l].low_seen) a.meta[l].low_seen = 1;  // for the essential estimate
+  constexpr int kTI = kTabItems;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kTI;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * kTI; i0 < v.n_act;
+       i0 += stride) {
+    int32_t j[kTI], l[kTI];
+#pragma unroll
+    for (int k = 0; k < kTI; k++) j[k] = i0 + k < v.n_act ? v.act[i0 + k] : -1;
+#pragma unroll
+    for (int k = 0; k < kTI; k++) l[k] = j[k] >= 0 ? a.low[j[k]] : -1;
+#pragma unroll
+    for (int k = 0; k < kTI; k++) {
+      if (l[k] >= 0 && PH_DCHECK(&a.ds->debug_fault, l[k] < a.rows_end, 1)) {
+        if (a.tab[l[k]] > j[k]) atomicMin(&a.tab[l[k]], j[k]);
+        if (!a.meta[l[k]].low_seen) a.meta[l[k]].low_seen = 1;  // for the essential estimate
+      }
     }
   }
 }
@@ -522,49 +533,78 @@ __global__ void k_p1_tiles(RArgs a) {
 
 
 
-// one 256-entry chunk per block iteration; its prefix is the tile's prefix combined with the
-// aggregates of the earlier chunks of the same tile
+// kMI consecutive slots per thread, kMI 256-slot chunks per block iteration (kMI divides the
+// chunks of a tile); every gather of the iteration is issued before any is used. The
+// iteration's prefix is the tile's prefix combined with the aggregates of the tile's earlier
+// chunks; the slots' own prefixes come from a thread-local fold and one block scan.
+constexpr int kMarkItems = 2;
+static_assert(kRItems % kMarkItems == 0, "a block iteration stays inside one Phase I tile");
+template <int kMI>
 __global__ void k_mark(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
   int64_t n_zero = 0, n_piv = 0, n_c10 = 0, n_pred = 0, n_empty = 0;
-  for (int64_t chunk = blockIdx.x; chunk < v.nchunks; chunk += gridDim.x) {
-    const int64_t tile = chunk / kRItems;
+  const int64_t nit = (v.n_act + (int64_t)kThreads * kMI - 1) / ((int64_t)kThreads * kMI);
+  for (int64_t it = blockIdx.x; it < nit; it += gridDim.x) {
+    const int64_t chunk0 = it * kMI;
+    const int64_t tile = chunk0 / kRItems;
     SegMax carry = a.tile_sm[tile];
-    for (int64_t c = tile * kRItems; c < chunk; c++) carry = segmax_combine(carry, a.chunk_sm[c]);
-    const int64_t e = chunk * kThreads + threadIdx.x;
-    SegMax val = p1_value(a, v, e);
+    for (int64_t c = tile * kRItems; c < chunk0; c++) carry = segmax_combine(carry, a.chunk_sm[c]);
+    const int64_t e0 = chunk0 * kThreads + (int64_t)threadIdx.x * kMI;
+    int32_t j[kMI], l[kMI], sg[kMI], s[kMI], b[kMI];
+    uint8_t f[kMI];
+#pragma unroll
+    for (int i = 0; i < kMI; i++) j[i] = e0 + i < v.n_act ? v.act[e0 + i] : -1;
+#pragma unroll
+    for (int i = 0; i < kMI; i++) {
+      l[i] = j[i] >= 0 ? a.low[j[i]] : -1;
+      sg[i] = j[i] >= 0 ? a.seg[j[i]] : INT32_MAX;
+      f[i] = j[i] >= 0 ? a.meta[j[i]].flags : 0;
+      b[i] = j[i] >= 0 ? a.beta[j[i]] : -1;
+    }
+#pragma unroll
+    for (int i = 0; i < kMI; i++) {
+      if (!PH_DCHECK(&a.ds->debug_fault, l[i] < a.rows_end, 2)) l[i] = -1, j[i] = -1;
+      s[i] = l[i] >= 0 ? a.tab[l[i]] : -1;
+    }
+    // Phase I values: the low of a colliding column, in its (cloud, dim) segment
+    SegMax x[kMI];
+#pragma unroll
+    for (int i = 0; i < kMI; i++)
+      x[i] = SegMax{sg[i], (l[i] >= 0 && s[i] != j[i]) ? l[i] : -1};
+    SegMax agg = x[0];
+#pragma unroll
+    for (int i = 1; i < kMI; i++) agg = segmax_combine(agg, x[i]);
     SegMax tot;
-    SegMax pre = block_scan_segmax(val, carry, sh, tot);
-    if (e < v.n_act) {
-      int32_t j = v.act[e];
-      int32_t l = a.low[j];
-      if (!PH_DCHECK(&a.ds->debug_fault, l < a.rows_end, 2)) continue;
-      uint8_t f = a.meta[j].flags;
-      const int32_t s = l >= 0 ? a.tab[l] : -1;
-      a.src_e[e] = s != j ? s : -1;  // Phase II reads it in list order
-      if (l < 0) {
-        a.meta[j].flags = f | F_FINAL;
+    SegMax run = block_scan_segmax(agg, carry, sh, tot);
+#pragma unroll
+    for (int i = 0; i < kMI; i++) {
+      const SegMax pre = run;
+      run = segmax_combine(run, x[i]);
+      if (j[i] < 0) continue;
+      const int64_t e = e0 + i;
+      a.src_e[e] = s[i] != j[i] ? s[i] : -1;  // Phase II reads it in list order
+      if (l[i] < 0) {
+        a.meta[j[i]].flags = f[i] | F_FINAL;
         n_zero++;
       } else {
-        int32_t P = (pre.seg == val.seg) ? pre.val : -1;
-        bool leftmost = s == j;
-        int32_t b = a.beta[j];
-        if (leftmost && (l == b || l > P)) {
-          a.meta[j].flags = f | F_PROVEN | F_NEWPIV;
-          a.owner[l] = j;
-          a.meta[l].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
+        const int32_t P = (pre.seg == x[i].seg) ? pre.val : -1;
+        const bool leftmost = s[i] == j[i];
+        if (leftmost && (l[i] == b[i] || l[i] > P)) {
+          a.meta[j[i]].flags = f[i] | F_PROVEN | F_NEWPIV;
+          a.owner[l[i]] = j[i];
+          a.meta[l[i]].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
           n_piv++;
-        } else if (a.cor10 && b < 0 && l < a.first_unp[val.seg - a.nc]) {
-          a.meta[j].flags = f | F_FINAL;  // Corollary 10, zero case
+        } else if (a.cor10 && b[i] < 0 && l[i] < a.first_unp[sg[i] - a.nc]) {
+          a.meta[j[i]].flags = f[i] | F_FINAL;  // Corollary 10, zero case
           n_c10++;
-        } else if (a.predict && b >= 0 && a.pred[j] < 0) {
-          const int32_t i = predicted_low(a, b, l);
-          if (i >= 0) {
-            a.pred[j] = i;
+        } else if (a.predict && b[i] >= 0 && a.pred[j[i]] < 0) {
+          const int32_t pi = predicted_low(a, b[i], l[i]);
+          if (pi >= 0) {
+            a.pred[j[i]] = pi;
             n_pred++;
-          } else if (i == -2) {
+          } else if (pi == -2) {
             n_empty++;
           }
         }
@@ -1233,7 +1273,6 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       look_publish(a, pass, chunk, n_surv);
       // the chunk's survivors take one contiguous run of the next arena
       if (wtot) wbase = atomicAdd(&a.ds->arena_used, (unsigned long long)wtot);
-      if (n_surv) atomicAdd(&a.ds->totals[0], (unsigned long long)n_surv);
     }
     off = (int64_t)__shfl_sync(0xffffffffu, wbase, 0) + wincl - w;
   } else {
@@ -1250,7 +1289,6 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       s_prefix[1] = (tot & kWordMask) ? (int64_t)atomicAdd(&a.ds->arena_used,
                                                            (unsigned long long)(tot & kWordMask))
                                       : 0;
-      if (n_surv) atomicAdd(&a.ds->totals[0], (unsigned long long)n_surv);
     }
     __syncthreads();
     off = s_prefix[1] + (excl & kWordMask);
@@ -1556,6 +1594,7 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   extern __shared__ __align__(16) unsigned char add_smem[];
   if (a.ds->status != ST_RUN) return;
   if (threadIdx.x == 0) s_v = pass_view(a.ds);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ds->chunk_slots = kWarp ? 32 : kAddThreads;
   const PV& v = s_v;
   WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[threadIdx.x >> 5];
   if (threadIdx.x < kNumCnt) s_cnt[threadIdx.x] = 0;
@@ -1670,7 +1709,20 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
   if (to_dense) ds->dense_on = 1;
   if (ds->status == ST_RUN) {
     const int32_t p = ds->pass;
-    ds->n_act = (int64_t)ds->totals[0];
+    // the survivors of the pass: the inclusive prefix the last chunk published in its look-back
+    // (anything but an inclusive state of this pass is an internal error)
+    const int64_t nch = (ds->n_act + ds->chunk_slots - 1) / ds->chunk_slots;
+    int64_t n_surv = 0;
+    if (nch > 0) {
+      const unsigned long long w = *(const volatile unsigned long long*)(a.look + nch - 1);
+      if ((w >> 40) != (look_tag(p) >> 40) || (w & kLookFlags) != kLookIncl) {
+        ds->status = ST_FAULT;
+        if (in_graph) cudaGraphSetConditional(cond, 0u);
+        return;
+      }
+      n_surv = (int64_t)(w & kLookVal);
+    }
+    ds->n_act = n_surv;
     int32_t* t = ds->act;
     ds->act = ds->act2;
     ds->act2 = t;
@@ -1685,11 +1737,11 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
       // ... and only once the jobs are long (mean arena words per survivor), where warps of one
       // block would otherwise wait on each other's merges
       const bool to_warp = !ds->warp_on && ds->n_act < ds->warp_below &&
-                           ds->arena_used >= (unsigned long long)ds->warp_words * ds->totals[0];
+                           ds->arena_used >= (unsigned long long)ds->warp_words * n_surv;
       if (to_warp) ds->warp_on = 1;
       // merge pieces over the lanes once the jobs are long enough to share them out
       const bool to_pieces =
-          ds->lane_on && ds->arena_used >= (unsigned long long)ds->lane_words * ds->totals[0];
+          ds->lane_on && ds->arena_used >= (unsigned long long)ds->lane_words * n_surv;
       if (to_pieces) ds->lane_on = 0;
       // the pass is complete, so a later call can resume from the next one
       if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
@@ -1804,11 +1856,11 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   };
   k_tab_init<<<grid_for(ctx, a.rows_end, kThreads), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_tab<<<blocks(sms * 8, kThreads), kThreads, 0, st>>>(a);
+  k_tab<<<blocks(sms * 8, kThreads * kTabItems), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
   k_p1_tiles<<<blocks(sms * 8, kRTile), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
-  k_mark<<<blocks(sms * 8, kThreads), kThreads, 0, st>>>(a);
+  k_mark<kMarkItems><<<blocks(sms * 8, kThreads * kMarkItems), kThreads, 0, st>>>(a);
   PH_CHECK_LAUNCH();
   if (ctx->opts.collect_stats) {
     k_ess_count<<<sms * 4, kThreads, 0, st>>>(a, ctx->m);
