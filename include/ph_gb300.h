@@ -118,6 +118,13 @@ typedef struct {
   /* The job length that switch needs, in mean arena words per survivor. 0 (default): 40;
    * < 0: any (then a complex of fewer than warp_chunks_below columns starts with warp chunks). */
   int32_t warp_chunk_words;
+  /* Once warp chunks and merge pieces are on, a pass that ends with fewer than this many active
+   * columns switches the warps, for the rest of the reduction, to chunks of 8 columns (lanes
+   * 8..31 hold no column of their own and take merge pieces), so that the short late passes
+   * spread over more warps. Results are identical either way. 0 (default): 16 columns per warp
+   * of the addition kernel's grid (77,824 columns on 152 SMs with add_blocks_per_sm = 4);
+   * < 0: 32-column chunks throughout. */
+  int32_t narrow_chunks_below;
   /* Phase II with p processors (Sec. 3.4.1-3.4.2). phase2_sets = p > 0: each pass the targets
    * fall into neighbour sets, one per low row i, holding the targets whose addition the pass
    * may do; only the targets of the first p sets in priority order receive their addition, the

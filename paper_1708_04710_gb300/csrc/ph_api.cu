@@ -291,6 +291,7 @@ void ph_default_opts(ph_opts* o) {
   o->dense_threshold = 0;
   o->warp_chunks_below = 0;
   o->warp_chunk_words = 0;
+  o->narrow_chunks_below = 0;
   o->phase2_sets = 0;
   o->phase2_priority = 0;
   o->arena_words = 0;

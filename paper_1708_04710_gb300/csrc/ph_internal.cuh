@@ -115,9 +115,11 @@ struct ReduceState {
   ColStore arena[2];           // pass p writes its survivors into arena[p & 1]
   std::vector<ColStore> pivots;  // chunks holding proven columns
   // the pass loop: one pass as the body of a conditional while node, per variant of the
-  // additions kernel (+1 bit-packed columns, +2 one chunk per warp, +4 jobs merged by lanes)
-  cudaGraph_t graph[8] = {};
-  cudaGraphExec_t graph_exec[8] = {};
+  // additions kernel (+1 bit-packed columns, +2 one chunk per warp, +4 jobs merged by lanes;
+  // 8, 9: 8-slot warp chunks with merge pieces, without and with bit-packed columns)
+  static constexpr int kAddVariants = 10;
+  cudaGraph_t graph[kAddVariants] = {};
+  cudaGraphExec_t graph_exec[kAddVariants] = {};
   int32_t passes = 0;
   bool init = false;
   bool done = false;

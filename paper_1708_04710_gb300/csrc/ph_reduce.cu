@@ -94,7 +94,11 @@ struct DevState {
   // switches once per reduction (ST_SWITCH)
   int32_t lane_on;
   int64_t lane_words;
-  int32_t chunk_slots;  // slots per chunk of this pass's additions kernel (32 or 128)
+  // ... and once merge pieces are on and fewer than narrow_below columns are active, warp
+  // chunks of 8 slots, so that the short late passes spread over more warps (ST_SWITCH, once)
+  int32_t narrow_on;
+  int64_t narrow_below;
+  int32_t chunk_slots;  // slots per chunk of this pass's additions kernel (8, 32 or 128)
 };
 
 struct RArgs {
@@ -180,6 +184,16 @@ __device__ __forceinline__ void stat_add(int64_t* stats, int k, int64_t v) {
 }
 
 
+// Programmatic dependent launch. The kernels of a pass are launched so that each may start
+// while the one before it in the stream drains (its blocks fill the SMs that kernel frees): every
+// pass kernel first waits here until the previous kernel has completed and its writes are
+// visible, before it reads or writes anything. Without such a predecessor the wait returns at
+// once. The trigger, given once a kernel's blocks run, lets the next kernel's launch begin.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // True in the one block that finishes the grid last; it then sees every other block's writes.
 // Only the first `participants` blocks of the grid may call it (the others have no work and
 // may leave at once).
@@ -194,6 +208,8 @@ __device__ __forceinline__ bool last_block(unsigned int* done, unsigned int part
 
 // ------------------------------------------------------------------------------------------
 __global__ void k_tab_init(RArgs a) {
+  pdl_wait();
+  pdl_trigger();
   DevState* ds = a.ds;
   if (ds->status != ST_RUN) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -269,6 +285,8 @@ __device__ __forceinline__ int32_t predicted_low(const RArgs& a, int32_t b, int3
 // kTI consecutive slots per thread and iteration, their loads issued together
 constexpr int kTabItems = 4;
 __global__ void k_tab(RArgs a) {
+  pdl_wait();
+  pdl_trigger();
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
   constexpr int kTI = kTabItems;
@@ -442,6 +460,8 @@ __global__ void k_p1_tiles(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
   __shared__ int64_t shs[kWarps + 1];
   __shared__ SegMax s_warp[kRItems][kWarps];  // aggregate of each warp's 32 slots per chunk
+  pdl_wait();
+  pdl_trigger();
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
   // blocks beyond the tiles leave at once; block 0 always takes part (it checks capacity)
@@ -542,6 +562,8 @@ static_assert(kRItems % kMarkItems == 0, "a block iteration stays inside one Pha
 template <int kMI>
 __global__ void k_mark(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
+  pdl_wait();
+  pdl_trigger();
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
   int64_t n_zero = 0, n_piv = 0, n_c10 = 0, n_pred = 0, n_empty = 0;
@@ -918,6 +940,11 @@ struct __align__(16) WarpStage {
 constexpr int kAddThreads = 128;
 constexpr int kAddWarps = kAddThreads / 32;
 constexpr size_t kAddSmem = sizeof(WarpStage) * kAddWarps;
+// the default switch to 8-slot warp chunks: fewer active columns than this many per warp of the
+// grid. An 8-slot chunk takes about half as long as a 32-slot one, but pays its fixed costs
+// (claim, column records, look-back) on a quarter of the columns: it wins once its chunks fit in
+// about two waves of the grid's warps, where the 32-slot chunks leave most warps idle
+constexpr int kNarrowColsPerWarp = 16;
 
 // merge the staged rows A[x0..x1), B[y0..y1) of one lane's range; equal rows cancel.
 // With WRITE, the surviving rows go to dst; returns their count and the last one in *last.
@@ -1248,14 +1275,17 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
   return v;
 }
 
-// kWarp: the chunk is 32 slots of one warp (warp scan, no block barrier); otherwise 128 slots of
-// the whole block
-template <bool kDense, bool kWarp, bool kLane>
+// kSlots > 0: the chunk is kSlots (32 or 8) slots of one warp, lanes kSlots.. without a job
+// (warp scan, no block barrier); kSlots = 0: 128 slots of the whole block
+template <bool kDense, int kSlots, bool kLane>
 __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
                                           WarpStage& S, int64_t* sh, int64_t* s_prefix,
                                           unsigned long long* s_cnt) {
+  constexpr bool kWarp = kSlots > 0;
   const int lane = lane_id();
-  const int64_t e = kWarp ? chunk * 32 + lane : chunk * kAddThreads + threadIdx.x;
+  const int64_t e = !kWarp         ? chunk * kAddThreads + threadIdx.x
+                    : kSlots == 32 ? chunk * 32 + lane
+                                   : (lane < kSlots ? chunk * kSlots + lane : v.n_act);
   Job jb = job_of<kDense>(a, v, e);
   const int32_t pass = a.ds->pass;
   int64_t off, n_surv;
@@ -1354,7 +1384,8 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   // small (8), their registers go to the merge pieces
   constexpr int kRegMax = kLane ? 16 : 8;
   int cls = !jb.surv ? 0 : (dense_job ? 4 : (need <= kRegMax ? 1 : 3));
-  if (__popc(__ballot_sync(0xffffffffu, cls == 1)) < 12 && cls == 1) cls = 3;
+  constexpr int kRegMinJobs = kWarp ? 12 * kSlots / 32 : 12;  // of the warp's slots
+  if (__popc(__ballot_sync(0xffffffffu, cls == 1)) < kRegMinJobs && cls == 1) cls = 3;
   const unsigned wneed = __reduce_max_sync(0xffffffffu, cls == 1 ? (unsigned)need : 0u);
   if (cls == 1) {
     int32_t last;
@@ -1581,32 +1612,36 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
 }
 
 // kDense: the pass may meet bit-packed columns or convert some; the row-list variant carries none
-// of it. kWarp: chunks of 32 slots claimed by single warps. kLane: each staged job merged by its
-// own lane (short columns), else merge pieces spread over the lanes. The host picks the variant
-// from DevState::dense_on, warp_on and lane_on (a separate graph for each).
-template <bool kDense, bool kWarp, bool kLane>
+// of it. kSlots: chunks of kSlots (32 or 8) slots claimed by single warps, 0: chunks of 128 slots
+// claimed by blocks. kLane: each staged job merged by its own lane (short columns), else merge
+// pieces spread over the lanes. The host picks the variant from DevState::dense_on, warp_on,
+// narrow_on and lane_on (a separate graph for each).
+template <bool kDense, int kSlots, bool kLane>
 __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
+  constexpr bool kWarp = kSlots > 0;
   __shared__ int64_t sh[kAddWarps + 1];
   __shared__ int64_t s_chunk;
   __shared__ int64_t s_prefix[2];
   __shared__ unsigned long long s_cnt[kNumCnt];
   __shared__ PV s_v;  // per-pass values from shared memory rather than held in registers
   extern __shared__ __align__(16) unsigned char add_smem[];
+  pdl_wait();
+  pdl_trigger();
   if (a.ds->status != ST_RUN) return;
   if (threadIdx.x == 0) s_v = pass_view(a.ds);
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.ds->chunk_slots = kWarp ? 32 : kAddThreads;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ds->chunk_slots = kWarp ? kSlots : kAddThreads;
   const PV& v = s_v;
   WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[threadIdx.x >> 5];
   if (threadIdx.x < kNumCnt) s_cnt[threadIdx.x] = 0;
   if constexpr (kWarp) {
     __syncthreads();  // publishes s_v and the zeroed counters
-    const int64_t nchunks = (v.n_act + 31) / 32;
-    for (;;) {  // device work queue of 32-slot chunks, claimed in order by whole warps
+    const int64_t nchunks = (v.n_act + kSlots - 1) / kSlots;
+    for (;;) {  // device work queue of kSlots-slot chunks, claimed in order by whole warps
       unsigned int chunk = 0;
       if (lane_id() == 0) chunk = atomicAdd(&a.ds->queue, 1u);
       chunk = __shfl_sync(0xffffffffu, chunk, 0);
       if ((int64_t)chunk >= nchunks) break;
-      add_chunk<kDense, true, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
+      add_chunk<kDense, kSlots, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
     }
     __syncthreads();
   } else {
@@ -1617,7 +1652,7 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
       const int64_t nchunks = (v.n_act + kAddThreads - 1) / kAddThreads;
       __syncthreads();
       if (chunk >= nchunks) break;
-      add_chunk<kDense, false, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
+      add_chunk<kDense, 0, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
     }
   }
   if (threadIdx.x == 0 && s_cnt[kCntTargets]) atomicAdd(&a.ds->totals[1], s_cnt[kCntTargets]);
@@ -1632,6 +1667,8 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
 // |E^l| after this pass's marks (per-pass counter; only with collect_stats)
 __global__ void k_ess_count(RArgs a, int64_t m) {
   __shared__ int64_t sh[kWarps + 1];
+  pdl_wait();
+  pdl_trigger();
   if (a.ds->status != ST_RUN) return;
   int64_t n = 0;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < m;
@@ -1665,6 +1702,7 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
 
 // the deferred column updates, then (last block) the end of the pass
 __global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
+  pdl_wait();
   // as many blocks as the deferred list needs take part; block 0 always does (it ends the pass)
   const int64_t n = a.ds->status == ST_RUN ? (int64_t)a.ds->n_deferred : 0;
   const unsigned parts =
@@ -1743,9 +1781,13 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
       const bool to_pieces =
           ds->lane_on && ds->arena_used >= (unsigned long long)ds->lane_words * n_surv;
       if (to_pieces) ds->lane_on = 0;
+      // 8-slot warp chunks once the active list is short
+      const bool to_narrow =
+          ds->warp_on && !ds->lane_on && !ds->narrow_on && n_surv < ds->narrow_below;
+      if (to_narrow) ds->narrow_on = 1;
       // the pass is complete, so a later call can resume from the next one
       if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
-      else if (to_dense || to_warp || to_pieces) ds->status = ST_SWITCH;  // another kernel
+      else if (to_dense || to_warp || to_pieces || to_narrow) ds->status = ST_SWITCH;
     }
   }
   if (in_graph) cudaGraphSetConditional(cond, ds->status == ST_RUN ? 1u : 0u);
@@ -1841,9 +1883,45 @@ static RArgs make_args(ph_ctx* ctx) {
   return a;
 }
 
+// the additions kernel a pass runs: 1 = handles bit-packed columns (DevState::dense_on) + 2 = one
+// chunk per warp (DevState::warp_on) + 4 = each job merged by its own lane (DevState::lane_on);
+// 8 + 1 = bit-packed: 8-slot warp chunks with merge pieces (DevState::narrow_on)
+static int add_variant(const DevState& h) {
+  if (h.narrow_on) return 8 + (h.dense_on ? 1 : 0);
+  return (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0) + (h.lane_on ? 4 : 0);
+}
+
+// grid of the persistent additions kernel: add_blocks_per_sm units of two 128-thread blocks per
+// SM, no more blocks than the largest active list (all m columns) can use
+static unsigned add_grid_of(const ph_ctx* ctx) {
+  const int64_t m = std::max<int64_t>(ctx->m, 1);
+  const int bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
+  const int64_t full = (int64_t)ctx->num_sms * bps * (kThreads / kAddThreads);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (m + kAddThreads - 1) / kAddThreads));
+}
+
+// launches one pass kernel; pdl: the kernel may start while the kernel before it in the stream
+// drains (programmatic dependent launch; the kernel waits in pdl_wait)
+constexpr bool kUsePdl = true;
+template <typename... KArgs, typename... Args>
+static void launch_k(ph_ctx* ctx, bool pdl, void (*kern)(KArgs...), unsigned grid, unsigned block,
+                     size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl && kUsePdl ? 1 : 0;
+  ctx->launches++;
+  PH_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+}
+
 // the kernels of one pass, in order; grids are fixed (persistent blocks loop over the work)
-// variant: the additions kernel, 1 = handles bit-packed columns (DevState::dense_on) + 2 = one
-// chunk per warp (DevState::warp_on) + 4 = each job merged by its own lane (DevState::lane_on)
+// variant: the additions kernel (add_variant)
 static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
                         bool in_graph, int variant, bool time_add, cudaStream_t st) {
   ReduceState& rs = ctx->rs;
@@ -1854,18 +1932,13 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   auto blocks = [&](int64_t full, int64_t per_block) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (m + per_block - 1) / per_block));
   };
-  k_tab_init<<<grid_for(ctx, a.rows_end, kThreads), kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
-  k_tab<<<blocks(sms * 8, kThreads * kTabItems), kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
-  k_p1_tiles<<<blocks(sms * 8, kRTile), kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
-  k_mark<kMarkItems><<<blocks(sms * 8, kThreads * kMarkItems), kThreads, 0, st>>>(a);
-  PH_CHECK_LAUNCH();
-  if (ctx->opts.collect_stats) {
-    k_ess_count<<<sms * 4, kThreads, 0, st>>>(a, ctx->m);
-    PH_CHECK_LAUNCH();
-  }
+  launch_k(ctx, true, k_tab_init, grid_for(ctx, a.rows_end, kThreads), kThreads, 0, st, a);
+  launch_k(ctx, true, k_tab, blocks(sms * 8, kThreads * kTabItems), kThreads, 0, st, a);
+  launch_k(ctx, true, k_p1_tiles, blocks(sms * 8, kRTile), kThreads, 0, st, a);
+  launch_k(ctx, true, k_mark<kMarkItems>, blocks(sms * 8, kThreads * kMarkItems), kThreads, 0, st,
+           a);
+  if (ctx->opts.collect_stats)
+    launch_k(ctx, true, k_ess_count, (unsigned)sms * 4, kThreads, 0, st, a, ctx->m);
   if (ctx->opts.phase2_sets > 0 && a.rows_end > 0) {  // host-driven loop only
     const int64_t rows = a.rows_end;
     int bits = 1;
@@ -1898,22 +1971,16 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
     rs.ev.push_back(e1);
     PH_CUDA(cudaEventRecord(e0, st));
   }
-  const int add_bps = ctx->opts.add_blocks_per_sm > 0 ? std::min(ctx->opts.add_blocks_per_sm, 4) : 4;
-  const unsigned add_grid = blocks(sms * add_bps * (kThreads / kAddThreads), kAddThreads);
-  switch (variant) {
-    case 0: k_add<false, false, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 1: k_add<true, false, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 2: k_add<false, true, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 3: k_add<true, true, false><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 4: k_add<false, false, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 5: k_add<true, false, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    case 6: k_add<false, true, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-    default: k_add<true, true, true><<<add_grid, kAddThreads, kAddSmem, st>>>(a); break;
-  }
-  PH_CHECK_LAUNCH();
+  static void (*const add_kernels[ReduceState::kAddVariants])(RArgs) = {
+      k_add<false, 0, false>,  k_add<true, 0, false>, k_add<false, 32, false>,
+      k_add<true, 32, false>,  k_add<false, 0, true>, k_add<true, 0, true>,
+      k_add<false, 32, true>,  k_add<true, 32, true>, k_add<false, 8, false>,
+      k_add<true, 8, false>};
+  // (an event recorded between two kernels needs the first one complete: no early start then)
+  launch_k(ctx, !time_add, add_kernels[variant], add_grid_of(ctx), kAddThreads, kAddSmem, st, a);
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
-  k_commit<<<blocks(sms * 2, kThreads), kThreads, 0, st>>>(a, cond, in_graph ? 1 : 0);
-  PH_CHECK_LAUNCH();
+  launch_k(ctx, !time_add, k_commit, blocks(sms * 2, kThreads), kThreads, 0, st, a, cond,
+           in_graph ? 1 : 0);
 }
 
 // the new buffer is taken before the old one goes, so a failed allocation (PH_ERR_ALLOC)
@@ -1946,7 +2013,7 @@ void reduce_init(ph_ctx* ctx) {
   int64_t ntiles = (m + kRTile - 1) / kRTile;
   rs.tiles_bytes = ntiles * (1 + kRItems) * sizeof(SegMax);
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
-  const int64_t nchunks = (m + 31) / 32 + 1;  // chunks of either shape
+  const int64_t nchunks = (m + 7) / 8 + 1;  // chunks of any shape (8 slots or more)
   rs.look = alloc_n<unsigned long long>(ctx, nchunks);
   PH_CUDA(cudaMemsetAsync(rs.look, 0, nchunks * sizeof(unsigned long long), st));
   rs.dlist = alloc_n<int32_t>(ctx, m);
@@ -2020,12 +2087,18 @@ void reduce_init(ph_ctx* ctx) {
   h.warp_on = h.warp_words == 0 && m < h.warp_below ? 1 : 0;
   h.lane_words = ctx->opts.lane_merge_words == 0 ? 20 : ctx->opts.lane_merge_words;
   h.lane_on = ctx->opts.lane_merge_words < 0 ? 0 : 1;
+  h.narrow_below = ctx->opts.narrow_chunks_below < 0 ? 0
+                   : ctx->opts.narrow_chunks_below == 0
+                       ? (int64_t)add_grid_of(ctx) * kAddWarps * kNarrowColsPerWarp
+                       : ctx->opts.narrow_chunks_below;
+  h.narrow_on = 0;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  const void* add_kernels[8] = {
-      (const void*)k_add<false, false, false>, (const void*)k_add<true, false, false>,
-      (const void*)k_add<false, true, false>,  (const void*)k_add<true, true, false>,
-      (const void*)k_add<false, false, true>,  (const void*)k_add<true, false, true>,
-      (const void*)k_add<false, true, true>,   (const void*)k_add<true, true, true>};
+  const void* add_kernels[ReduceState::kAddVariants] = {
+      (const void*)k_add<false, 0, false>,  (const void*)k_add<true, 0, false>,
+      (const void*)k_add<false, 32, false>, (const void*)k_add<true, 32, false>,
+      (const void*)k_add<false, 0, true>,   (const void*)k_add<true, 0, true>,
+      (const void*)k_add<false, 32, true>,  (const void*)k_add<true, 32, true>,
+      (const void*)k_add<false, 8, false>,  (const void*)k_add<true, 8, false>};
   for (const void* f : add_kernels)
     PH_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAddSmem));
   rs.passes = 0;
@@ -2146,12 +2219,11 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     const int32_t first_pass = h.pass;
     NvtxRange nvtx_range_(use_graph ? "pass loop (graph)" : "pass");
     if (use_graph) {
-      const int variant = (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0) + (h.lane_on ? 4 : 0);
+      const int variant = add_variant(h);
       if (!rs.graph_exec[variant]) build_graph(ctx, a, variant);
       PH_CUDA(cudaGraphLaunch(rs.graph_exec[variant], st));
     } else {
-      launch_pass(ctx, a, 0, false,
-                  (h.dense_on ? 1 : 0) + (h.warp_on ? 2 : 0) + (h.lane_on ? 4 : 0), time_add, st);
+      launch_pass(ctx, a, 0, false, add_variant(h), time_add, st);
       if (time_add) rs.add_launches++;
     }
     PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
@@ -2374,7 +2446,7 @@ void reduced_columns(ph_ctx* ctx, int32_t cloud, int64_t n, int64_t* colptr, int
 
 void free_reduce_state(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
-  for (int d = 0; d < 8; d++) {
+  for (int d = 0; d < ReduceState::kAddVariants; d++) {
     if (rs.graph_exec[d]) cudaGraphExecDestroy(rs.graph_exec[d]);
     if (rs.graph[d]) cudaGraphDestroy(rs.graph[d]);
   }

@@ -37,7 +37,7 @@ class PhOpts(Structure):
                 ("add_blocks_per_sm", c_int32), ("timeout_ms", c_int32),
                 ("predict_pairs", c_int32), ("dense_threshold", c_int32),
                 ("warp_chunks_below", c_int32), ("warp_chunk_words", c_int32),
-                ("phase2_sets", c_int32),
+                ("narrow_chunks_below", c_int32), ("phase2_sets", c_int32),
                 ("phase2_priority", c_int32), ("arena_words", c_int64)]
 
 
@@ -135,7 +135,7 @@ class Context:
                  use_graph: bool = True, time_kernels: bool = False, add_blocks_per_sm: int = 0,
                  timeout_ms: int = 0, predict_pairs: bool = False, dense_threshold: int = 0,
                  warp_chunks_below: int = 0, warp_chunk_words: int = 0, lane_merge_words: int = 0,
-                 phase2_sets: int = 0,
+                 narrow_chunks_below: int = 0, phase2_sets: int = 0,
                  phase2_priority: int = 0,
                  arena_words: int = 0,
                  stream=None, device_alloc=None, device_free=None):
@@ -159,6 +159,7 @@ class Context:
         opts.warp_chunks_below = int(warp_chunks_below)
         opts.warp_chunk_words = int(warp_chunk_words)
         opts.lane_merge_words = int(lane_merge_words)
+        opts.narrow_chunks_below = int(narrow_chunks_below)
         opts.phase2_sets = int(phase2_sets)
         opts.phase2_priority = int(phase2_priority)
         opts.arena_words = int(arena_words)

@@ -575,6 +575,10 @@ R_OPTS = [
     {"staged_merge_max": 16, "merge_items": 3},
     {"lane_merge_words": -1},
     {"lane_merge_words": 1 << 30},
+    {"lane_merge_words": -1, "warp_chunks_below": 1 << 30, "warp_chunk_words": -1,
+     "narrow_chunks_below": -1},
+    {"lane_merge_words": -1, "warp_chunks_below": 1 << 30, "warp_chunk_words": -1,
+     "narrow_chunks_below": 1 << 30, "dense_threshold": 1},
     {"strict_phase2": True},
     {"use_cor10": False},
     {"phase2_sets": 3, "phase2_priority": 1},
@@ -665,6 +669,20 @@ def test_full_size_single(ph, name, use_graph):
     assert _sha(gp) == g["pairs_sha"]
     assert _sha(ge) == g["ess_sha"]
     assert np.bincount(es["dim"], minlength=max_dim + 1).tolist() == g["ess_per_dim"]
+
+
+@pytest.mark.parametrize("narrow", [-1, 1 << 30])
+def test_full_size_torus400_chunk_widths(ph, narrow):
+    # the late passes in 32-slot warp chunks throughout (-1), or in 8-slot warp chunks from the
+    # first pass with merge pieces on (2^30): the golden pairs and per-pass counters either way
+    g = _golden("torus400")
+    ctx = _gpu(ph, pc.torus400(), 2, narrow_chunks_below=narrow)
+    st = ctx.reduce()
+    assert st["converged"] and st["passes"] == g["passes"]
+    assert np.array_equal(ctx.pass_stats()[:, :8], np.array(g["pass_stats"], np.int64))
+    pr, es = _gpu_pairs(ctx, 0)
+    gp, ge = _canon(pr["birth"], pr["death"], es["idx"])
+    assert _sha(gp) == g["pairs_sha"] and _sha(ge) == g["ess_sha"]
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
@@ -774,6 +792,8 @@ def test_random_complexes_and_options(ph, orc):
             opts["merge_items"] = int(rng.choice([0, 2, 5, 16]))
         if rng.random() < 0.4:
             opts["lane_merge_words"] = int(rng.choice([-1, 4, 12, 1 << 30]))
+        if rng.random() < 0.3:
+            opts["narrow_chunks_below"] = int(rng.choice([-1, 50, 1 << 30]))
         if rng.random() < 0.25:
             opts["strict_phase2"] = True
         if rng.random() < 0.2:
@@ -994,9 +1014,11 @@ def _addition_cases(seed=5):
                                   {"lane_merge_words": -1},
                                   {"lane_merge_words": 1 << 30},
                                   {"lane_merge_words": -1, "warp_chunks_below": 1 << 30,
-                                   "warp_chunk_words": -1}],
+                                   "warp_chunk_words": -1, "narrow_chunks_below": -1},
+                                  {"lane_merge_words": -1, "warp_chunks_below": 1 << 30,
+                                   "warp_chunk_words": -1, "narrow_chunks_below": 1 << 30}],
                          ids=["default", "global", "staged16", "bitmaps", "warp", "host_km3",
-                              "pieces", "lanes", "pieces_warp"])
+                              "pieces", "lanes", "pieces_warp32", "pieces_warp8"])
 def test_column_additions_edge_cases(ph, orc, opts):
     # the symmetric difference itself on crafted columns, through every merge path: the
     # reduced matrix, lows and counters against the oracle's sorted-array additions
