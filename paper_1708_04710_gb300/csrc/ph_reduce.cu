@@ -320,6 +320,16 @@ __device__ __forceinline__ int32_t dense_min_of(const RArgs& a, int32_t j) {
   return t;
 }
 
+// the (cloud, dim) segment of column j, seg[j] = dim * clouds + cloud: with one cloud the
+// dimension, found from the dimension starts (no load); else loaded
+__device__ __forceinline__ int32_t seg_of(const RArgs& a, int32_t j) {
+  if (a.nc != 1) return a.seg[j];
+  int32_t d = 0;
+#pragma unroll
+  for (int k = 1; k <= kMaxDim; k++) d += j >= a.dim_start[k] ? 1 : 0;
+  return d;
+}
+
 // first column id of column j's dimension
 __device__ __forceinline__ int32_t dim_start_of(const RArgs& a, int32_t j) {
   int32_t b = 0;
@@ -492,7 +502,7 @@ __global__ void k_p1_tiles(RArgs a) {
 #pragma unroll
     for (int it = 0; it < kRItems; it++) {
       l[it] = j[it] >= 0 ? a.low[j[it]] : -1;
-      sg[it] = j[it] >= 0 ? a.seg[j[it]] : INT32_MAX;
+      sg[it] = j[it] >= 0 ? seg_of(a, j[it]) : INT32_MAX;
       n[it] = j[it] >= 0 ? a.meta[j[it]].len : 0;
     }
 #pragma unroll
@@ -581,7 +591,7 @@ __global__ void k_mark(RArgs a) {
 #pragma unroll
     for (int i = 0; i < kMI; i++) {
       l[i] = j[i] >= 0 ? a.low[j[i]] : -1;
-      sg[i] = j[i] >= 0 ? a.seg[j[i]] : INT32_MAX;
+      sg[i] = j[i] >= 0 ? seg_of(a, j[i]) : INT32_MAX;
       f[i] = j[i] >= 0 ? a.meta[j[i]].flags : 0;
       b[i] = j[i] >= 0 ? a.beta[j[i]] : -1;
     }
