@@ -88,6 +88,8 @@ struct ColStore {  // a device buffer that holds column storage (int32 rows)
 struct ReduceState {
   int32_t* act = nullptr;      // active list buffers (which one is current: device state)
   int32_t* act2 = nullptr;
+  int32_t* alen = nullptr;     // per slot: the column's stored length (both lists)
+  int32_t* alen2 = nullptr;
   int64_t act_cap = 0;
   void* meta = nullptr;        // per id: ColMeta (rows, length, flags, clearing mark)
   int32_t** nxt_ptr = nullptr; // per active slot: new location

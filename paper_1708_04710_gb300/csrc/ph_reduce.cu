@@ -52,6 +52,8 @@ constexpr int kSpinLimit = 1 << 22;  // iterations of a look-back wait before it
 struct DevState {
   int32_t* act;   // active ids, ascending
   int32_t* act2;  // next active list
+  int32_t* alen;   // per slot of act: its column's stored length (ColMeta::len)
+  int32_t* alen2;  // the same for act2
   int64_t n_act;
   int32_t* arena[2];  // pass p writes its survivors into arena[p & 1]
   int64_t arena_cap[2];
@@ -146,6 +148,8 @@ struct RArgs {
 struct PV {
   int32_t* act;
   int32_t* act2;
+  int32_t* alen;
+  int32_t* alen2;
   int64_t n_act;
   int64_t ntiles;
   int64_t nchunks;
@@ -162,6 +166,8 @@ __device__ __forceinline__ PV pass_view(const DevState* ds) {
   PV v;
   v.act = ds->act;
   v.act2 = ds->act2;
+  v.alen = ds->alen;
+  v.alen2 = ds->alen2;
   v.n_act = ds->n_act;
   v.ntiles = (v.n_act + kRTile - 1) / kRTile;
   v.nchunks = (v.n_act + kThreads - 1) / kThreads;
@@ -501,9 +507,10 @@ __global__ void k_p1_tiles(RArgs a) {
     }
 #pragma unroll
     for (int it = 0; it < kRItems; it++) {
+      const int64_t e = tile0 + it * kThreads + threadIdx.x;
       l[it] = j[it] >= 0 ? a.low[j[it]] : -1;
       sg[it] = j[it] >= 0 ? seg_of(a, j[it]) : INT32_MAX;
-      n[it] = j[it] >= 0 ? a.meta[j[it]].len : 0;
+      n[it] = j[it] >= 0 ? v.alen[e] : 0;
     }
 #pragma unroll
     for (int it = 0; it < kRItems; it++) {
@@ -585,14 +592,12 @@ __global__ void k_mark(RArgs a) {
     for (int64_t c = tile * kRItems; c < chunk0; c++) carry = segmax_combine(carry, a.chunk_sm[c]);
     const int64_t e0 = chunk0 * kThreads + (int64_t)threadIdx.x * kMI;
     int32_t j[kMI], l[kMI], sg[kMI], s[kMI], b[kMI];
-    uint8_t f[kMI];
 #pragma unroll
     for (int i = 0; i < kMI; i++) j[i] = e0 + i < v.n_act ? v.act[e0 + i] : -1;
 #pragma unroll
     for (int i = 0; i < kMI; i++) {
       l[i] = j[i] >= 0 ? a.low[j[i]] : -1;
       sg[i] = j[i] >= 0 ? seg_of(a, j[i]) : INT32_MAX;
-      f[i] = j[i] >= 0 ? a.meta[j[i]].flags : 0;
       b[i] = j[i] >= 0 ? a.beta[j[i]] : -1;
     }
 #pragma unroll
@@ -617,19 +622,23 @@ __global__ void k_mark(RArgs a) {
       if (j[i] < 0) continue;
       const int64_t e = e0 + i;
       a.src_e[e] = s[i] != j[i] ? s[i] : -1;  // Phase II reads it in list order
+      // an active column carries no flag (proven, final and cleared columns leave the active
+      // list in the pass that marks them; the new-pivot mark goes with them), so the marks below
+      // are stored without a load
+      (void)PH_DCHECK(&a.ds->debug_fault, a.meta[j[i]].flags == 0, 7);
       if (l[i] < 0) {
-        a.meta[j[i]].flags = f[i] | F_FINAL;
+        a.meta[j[i]].flags = F_FINAL;
         n_zero++;
       } else {
         const int32_t P = (pre.seg == x[i].seg) ? pre.val : -1;
         const bool leftmost = s[i] == j[i];
         if (leftmost && (l[i] == b[i] || l[i] > P)) {
-          a.meta[j[i]].flags = f[i] | F_PROVEN | F_NEWPIV;
+          a.meta[j[i]].flags = F_PROVEN | F_NEWPIV;
           a.owner[l[i]] = j[i];
           a.meta[l[i]].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
           n_piv++;
         } else if (a.cor10 && b[i] < 0 && l[i] < a.first_unp[sg[i] - a.nc]) {
-          a.meta[j[i]].flags = f[i] | F_FINAL;  // Corollary 10, zero case
+          a.meta[j[i]].flags = F_FINAL;  // Corollary 10, zero case
           n_c10++;
         } else if (a.predict && b[i] >= 0 && a.pred[j[i]] < 0) {
           const int32_t pi = predicted_low(a, b[i], l[i]);
@@ -1561,15 +1570,20 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
   // ---- the survivors' places in the next active list
   if constexpr (kWarp) {
     const int64_t pre = look_back(a, pass, chunk, n_surv);
-    if (jb.surv && PH_DCHECK(&a.ds->debug_fault, pre + rank < v.n_act, 5)) v.act2[pre + rank] = jb.j;
+    if (jb.surv && PH_DCHECK(&a.ds->debug_fault, pre + rank < v.n_act, 5)) {
+      v.act2[pre + rank] = jb.j;
+      v.alen2[pre + rank] = o_len;
+    }
   } else {
     if (threadIdx.x < 32) {
       const int64_t pre = look_back(a, pass, chunk, n_surv);
       if (threadIdx.x == 0) s_prefix[0] = pre;
     }
     __syncthreads();
-    if (jb.surv && PH_DCHECK(&a.ds->debug_fault, s_prefix[0] + rank < v.n_act, 5))
+    if (jb.surv && PH_DCHECK(&a.ds->debug_fault, s_prefix[0] + rank < v.n_act, 5)) {
       v.act2[s_prefix[0] + rank] = jb.j;
+      v.alen2[s_prefix[0] + rank] = o_len;
+    }
   }
   // ---- publish: in place for targets and zeroed columns, through k_commit for the others
   if (jb.j >= 0) {
@@ -1774,6 +1788,9 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
     int32_t* t = ds->act;
     ds->act = ds->act2;
     ds->act2 = t;
+    t = ds->alen;
+    ds->alen = ds->alen2;
+    ds->alen2 = t;
     if (ds->totals[1] == 0) {
       ds->status = ST_DONE;
       ds->passes = p;
@@ -1817,7 +1834,7 @@ struct InitLayout {
 // col_off: the columns of a loaded matrix (any length); null: d + 1 rows at a fixed stride
 __global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0,
                               const int64_t* __restrict__ col_off, ColMeta* meta, int32_t* low,
-                              int32_t* act, int32_t* owner) {
+                              int32_t* act, int32_t* alen, int32_t* owner) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < m;
        x += (int64_t)gridDim.x * blockDim.x) {
     int d = 0;
@@ -1835,6 +1852,7 @@ __global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0,
     meta[x] = mx;
     low[x] = n > 0 ? c[n - 1] : -1;  // largest row of the unreduced column
     act[x] = (int32_t)x;
+    alen[x] = n;
     owner[x] = -1;
   }
 }
@@ -2011,6 +2029,8 @@ void reduce_init(ph_ctx* ctx) {
   const int64_t m = ctx->m;
   rs.act = alloc_n<int32_t>(ctx, m);
   rs.act2 = alloc_n<int32_t>(ctx, m);
+  rs.alen = alloc_n<int32_t>(ctx, m);
+  rs.alen2 = alloc_n<int32_t>(ctx, m);
   rs.act_cap = m;
   rs.meta = alloc_n<ColMeta>(ctx, m);
   rs.nxt_ptr = alloc_n<int32_t*>(ctx, m);
@@ -2056,7 +2076,7 @@ void reduce_init(ph_ctx* ctx) {
   }
   k_reduce_init<<<grid_for(ctx, m, kThreads), kThreads, 0, st>>>(
       m, L, ctx->rows0, ctx->col_off, static_cast<ColMeta*>(rs.meta), ctx->low, rs.act,
-      rs.owner);
+      rs.alen, rs.owner);
   PH_CHECK_LAUNCH();
   // first arenas: pass 0 needs at most the boundary matrix twice over
   // passes 0 and 1 need about the same; later passes less (they grow on demand otherwise)
@@ -2075,6 +2095,8 @@ void reduce_init(ph_ctx* ctx) {
   h = DevState{};
   h.act = rs.act;
   h.act2 = rs.act2;
+  h.alen = rs.alen;
+  h.alen2 = rs.alen2;
   h.n_act = m;
   for (int i = 0; i < 2; i++) {
     h.arena[i] = rs.arena[i].p;
@@ -2460,7 +2482,7 @@ void free_reduce_state(ph_ctx* ctx) {
     if (rs.graph_exec[d]) cudaGraphExecDestroy(rs.graph_exec[d]);
     if (rs.graph[d]) cudaGraphDestroy(rs.graph[d]);
   }
-  for (void* p : {(void*)rs.act, (void*)rs.act2, rs.meta,
+  for (void* p : {(void*)rs.act, (void*)rs.act2, (void*)rs.alen, (void*)rs.alen2, rs.meta,
                   (void*)rs.nxt_ptr, (void*)rs.nxt_len, (void*)rs.owner, (void*)rs.tab,
                   (void*)rs.first_unp, rs.tiles, rs.dstate,
                   rs.look, rs.dlist, rs.src_e, (void*)rs.unp_bits, (void*)rs.unp_words,
