@@ -95,7 +95,7 @@ struct ReduceState {
   int32_t** nxt_ptr = nullptr; // per active slot: new location
   int32_t* nxt_len = nullptr;
   int32_t* owner = nullptr;    // per row id: proven pivot with that low, -1
-  int32_t* tab = nullptr;      // per row id: left-most column with that low (this pass)
+  int32_t* tab = nullptr;      // two tables per row id: left-most column with that low (pass p: p & 1)
   int32_t* first_unp = nullptr;// per segment: first row id not known to be paired
   void* tiles = nullptr;       // scan scratch
   void* look = nullptr;        // look-back states of the survivor scan

@@ -2,10 +2,13 @@
 //
 // One pass = one cycle of the outer loop of Algorithm 2. Every decision of a pass is taken from
 // the state at its start, so the result of a pass does not depend on thread scheduling:
-//   k_tab_init   tab[i] <- owner[i] (proven pivot with low i); first row of each (cloud, dim)
-//                that is not known to be paired (for Corollary 10).
-//   k_tab        tab[low(j)] <- min j over the active columns (atomicMin): the left-most column
-//                with each low, which defines the neighbour sets N(j) (Eq. neighbours).
+//   k_tab_init   the next pass's table: tab'[i] <- owner[i] (proven pivot with low i); first
+//                row of each (cloud, dim) that is not known to be paired (for Corollary 10).
+//   (table)      tab[low(j)] = min j over the active columns and the pivots: the left-most
+//                column with each low, which defines the neighbour sets N(j) (Eq. neighbours).
+//                Two tables alternate between passes: each pass's new pivots (k_mark) and
+//                survivors with their new lows (k_add, atomicMin) fill the next pass's, so no
+//                kernel gathers the lows again; k_tab builds the first pass's at set-up.
 //   k_p1_tiles   Phase I (Algorithm 5) as a segmented exclusive prefix-max over the active
 //                columns of each (cloud, dim): P_j = largest low of an earlier colliding column;
 //                also upper bounds of the space this pass can need. The block that finishes
@@ -56,6 +59,7 @@ struct DevState {
   int32_t* alen2;  // the same for act2
   int64_t n_act;
   int32_t* arena[2];  // pass p writes its survivors into arena[p & 1]
+  int32_t* tab[2];    // pass p reads its left-most-column table tab[p & 1], builds tab[(p+1) & 1]
   int64_t arena_cap[2];
   int32_t* piv_base;  // current chunk of the pivot store
   int64_t piv_cap;
@@ -111,7 +115,6 @@ struct RArgs {
   int32_t** nxt_ptr;
   int32_t* nxt_len;
   int32_t* owner;
-  int32_t* tab;
   int32_t* first_unp;
   const int32_t* seg;
   int64_t rows_end;
@@ -160,6 +163,8 @@ struct PV {
   int dense_on;
   int64_t arena_next_cap;  // words of arena_next and of the pivot store's chunk (bounds checks)
   int64_t piv_cap;
+  int32_t* tab;       // per row: the left-most active column with that low (or its pivot)
+  int32_t* tab_next;  // the same for the next pass, built during this one
 };
 
 __device__ __forceinline__ PV pass_view(const DevState* ds) {
@@ -178,6 +183,8 @@ __device__ __forceinline__ PV pass_view(const DevState* ds) {
   v.dense_on = ds->dense_on;
   v.arena_next_cap = ds->arena_cap[ds->pass & 1];
   v.piv_cap = ds->piv_cap;
+  v.tab = ds->tab[ds->pass & 1];
+  v.tab_next = ds->tab[(ds->pass + 1) & 1];
   return v;
 }
 
@@ -218,6 +225,7 @@ __global__ void k_tab_init(RArgs a) {
   pdl_trigger();
   DevState* ds = a.ds;
   if (ds->status != ST_RUN) return;
+  const PV v = pass_view(ds);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ds->bound_words = 0;
     ds->bound_piv = 0;
@@ -234,7 +242,7 @@ __global__ void k_tab_init(RArgs a) {
     bool unpaired = false;
     if (x < a.rows_end) {
       int32_t o = a.owner[x];
-      a.tab[x] = o < 0 ? INT32_MAX : o;
+      v.tab_next[x] = o < 0 ? INT32_MAX : o;
       bool paired = (a.meta[x].flags & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
       if (!paired) atomicMin(&a.first_unp[a.seg[x]], (int32_t)x);
       unpaired = !paired;
@@ -307,7 +315,7 @@ __global__ void k_tab(RArgs a) {
 #pragma unroll
     for (int k = 0; k < kTI; k++) {
       if (l[k] >= 0 && PH_DCHECK(&a.ds->debug_fault, l[k] < a.rows_end, 1)) {
-        if (a.tab[l[k]] > j[k]) atomicMin(&a.tab[l[k]], j[k]);
+        if (v.tab[l[k]] > j[k]) atomicMin(&v.tab[l[k]], j[k]);
         if (!a.meta[l[k]].low_seen) a.meta[l[k]].low_seen = 1;  // for the essential estimate
       }
     }
@@ -387,16 +395,6 @@ __device__ __forceinline__ bool goes_dense(const RArgs& a, int32_t j, int64_t n)
 // ------------------------------------------------------------------------------------------
 // Phase I scan
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ SegMax p1_value(const RArgs& a, const PV& v, int64_t e) {
-  if (e >= v.n_act) return SegMax{INT32_MAX, -1};
-  int32_t j = v.act[e];
-  int32_t l = a.low[j];
-  SegMax r;
-  r.seg = a.seg[j];
-  r.val = (l >= 0 && a.tab[l] != j) ? l : -1;  // low of a colliding column
-  return r;
-}
-
 // exclusive block scan with carry-in; returns the exclusive prefix, sets the running total
 __device__ __forceinline__ SegMax block_scan_segmax(SegMax v, SegMax carry, SegMax* sh,
                                                     SegMax& total) {
@@ -514,7 +512,7 @@ __global__ void k_p1_tiles(RArgs a) {
     }
 #pragma unroll
     for (int it = 0; it < kRItems; it++) {
-      const int32_t s = l[it] >= 0 ? a.tab[l[it]] : -1;
+      const int32_t s = l[it] >= 0 ? v.tab[l[it]] : -1;
       const bool collide = l[it] >= 0 && s != j[it];
       // a column's reservation is its stored words: its rows, or its bitmap with the header
       bw += stored_words(n[it]);
@@ -603,7 +601,7 @@ __global__ void k_mark(RArgs a) {
 #pragma unroll
     for (int i = 0; i < kMI; i++) {
       if (!PH_DCHECK(&a.ds->debug_fault, l[i] < a.rows_end, 2)) l[i] = -1, j[i] = -1;
-      s[i] = l[i] >= 0 ? a.tab[l[i]] : -1;
+      s[i] = l[i] >= 0 ? v.tab[l[i]] : -1;
     }
     // Phase I values: the low of a colliding column, in its (cloud, dim) segment
     SegMax x[kMI];
@@ -635,6 +633,7 @@ __global__ void k_mark(RArgs a) {
         if (leftmost && (l[i] == b[i] || l[i] > P)) {
           a.meta[j[i]].flags = F_PROVEN | F_NEWPIV;
           a.owner[l[i]] = j[i];
+          atomicMin(&v.tab_next[l[i]], j[i]);  // its row's pivot from the next pass on
           a.meta[l[i]].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
           n_piv++;
         } else if (a.cor10 && b[i] < 0 && l[i] < a.first_unp[sg[i] - a.nc]) {
@@ -1274,6 +1273,15 @@ __device__ __forceinline__ int lane_merge_job(const int32_t* __restrict__ in, in
   return q;
 }
 
+// A survivor j with low l enters the next pass's left-most-column table (and l is marked as a
+// low seen, for the essential estimate): the table is built while the pass's additions write the
+// new lows, so no kernel of the next pass gathers the lows for it
+__device__ __forceinline__ void next_tab(const RArgs& a, const PV& v, int32_t l, int32_t j) {
+  if (l < 0 || !PH_DCHECK(&a.ds->debug_fault, l < a.rows_end, 1)) return;
+  if (v.tab_next[l] > j) atomicMin(&v.tab_next[l], j);
+  if (!a.meta[l].low_seen) a.meta[l].low_seen = 1;
+}
+
 // Phase II for one chunk of the active list (128 slots of a block, or 32 of a warp). Survivors
 // get their place in the next active list from a block (or warp) scan plus the look-back, and
 // their rows a slot of the next arena from one atomic per chunk. New pivots are copied to the
@@ -1419,7 +1427,10 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     }
     o_ptr = slot;
     o_len = len;
-    if (B) a.low[jb.j] = last;
+    if (B) {
+      a.low[jb.j] = last;
+      next_tab(a, v, last, jb.j);
+    }
   }
   const unsigned smask = __ballot_sync(0xffffffffu, cls == 3);
   if (smask) {
@@ -1511,7 +1522,10 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     if (staged) {
       o_ptr = slot;
       o_len = S.jcnt[ord];
-      if (B) a.low[jb.j] = S.jlow[ord];
+      if (B) {
+        a.low[jb.j] = S.jlow[ord];
+        next_tab(a, v, S.jlow[ord], jb.j);
+      }
     }
     // merges too long to stage: straight from global memory into their slot
     unsigned bmask = __ballot_sync(0xffffffffu, big);
@@ -1532,7 +1546,10 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
         len = wna;
       }
       if (lane == src) {
-        if (B) a.low[jb.j] = last;
+        if (B) {
+          a.low[jb.j] = last;
+          next_tab(a, v, last, jb.j);
+        }
         o_ptr = wd;
         o_len = len;
       }
@@ -1565,6 +1582,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       o_ptr = wd;
       o_len = rows ? dense_len(words) : 0;  // a zero column stores nothing
       a.low[jb.j] = low;
+      next_tab(a, v, low, jb.j);
     }
   }
   // ---- the survivors' places in the next active list
@@ -1586,6 +1604,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     }
   }
   // ---- publish: in place for targets and zeroed columns, through k_commit for the others
+  if (jb.surv && B == nullptr) next_tab(a, v, a.low[jb.j], jb.j);  // its low stays
   if (jb.j >= 0) {
     if (jb.surv && jb.target) {
       a.meta[jb.j].ptr = o_ptr;
@@ -1834,7 +1853,7 @@ struct InitLayout {
 // col_off: the columns of a loaded matrix (any length); null: d + 1 rows at a fixed stride
 __global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0,
                               const int64_t* __restrict__ col_off, ColMeta* meta, int32_t* low,
-                              int32_t* act, int32_t* alen, int32_t* owner) {
+                              int32_t* act, int32_t* alen, int32_t* owner, int32_t* tab0) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < m;
        x += (int64_t)gridDim.x * blockDim.x) {
     int d = 0;
@@ -1854,6 +1873,7 @@ __global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0,
     act[x] = (int32_t)x;
     alen[x] = n;
     owner[x] = -1;
+    tab0[x] = INT32_MAX;  // the first pass's table before its atomics: no pivot yet
   }
 }
 
@@ -1868,7 +1888,6 @@ static RArgs make_args(ph_ctx* ctx) {
   a.nxt_ptr = rs.nxt_ptr;
   a.nxt_len = rs.nxt_len;
   a.owner = rs.owner;
-  a.tab = rs.tab;
   a.first_unp = rs.first_unp;
   a.seg = ctx->seg;
   a.rows_end = ctx->dimoff[ctx->max_dim];
@@ -1961,7 +1980,6 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (m + per_block - 1) / per_block));
   };
   launch_k(ctx, true, k_tab_init, grid_for(ctx, a.rows_end, kThreads), kThreads, 0, st, a);
-  launch_k(ctx, true, k_tab, blocks(sms * 8, kThreads * kTabItems), kThreads, 0, st, a);
   launch_k(ctx, true, k_p1_tiles, blocks(sms * 8, kRTile), kThreads, 0, st, a);
   launch_k(ctx, true, k_mark<kMarkItems>, blocks(sms * 8, kThreads * kMarkItems), kThreads, 0, st,
            a);
@@ -2036,7 +2054,7 @@ void reduce_init(ph_ctx* ctx) {
   rs.nxt_ptr = alloc_n<int32_t*>(ctx, m);
   rs.nxt_len = alloc_n<int32_t>(ctx, m);
   rs.owner = alloc_n<int32_t>(ctx, m);
-  rs.tab = alloc_n<int32_t>(ctx, m);
+  rs.tab = alloc_n<int32_t>(ctx, 2 * std::max<int64_t>(m, 1));  // two alternating tables
   int nseg = (int)ctx->seg_start.size() - 1;
   rs.first_unp = alloc_n<int32_t>(ctx, nseg);
   PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, nseg * sizeof(int32_t), st));  // above every id
@@ -2076,7 +2094,7 @@ void reduce_init(ph_ctx* ctx) {
   }
   k_reduce_init<<<grid_for(ctx, m, kThreads), kThreads, 0, st>>>(
       m, L, ctx->rows0, ctx->col_off, static_cast<ColMeta*>(rs.meta), ctx->low, rs.act,
-      rs.alen, rs.owner);
+      rs.alen, rs.owner, rs.tab);
   PH_CHECK_LAUNCH();
   // first arenas: pass 0 needs at most the boundary matrix twice over
   // passes 0 and 1 need about the same; later passes less (they grow on demand otherwise)
@@ -2101,6 +2119,7 @@ void reduce_init(ph_ctx* ctx) {
   for (int i = 0; i < 2; i++) {
     h.arena[i] = rs.arena[i].p;
     h.arena_cap[i] = rs.arena[i].cap;
+    h.tab[i] = rs.tab + i * std::max<int64_t>(m, 1);
   }
   h.piv_base = c.p;
   h.piv_cap = c.cap;
@@ -2125,6 +2144,12 @@ void reduce_init(ph_ctx* ctx) {
                        : ctx->opts.narrow_chunks_below;
   h.narrow_on = 0;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  // the first pass's table (the later ones are built by the pass before)
+  {
+    const RArgs a0 = make_args(ctx);
+    launch_k(ctx, false, k_tab, (unsigned)grid_for(ctx, m, kThreads * kTabItems), kThreads, 0, st,
+             a0);
+  }
   const void* add_kernels[ReduceState::kAddVariants] = {
       (const void*)k_add<false, 0, false>,  (const void*)k_add<true, 0, false>,
       (const void*)k_add<false, 32, false>, (const void*)k_add<true, 32, false>,
@@ -2262,7 +2287,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     PH_CUDA(cudaStreamSynchronize(st));
     if (use_graph) {  // kernels per executed pass of the graph's loop
       const int32_t last = (h.status == ST_DONE || h.status == ST_CAPPED) ? h.passes : h.pass;
-      const int per_pass = 6 + (ctx->opts.collect_stats ? 1 : 0);
+      const int per_pass = 5 + (ctx->opts.collect_stats ? 1 : 0);
       ctx->launches += per_pass * (int64_t)(last - first_pass + 1);
     }
     if (h.status == ST_RUN) continue;
