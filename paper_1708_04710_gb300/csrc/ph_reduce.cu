@@ -2,13 +2,13 @@
 //
 // One pass = one cycle of the outer loop of Algorithm 2. Every decision of a pass is taken from
 // the state at its start, so the result of a pass does not depend on thread scheduling:
-//   k_tab_init   the next pass's table: tab'[i] <- owner[i] (proven pivot with low i); first
-//                row of each (cloud, dim) that is not known to be paired (for Corollary 10).
 //   (table)      tab[low(j)] = min j over the active columns and the pivots: the left-most
 //                column with each low, which defines the neighbour sets N(j) (Eq. neighbours).
-//                Two tables alternate between passes: each pass's new pivots (k_mark) and
-//                survivors with their new lows (k_add, atomicMin) fill the next pass's, so no
-//                kernel gathers the lows again; k_tab builds the first pass's at set-up.
+//                Two tables alternate between passes: the pass before resets one to the proven
+//                pivots (owner), and its new pivots (k_mark) and its survivors with their new
+//                lows (k_add, atomicMin) fill it, so no kernel gathers the lows again; k_tab
+//                builds the first pass's at set-up. With it, the first row of each (cloud, dim)
+//                that is not known to be paired (for Corollary 10).
 //   k_p1_tiles   Phase I (Algorithm 5) as a segmented exclusive prefix-max over the active
 //                columns of each (cloud, dim): P_j = largest low of an earlier colliding column;
 //                also upper bounds of the space this pass can need. The block that finishes
@@ -33,10 +33,10 @@
 //                between them at most three times per reduction.
 //   (p sets)     With Phase II limited to p neighbour sets (Sec. 3.4), k_set_* rank the sets
 //                between k_mark and k_add and hold back the other targets.
-//   k_commit     publishes the new locations of the columns other jobs may have been reading;
-//                its last block ends the pass: the next active list, convergence (no collision
-//                left, Thm 8), the pass cap and time bound, and inside a CUDA graph the
-//                conditional that repeats the pass.
+//   k_commit     publishes the new locations of the columns other jobs may have been reading
+//                and prepares the next pass's row state; its last block ends the pass: the
+//                next active list, convergence (no collision left, Thm 8), the pass cap and
+//                time bound, and inside a CUDA graph the conditional that repeats the pass.
 // All per-pass state lives in device memory (DevState), so the same kernel sequence runs either
 // from a host loop or as the body of a graph's conditional while node.
 #include <algorithm>
@@ -220,20 +220,15 @@ __device__ __forceinline__ bool last_block(unsigned int* done, unsigned int part
 }
 
 // ------------------------------------------------------------------------------------------
-__global__ void k_tab_init(RArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  DevState* ds = a.ds;
-  if (ds->status != ST_RUN) return;
-  const PV v = pass_view(ds);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ds->bound_words = 0;
-    ds->bound_piv = 0;
-    ds->queue = 0;
-    ds->arena_used = 0;
-    ds->n_deferred = 0;
-    ds->totals[0] = ds->totals[1] = 0;
-  }
+// The row state pass q reads, from the pivots, flags and beta as they stand when the pass before
+// it ends (k_commit; at set-up for the first pass): the reset, to the proven pivots (owner), of
+// the table that pass q's additions fill for pass q + 1; the first row of each (cloud, dim)
+// segment that is not known to be paired (Corollary 10; two copies alternate between passes);
+// and the unpaired bitmap (pair predictions). Every block of the grid takes part; the grid's last
+// block then finishes it with rows_of_pass_last.
+__device__ void rows_of_pass(const RArgs& a, int32_t q) {
+  int32_t* tab_reset = a.ds->tab[(q + 1) & 1];
+  int32_t* fu = a.first_unp + (int64_t)(q & 1) * a.nseg;
   // warp-uniform loop: each iteration a warp covers 32 consecutive rows, one bitmap word
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); x0 < a.rows_end;
@@ -242,9 +237,9 @@ __global__ void k_tab_init(RArgs a) {
     bool unpaired = false;
     if (x < a.rows_end) {
       int32_t o = a.owner[x];
-      v.tab_next[x] = o < 0 ? INT32_MAX : o;
+      tab_reset[x] = o < 0 ? INT32_MAX : o;
       bool paired = (a.meta[x].flags & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
-      if (!paired) atomicMin(&a.first_unp[a.seg[x]], (int32_t)x);
+      if (!paired) atomicMin(&fu[a.seg[x]], (int32_t)x);
       unpaired = !paired;
     }
     if (a.predict) {
@@ -252,7 +247,12 @@ __global__ void k_tab_init(RArgs a) {
       if ((threadIdx.x & 31) == 0) a.unp_bits[x0 >> 5] = w;
     }
   }
-  if (a.predict && last_block(&ds->blocks_done, gridDim.x)) {  // prefix counts of the words
+}
+
+// by the last block: the bitmap's prefix counts per word, and the first-unpaired copy of pass
+// q + 1 cleared for the atomics at the end of pass q
+__device__ void rows_of_pass_last(const RArgs& a, int32_t q) {
+  if (a.predict) {
     __shared__ int64_t sh[kWarps + 1];
     const int64_t nwords = (a.rows_end + 31) / 32;
     int64_t carry = 0;
@@ -264,10 +264,19 @@ __global__ void k_tab_init(RArgs a) {
       if (w < nwords) a.unp_words[w] = (int32_t)(carry + ex);
       carry += tot;
     }
-    if (threadIdx.x == 0) {
-      a.unp_words[nwords] = (int32_t)carry;
-      ds->blocks_done = 0;
-    }
+    if (threadIdx.x == 0) a.unp_words[nwords] = (int32_t)carry;
+  }
+  int32_t* fu_next = a.first_unp + (int64_t)((q + 1) & 1) * a.nseg;
+  for (int i = threadIdx.x; i < a.nseg; i += blockDim.x) fu_next[i] = INT32_MAX;
+}
+
+// set-up: the first pass's row state
+__global__ void k_rows_first(RArgs a) {
+  const int32_t q = a.ds->pass;
+  rows_of_pass(a, q);
+  if (last_block(&a.ds->blocks_done, gridDim.x)) {
+    rows_of_pass_last(a, q);
+    if (threadIdx.x == 0) a.ds->blocks_done = 0;
   }
 }
 
@@ -581,6 +590,7 @@ __global__ void k_mark(RArgs a) {
   pdl_trigger();
   if (a.ds->status != ST_RUN) return;
   const PV v = pass_view(a.ds);
+  const int32_t* fu = a.first_unp + (int64_t)(a.ds->pass & 1) * a.nseg;  // this pass's copy
   int64_t n_zero = 0, n_piv = 0, n_c10 = 0, n_pred = 0, n_empty = 0;
   const int64_t nit = (v.n_act + (int64_t)kThreads * kMI - 1) / ((int64_t)kThreads * kMI);
   for (int64_t it = blockIdx.x; it < nit; it += gridDim.x) {
@@ -636,7 +646,7 @@ __global__ void k_mark(RArgs a) {
           atomicMin(&v.tab_next[l[i]], j[i]);  // its row's pivot from the next pass on
           a.meta[l[i]].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
           n_piv++;
-        } else if (a.cor10 && b[i] < 0 && l[i] < a.first_unp[sg[i] - a.nc]) {
+        } else if (a.cor10 && b[i] < 0 && l[i] < fu[sg[i] - a.nc]) {
           a.meta[j[i]].flags = F_FINAL;  // Corollary 10, zero case
           n_c10++;
         } else if (a.predict && b[i] >= 0 && a.pred[j[i]] < 0) {
@@ -1273,13 +1283,15 @@ __device__ __forceinline__ int lane_merge_job(const int32_t* __restrict__ in, in
   return q;
 }
 
-// A survivor j with low l enters the next pass's left-most-column table (and l is marked as a
-// low seen, for the essential estimate): the table is built while the pass's additions write the
-// new lows, so no kernel of the next pass gathers the lows for it
+// A survivor j with low l enters the next pass's left-most-column table (and a new low l is
+// marked as seen, for the essential estimate; a low that stays was marked when it appeared): the
+// table is built while the pass's additions write the new lows, so no kernel of the next pass
+// gathers the lows for it
+template <bool kNewLow>
 __device__ __forceinline__ void next_tab(const RArgs& a, const PV& v, int32_t l, int32_t j) {
   if (l < 0 || !PH_DCHECK(&a.ds->debug_fault, l < a.rows_end, 1)) return;
   if (v.tab_next[l] > j) atomicMin(&v.tab_next[l], j);
-  if (!a.meta[l].low_seen) a.meta[l].low_seen = 1;
+  if (kNewLow && !a.meta[l].low_seen) a.meta[l].low_seen = 1;
 }
 
 // Phase II for one chunk of the active list (128 slots of a block, or 32 of a warp). Survivors
@@ -1429,7 +1441,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     o_len = len;
     if (B) {
       a.low[jb.j] = last;
-      next_tab(a, v, last, jb.j);
+      next_tab<true>(a, v, last, jb.j);
     }
   }
   const unsigned smask = __ballot_sync(0xffffffffu, cls == 3);
@@ -1524,7 +1536,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       o_len = S.jcnt[ord];
       if (B) {
         a.low[jb.j] = S.jlow[ord];
-        next_tab(a, v, S.jlow[ord], jb.j);
+        next_tab<true>(a, v, S.jlow[ord], jb.j);
       }
     }
     // merges too long to stage: straight from global memory into their slot
@@ -1548,7 +1560,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       if (lane == src) {
         if (B) {
           a.low[jb.j] = last;
-          next_tab(a, v, last, jb.j);
+          next_tab<true>(a, v, last, jb.j);
         }
         o_ptr = wd;
         o_len = len;
@@ -1582,7 +1594,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
       o_ptr = wd;
       o_len = rows ? dense_len(words) : 0;  // a zero column stores nothing
       a.low[jb.j] = low;
-      next_tab(a, v, low, jb.j);
+      next_tab<true>(a, v, low, jb.j);
     }
   }
   // ---- the survivors' places in the next active list
@@ -1604,7 +1616,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     }
   }
   // ---- publish: in place for targets and zeroed columns, through k_commit for the others
-  if (jb.surv && B == nullptr) next_tab(a, v, a.low[jb.j], jb.j);  // its low stays
+  if (jb.surv && B == nullptr) next_tab<false>(a, v, a.low[jb.j], jb.j);  // its low stays
   if (jb.j >= 0) {
     if (jb.surv && jb.target) {
       a.meta[jb.j].ptr = o_ptr;
@@ -1743,18 +1755,29 @@ __global__ void k_ess_flags(int64_t lo, int64_t hi, const ColMeta* __restrict__ 
 // the deferred column updates: new pivots (now in the pivot store) and left-most survivors
 __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int in_graph);
 
-// the deferred column updates, then (last block) the end of the pass
+// the counters a pass accumulates, cleared for the next one
+__host__ __device__ inline void reset_counters(DevState* ds) {
+  ds->bound_words = 0;
+  ds->bound_piv = 0;
+  ds->queue = 0;
+  ds->arena_used = 0;
+  ds->n_deferred = 0;
+  ds->totals[0] = ds->totals[1] = 0;
+}
+
+// the deferred column updates and the next pass's row state, then (last block) the end of the
+// pass and the reset of the per-pass counters. A pass stopped before any change (ST_HOST) runs
+// again on the row state it had, so neither is touched then (the host resets the counters).
 __global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
   pdl_wait();
-  // as many blocks as the deferred list needs take part; block 0 always does (it ends the pass)
-  const int64_t n = a.ds->status == ST_RUN ? (int64_t)a.ds->n_deferred : 0;
-  const unsigned parts =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>(gridDim.x, (n + blockDim.x - 1) / blockDim.x));
-  if (blockIdx.x >= parts) return;
+  DevState* ds = a.ds;
+  const bool run = ds->status == ST_RUN;
+  const int32_t p = ds->pass;
+  const int64_t n = run ? (int64_t)ds->n_deferred : 0;
   if (n > 0) {
-    const PV v = pass_view(a.ds);
+    const PV v = pass_view(ds);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)parts * blockDim.x) {
+         i += (int64_t)gridDim.x * blockDim.x) {
       const int32_t e = a.dlist[i];
       const int32_t j = v.act[e];
       a.meta[j].ptr = a.nxt_ptr[e];
@@ -1762,12 +1785,13 @@ __global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph)
       a.meta[j].flags &= (uint8_t)~F_NEWPIV;
     }
   }
-  if (last_block(&a.ds->blocks_done, parts)) {
-    // the first unpaired row of each segment is found afresh (atomicMin) by the next pass
-    for (int i = threadIdx.x; i < a.nseg; i += blockDim.x) a.first_unp[i] = INT32_MAX;
+  if (run) rows_of_pass(a, p + 1);
+  if (last_block(&ds->blocks_done, gridDim.x)) {
+    if (run) rows_of_pass_last(a, p + 1);
     if (threadIdx.x == 0) {
-      a.ds->blocks_done = 0;
+      ds->blocks_done = 0;
       end_of_pass(a, cond, in_graph);
+      if (run) reset_counters(ds);
     }
   }
 }
@@ -1979,7 +2003,6 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
   auto blocks = [&](int64_t full, int64_t per_block) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (m + per_block - 1) / per_block));
   };
-  launch_k(ctx, true, k_tab_init, grid_for(ctx, a.rows_end, kThreads), kThreads, 0, st, a);
   launch_k(ctx, true, k_p1_tiles, blocks(sms * 8, kRTile), kThreads, 0, st, a);
   launch_k(ctx, true, k_mark<kMarkItems>, blocks(sms * 8, kThreads * kMarkItems), kThreads, 0, st,
            a);
@@ -2056,8 +2079,8 @@ void reduce_init(ph_ctx* ctx) {
   rs.owner = alloc_n<int32_t>(ctx, m);
   rs.tab = alloc_n<int32_t>(ctx, 2 * std::max<int64_t>(m, 1));  // two alternating tables
   int nseg = (int)ctx->seg_start.size() - 1;
-  rs.first_unp = alloc_n<int32_t>(ctx, nseg);
-  PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, nseg * sizeof(int32_t), st));  // above every id
+  rs.first_unp = alloc_n<int32_t>(ctx, 2 * nseg);  // two copies, alternating between passes
+  PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, 2 * nseg * sizeof(int32_t), st));  // above every id
   int64_t ntiles = (m + kRTile - 1) / kRTile;
   rs.tiles_bytes = ntiles * (1 + kRItems) * sizeof(SegMax);
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
@@ -2144,9 +2167,11 @@ void reduce_init(ph_ctx* ctx) {
                        : ctx->opts.narrow_chunks_below;
   h.narrow_on = 0;
   PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  // the first pass's table (the later ones are built by the pass before)
+  // the first pass's row state and table (the later ones come from the pass before)
   {
     const RArgs a0 = make_args(ctx);
+    launch_k(ctx, false, k_rows_first, (unsigned)grid_for(ctx, a0.rows_end, kThreads), kThreads,
+             0, st, a0);
     launch_k(ctx, false, k_tab, (unsigned)grid_for(ctx, m, kThreads * kTabItems), kThreads, 0, st,
              a0);
   }
@@ -2287,7 +2312,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     PH_CUDA(cudaStreamSynchronize(st));
     if (use_graph) {  // kernels per executed pass of the graph's loop
       const int32_t last = (h.status == ST_DONE || h.status == ST_CAPPED) ? h.passes : h.pass;
-      const int per_pass = 5 + (ctx->opts.collect_stats ? 1 : 0);
+      const int per_pass = 4 + (ctx->opts.collect_stats ? 1 : 0);
       ctx->launches += per_pass * (int64_t)(last - first_pass + 1);
     }
     if (h.status == ST_RUN) continue;
@@ -2305,6 +2330,7 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
         rs.add_launches--;
       }
       serve_host_request(ctx, h);
+      reset_counters(&h);  // the pass runs again from its start
       PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
       continue;
     }
