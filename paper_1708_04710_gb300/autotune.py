@@ -1,6 +1,6 @@
 """Autotuner for the Phase II addition kernel.
 
-Five knobs shape the hot loop:
+Six knobs shape the hot loop:
 - ``staged_merge_max``: the longest merge that is still staged in shared memory (the threshold
   between the staged and the straight-from-memory merge);
 - ``add_blocks_per_sm``: persistent blocks per SM (the grid shape);
@@ -10,7 +10,9 @@ Five knobs shape the hot loop:
 - ``warp_chunks_below``: the active-list length below which a warp, not a block, claims a chunk
   of the work queue (0 = 4,194,304, -1 = never), the block shape of the work queue;
 - ``lane_merge_words``: the mean job length (target + source rows) up to which each lane merges
-  its own job, before the lanes share every job's merge pieces (0 = 20, -1 = pieces throughout).
+  its own job, before the lanes share every job's merge pieces (0 = 20, -1 = pieces throughout);
+- ``narrow_chunks_below``: the active-list length below which the warps take chunks of 8 columns
+  in the last passes (0 = 16 per warp of the grid, -1 = never).
 The tuner times full reductions of the caller's own filtration, one knob at a time (coordinate
 descent from the library defaults), and caches the winner per GPU model and workload class in a
 JSON file (``$PH_GB300_CACHE`` or ``~/.cache/ph_gb300/autotune.json``). Every option gives the
@@ -32,9 +34,10 @@ KNOBS = {
     "dense_threshold": (0, -1, 128, 1024),
     "warp_chunks_below": (0, -1, 1 << 20, 1 << 24),
     "lane_merge_words": (0, -1, 16, 40),
+    "narrow_chunks_below": (0, -1, 1 << 18),
 }
-DEFAULTS = {"staged_merge_max": 1024, "add_blocks_per_sm": 4,
-            "dense_threshold": 0, "warp_chunks_below": 0, "lane_merge_words": 0}
+DEFAULTS = {"staged_merge_max": 1024, "add_blocks_per_sm": 4, "dense_threshold": 0,
+            "warp_chunks_below": 0, "lane_merge_words": 0, "narrow_chunks_below": 0}
 
 
 def cache_path() -> Path:

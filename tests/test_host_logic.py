@@ -11,8 +11,8 @@ import pointclouds as pc
 def test_coordinate_descent_finds_separable_optimum():
     from paper_1708_04710_gb300.autotune import DEFAULTS, KNOBS, coordinate_descent
 
-    target = {"staged_merge_max": 512, "add_blocks_per_sm": 3,
-              "dense_threshold": -1, "warp_chunks_below": 1 << 20, "lane_merge_words": 16}
+    target = {"staged_merge_max": 512, "add_blocks_per_sm": 3, "dense_threshold": -1,
+              "warp_chunks_below": 1 << 20, "lane_merge_words": 16, "narrow_chunks_below": -1}
 
     def timer(o):  # separable cost with its minimum at `target`
         return 1.0 + sum(abs(KNOBS[k].index(o[k]) - KNOBS[k].index(target[k])) for k in KNOBS)
