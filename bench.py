@@ -351,6 +351,7 @@ def main():
         line["forms"] = compare_forms(ph, torch, dev)
         line["configs"] = other_configs(ph, torch, dev, peak, peak_kind)
         line["early"] = early_summary(ph, torch)
+        line["packed"] = packed_summary(ph, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         n_sample = 250
         ms, secs = cpu_oracle_sample(n_sample)
@@ -499,6 +500,49 @@ def other_configs(ph, torch, dev, peak, peak_kind):
                                                    "ms_per_launch", "launches_per_step")}}
         ctx.close()
         prof.close()
+    return out
+
+
+def packed_summary(ph, torch, dev):
+    """The bit-packed column path, timed on two small complexes: 24 random points to dimension 4
+    (55,454 simplices) and circle40 (10,700), each reduced with row lists only (dense_threshold
+    -1), the default threshold (0: a column goes bit-packed once its bitmap is the smaller form,
+    past 32 rows) and every addition past one row bit-packed (1). Per variant: the reduction's
+    median time (graph loop, 10 runs after 3 warm-ups), passes, and the additions computed on
+    bitmaps; the variants of a complex must agree on every low."""
+    out = {}
+    for name, x, k in (("rand24_dim4", pc.random_cloud(24, 3, 77), 4), ("circle40", pc.circle40(), 2)):
+        coords = torch.from_numpy(x).to(dev)
+        res = {"variants": {}}
+        lows = []
+        for var, thr in (("row_lists", -1), ("default", 0), ("forced", 1)):
+            ctx = ph.Context(dense_threshold=thr)
+            times = []
+            for it in range(3 + 10):
+                ctx.build_filtration(coords, None, k)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = ctx.reduce()
+                e1.record()
+                e1.synchronize()
+                if it >= 3:
+                    times.append(e0.elapsed_time(e1))
+            cnt = ph.Context(dense_threshold=thr, collect_stats=True)
+            cnt.build_filtration(coords, None, k)
+            cnt.reduce()
+            ps = cnt.pass_stats()
+            lows.append(cnt.filtration(0)["low"])
+            res["m"] = ctx.m
+            res["variants"][var] = {
+                "dense_threshold": thr, "reduce_ms": statistics.median(times),
+                "passes": st["passes"],
+                "packed_additions": int(ps[:, ph.PS_FIELDS.index("packed")].sum()),
+                "additions": int(ps[:, ph.PS_FIELDS.index("adds")].sum())}
+            ctx.close()
+            cnt.close()
+        res["same_lows"] = all(np.array_equal(lows[0], lw) for lw in lows[1:])
+        out[name] = res
     return out
 
 

@@ -544,15 +544,22 @@ __global__ void k_p1_tiles(RArgs a) {
       if (lane == 0) s_warp[it][warp] = val;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      SegMax carry{-1, -1};
-      for (int it = 0; it < kRItems; it++) {
-        SegMax c = s_warp[it][0];
-        for (int w = 1; w < kWarps; w++) c = segmax_combine(c, s_warp[it][w]);
-        a.chunk_sm[t * kRItems + it] = c;  // this chunk alone
-        carry = segmax_combine(carry, c);
+    if (threadIdx.x < 32) {  // lane k: chunk k over the warps; lane 0 folds the chunks in order
+      SegMax c{-1, -1};
+      if (lane < kRItems) {
+        c = s_warp[lane][0];
+        for (int w = 1; w < kWarps; w++) c = segmax_combine(c, s_warp[lane][w]);
+        a.chunk_sm[t * kRItems + lane] = c;  // this chunk alone
       }
-      a.tile_sm[t] = carry;
+      SegMax carry{-1, -1};
+#pragma unroll
+      for (int k = 0; k < kRItems; k++) {
+        SegMax ck;
+        ck.seg = __shfl_sync(0xffffffffu, c.seg, k);
+        ck.val = __shfl_sync(0xffffffffu, c.val, k);
+        carry = segmax_combine(carry, ck);
+      }
+      if (lane == 0) a.tile_sm[t] = carry;
     }
     __syncthreads();
   }
@@ -581,7 +588,7 @@ __global__ void k_p1_tiles(RArgs a) {
 // chunks of a tile); every gather of the iteration is issued before any is used. The
 // iteration's prefix is the tile's prefix combined with the aggregates of the tile's earlier
 // chunks; the slots' own prefixes come from a thread-local fold and one block scan.
-constexpr int kMarkItems = 2;
+constexpr int kMarkItems = 4;
 static_assert(kRItems % kMarkItems == 0, "a block iteration stays inside one Phase I tile");
 template <int kMI>
 __global__ void k_mark(RArgs a) {
