@@ -238,14 +238,15 @@ __device__ void rows_of_pass(const RArgs& a, int32_t q) {
     if (x < a.rows_end) {
       int32_t o = a.owner[x];
       tab_reset[x] = o < 0 ? INT32_MAX : o;
-      bool paired = (a.meta[x].flags & F_PROVEN) || a.beta[x] >= 0 || o >= 0;
-      if (!paired) atomicMin(&fu[a.seg[x]], (int32_t)x);
-      unpaired = !paired;
+      unpaired = !((a.meta[x].flags & F_PROVEN) || a.beta[x] >= 0 || o >= 0);
     }
-    if (a.predict) {
-      const unsigned w = __ballot_sync(0xffffffffu, unpaired);
-      if ((threadIdx.x & 31) == 0) a.unp_bits[x0 >> 5] = w;
+    const unsigned w = __ballot_sync(0xffffffffu, unpaired);
+    if (unpaired) {  // one atomic per segment present among the warp's unpaired rows: its first
+      const int32_t sg = a.seg[x];
+      const unsigned same = __match_any_sync(w, sg);
+      if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMin(&fu[sg], (int32_t)x);
     }
+    if (a.predict && (threadIdx.x & 31) == 0) a.unp_bits[x0 >> 5] = w;
   }
 }
 
