@@ -368,11 +368,11 @@ int ph_diagram_backward(ph_ctx* ctx, const float* coords, int32_t D, int32_t dim
  *                 (16 MiB) stays resident on every GPU that loads the library until exit.
  *   beta          device int32 [n_cols], output: largest row whose first column is j, or -1.
  *   stream        cudaStream_t as void*.
- * Allocates nothing (no cudaMalloc, cudaFree or allocator call). The first call on a device
- * looks up the scratch's device address with cudaGetSymbolAddress; make that first call before
- * any stream capture on that device. The address is kept for the process: after a
- * cudaDeviceReset of that device the scratch is gone, so do not call this entry point on it
- * again in the same process. Every call shares the one scratch array, which it resets
+ * Allocates nothing (no cudaMalloc, cudaFree or allocator call). Every call looks up the
+ * scratch's device address in the current context with cudaGetSymbolAddress (which allocates
+ * nothing), so a device reset or another context on the device leaves no stale address; the
+ * first call in a context loads the library's module, so make it before any stream capture in
+ * that context. Every call shares the one scratch array, which it resets
  * at its start: calls that overlap on the GPU (other streams or threads) race and give wrong
  * results. Rows outside [0, n_rows) are skipped and make the call return PH_ERR_INVALID.
  * Synchronises `stream`. */

@@ -6,24 +6,16 @@
 // library context at all. For them this entry point keeps its only scratch -- left(i), the
 // first column holding each row (Definition 3) -- in a fixed file-scope device array, so the
 // caller passes just its input and output buffers.
-#include <mutex>
-
 #include "ph_internal.cuh"
 
 namespace {
 
 constexpr int64_t kStaticRows = int64_t(1) << 22;  // 4,194,304 rows: 16 MiB of int32
-constexpr int kMaxDevices = 64;
 
 // Resident on every GPU that loads the library, until the process exits.
 __device__ __align__(256) int32_t g_left_scratch[kStaticRows];
 __device__ __align__(256) unsigned long long g_bad_rows;
 
-// Host side: device addresses of the two symbols, found once per device. In host code the
-// symbol names are host stand-ins, never device addresses, so kernels get these pointers.
-int32_t* g_left_ptr[kMaxDevices] = {nullptr};
-unsigned long long* g_bad_ptr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mu;
 
 __global__ void k_fill_left(int32_t* left, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -56,26 +48,23 @@ __global__ void k_beta_static(const int32_t* __restrict__ left, int64_t n_rows, 
   }
 }
 
-// Finds the device addresses of the static arrays for the current device, once.
-int setup_current_device(int* dev_out) {
+// The device addresses of the two static arrays in the current context, looked up on every
+// call (a lookup allocates nothing): an address kept from an earlier call would be stale once
+// the module is loaded again, after a device reset or in another context on the device. In host
+// code the symbol names are host stand-ins, never device addresses, so kernels get these.
+int static_arrays(int* dev_out, int32_t** left, unsigned long long** bad) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  void* p = nullptr;
+  void* q = nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 ||
+      cudaGetSymbolAddress(&p, g_left_scratch) != cudaSuccess ||
+      cudaGetSymbolAddress(&q, g_bad_rows) != cudaSuccess || !p || !q) {
     cudaGetLastError();
     return PH_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_left_ptr[dev]) {
-    void* p = nullptr;
-    void* q = nullptr;
-    if (cudaGetSymbolAddress(&p, g_left_scratch) != cudaSuccess ||
-        cudaGetSymbolAddress(&q, g_bad_rows) != cudaSuccess || !p || !q) {
-      cudaGetLastError();
-      return PH_ERR_CUDA;
-    }
-    g_left_ptr[dev] = static_cast<int32_t*>(p);
-    g_bad_ptr[dev] = static_cast<unsigned long long*>(q);
-  }
   *dev_out = dev;
+  *left = static_cast<int32_t*>(p);
+  *bad = static_cast<unsigned long long*>(q);
   return PH_OK;
 }
 
@@ -88,11 +77,11 @@ extern "C" int ph_beta_static(const int32_t* rows, int64_t n_cols, int32_t rows_
   if (n_cols == 0) return PH_OK;
   if (!rows || !beta) return PH_ERR_INVALID;
   int dev = 0;
-  int rc = setup_current_device(&dev);
+  int32_t* left = nullptr;
+  unsigned long long* bad = nullptr;
+  int rc = static_arrays(&dev, &left, &bad);
   if (rc != PH_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int32_t* left = g_left_ptr[dev];
-  unsigned long long* bad = g_bad_ptr[dev];
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int threads = 256;
