@@ -5,21 +5,20 @@
 //   (table)      tab[low(j)] = min j over the active columns and the pivots: the left-most
 //                column with each low, which defines the neighbour sets N(j) (Eq. neighbours).
 //                Two tables alternate between passes: the pass before resets one to the proven
-//                pivots (owner), and its new pivots (k_mark) and its survivors with their new
+//                pivots (owner), and its new pivots (k_phase1) and its survivors with their new
 //                lows (k_add, atomicMin) fill it, so no kernel gathers the lows again; k_tab
 //                builds the first pass's at set-up. With it, the first row of each (cloud, dim)
 //                that is not known to be paired (for Corollary 10).
-//   k_p1_tiles   Phase I (Algorithm 5) as a segmented exclusive prefix-max over the active
-//                columns of each (cloud, dim): P_j = largest low of an earlier colliding column;
-//                also upper bounds of the space this pass can need. The block that finishes
-//                last scans the tile aggregates and stops the pass before anything changes if
-//                the bounds exceed the space the host provided (the host then grows it and the
-//                pass runs again).
-//   k_mark       j is proven if it is left-most for its low and low(j) = beta_j (Thm 5) or
-//                low(j) > P_j (Thms 6-7). Empty columns become final; the zero case of
-//                Corollary 10 zeroes a column whose candidate rows are all paired. Each new
-//                pivot clears column low(j) (Lemma 1). Each active slot's source candidate is
-//                stored for Phase II.
+//   k_phase1     Phase I (Algorithm 5) as a segmented exclusive prefix-max over the active
+//                columns of each (cloud, dim), P_j = largest low of an earlier colliding column,
+//                in one pass over tiles with a decoupled look-back; then the marks: j is proven
+//                if it is left-most for its low and low(j) = beta_j (Thm 5) or low(j) > P_j
+//                (Thms 6-7); empty columns become final; the zero case of Corollary 10 zeroes a
+//                column whose candidate rows are all paired; each new pivot clears column
+//                low(j) (Lemma 1); each active slot's source candidate is stored for Phase II.
+//                Also upper bounds of the space Phase II can need: the grid's last block stops
+//                the pass after its marks if they exceed what the host provided (the host grows
+//                it and continues the pass at Phase II).
 //   k_add        Phase II: every colliding column l gets column tab[low(l)] added (XOR of two
 //                sorted row lists, or of bitmaps once a column fills in). Sources are
 //                left-most, hence never targets, so additions are independent. Survivors take
@@ -27,26 +26,26 @@
 //                the other arena by one atomic per chunk; new pivots move to the pivot store
 //                (their columns never change again). Blocks of 128 threads take 128-slot chunks
 //                from a device work queue, or each warp 32 slots once the list is short and
-//                its jobs long. While jobs are short each lane merges its own job; later the
-//                lanes share every job's merge-path pieces. Eight specialisations (row lists /
-//                bitmaps x block / warp chunks x lane / piece merges); the loop switches
-//                between them at most three times per reduction.
+//                its jobs long, and 8 slots in the last, short passes. While jobs are short
+//                each lane merges its own job; later the lanes share every job's merge-path
+//                pieces. Ten specialisations (row lists / bitmaps x block / 32-slot warp
+//                chunks x lane / piece merges, and 8-slot warp chunks with pieces); the loop
+//                switches between them at most four times per reduction.
 //   (p sets)     With Phase II limited to p neighbour sets (Sec. 3.4), k_set_* rank the sets
-//                between k_mark and k_add and hold back the other targets.
+//                between k_phase1 and k_add and hold back the other targets.
 //   k_commit     publishes the new locations of the columns other jobs may have been reading
 //                and prepares the next pass's row state; its last block ends the pass: the
 //                next active list, convergence (no collision left, Thm 8), the pass cap and
 //                time bound, and inside a CUDA graph the conditional that repeats the pass.
 // All per-pass state lives in device memory (DevState), so the same kernel sequence runs either
-// from a host loop or as the body of a graph's conditional while node.
+// from a host loop or as the body of a graph's conditional while node. Each kernel may start
+// while its predecessor drains (programmatic dependent launch) and waits for it first.
 #include <algorithm>
 
 #include "ph_internal.cuh"
 
 namespace ph {
 
-constexpr int kRItems = 8;
-constexpr int kRTile = kThreads * kRItems;
 
 enum : int32_t { ST_RUN = 0, ST_DONE = 1, ST_CAPPED = 2, ST_HOST = 3, ST_FAULT = 4,
                  ST_TIMEOUT = 5, ST_SWITCH = 6 };
@@ -80,6 +79,7 @@ struct DevState {
   unsigned long long bound_words, bound_piv;
   alignas(128) unsigned long long arena_used;  // words taken in the arena of the current pass
   alignas(128) unsigned int queue;             // next chunk for k_add
+  alignas(128) unsigned int tile_queue;        // next tile for k_phase1
   alignas(128) int32_t n_deferred;             // entries of dlist
   alignas(128) int32_t fault;                  // a bounded wait ran out
   int32_t debug_fault;  // the first failed bounds check of the debug build (PH_DCHECK), 0 if none
@@ -122,8 +122,7 @@ struct RArgs {
   int nc;
   int strict;
   int cor10;
-  SegMax* tile_sm;    // [ntiles] Phase I tile aggregates (scanned in place to prefixes)
-  SegMax* chunk_sm;   // [ntiles][kRItems] aggregate of each 256-entry chunk alone
+  unsigned long long* tile_st;  // per Phase I tile: look-back state of its aggregate / prefix
   unsigned long long* look;  // per Phase II chunk: look-back state of the survivor count
   int32_t* dlist;     // active slots whose column update waits for k_commit
   int32_t* src_e;     // per active slot: the colliding column's left-most column, -1 if none
@@ -154,8 +153,6 @@ struct PV {
   int32_t* alen;
   int32_t* alen2;
   int64_t n_act;
-  int64_t ntiles;
-  int64_t nchunks;
   int do_adds;
   int64_t* stats;
   int32_t* arena_next;
@@ -174,8 +171,6 @@ __device__ __forceinline__ PV pass_view(const DevState* ds) {
   v.alen = ds->alen;
   v.alen2 = ds->alen2;
   v.n_act = ds->n_act;
-  v.ntiles = (v.n_act + kRTile - 1) / kRTile;
-  v.nchunks = (v.n_act + kThreads - 1) / kThreads;
   v.do_adds = ds->pass < ds->max_passes;
   v.stats = ds->stats ? ds->stats + (int64_t)ds->pass * PH_PS_N : nullptr;
   v.arena_next = ds->arena[ds->pass & 1];
@@ -434,36 +429,6 @@ __device__ __forceinline__ SegMax block_scan_segmax(SegMax v, SegMax carry, SegM
 }
 
 
-// scan of the tile aggregates to tile prefixes, by one block; each thread takes kTopItems
-// consecutive tiles, so a pass of 10M columns (5,200 tiles) needs three block scans
-constexpr int kTopItems = 8;
-__device__ __forceinline__ void p1_top(const RArgs& a, const PV& v, SegMax* sh) {
-  SegMax carry{-1, -1};
-  for (int64_t base = 0; base < v.ntiles; base += (int64_t)kThreads * kTopItems) {
-    const int64_t i0 = base + (int64_t)threadIdx.x * kTopItems;
-    SegMax x[kTopItems];
-#pragma unroll
-    for (int k = 0; k < kTopItems; k++) {
-      x[k] = SegMax{INT32_MAX, -1};
-      if (i0 + k < v.ntiles) {  // written by other blocks of this grid: read from L2
-        const int2 t = __ldcg(reinterpret_cast<const int2*>(a.tile_sm + i0 + k));
-        x[k] = SegMax{t.x, t.y};
-      }
-    }
-    SegMax agg = x[0];
-#pragma unroll
-    for (int k = 1; k < kTopItems; k++) agg = segmax_combine(agg, x[k]);
-    SegMax tot;
-    SegMax run = block_scan_segmax(agg, carry, sh, tot);
-#pragma unroll
-    for (int k = 0; k < kTopItems; k++) {
-      if (i0 + k < v.ntiles) a.tile_sm[i0 + k] = run;
-      run = segmax_combine(run, x[k]);
-    }
-    carry = tot;
-  }
-}
-
 // the space this pass can need (arena, pivot store, counter rows) against what the host
 // provided; nothing has changed yet, so a pass stopped here runs again unchanged once the host
 // has grown the buffers
@@ -471,168 +436,170 @@ __device__ __forceinline__ void check_capacity(DevState* ds) {
   int reason = 0;
   if (ds->bound_words > (unsigned long long)ds->arena_cap[ds->pass & 1]) reason |= 1;
   if (ds->bound_piv + ds->piv_used > (unsigned long long)ds->piv_cap) reason |= 2;
-  if (ds->stats && ds->pass >= ds->stats_rows) reason |= 4;
   if (reason) {
     ds->host_reason = reason;
     ds->status = ST_HOST;
   }
 }
 
-// per tile: Phase I aggregates of each chunk and of the tile, and upper bounds of the arena
-// words (target + source) and pivot-store words (only a left-most column can become a pivot)
-__global__ void k_p1_tiles(RArgs a) {
+// Phase I and the marks in one kernel, a single-pass scan over tiles of kFTile active slots
+// (kFItems consecutive slots per thread), claimed in order from a work queue. A tile loads its
+// slots' columns, lows, sources and lengths once; takes its Phase I aggregate and each thread's
+// prefix within the tile from one block scan; publishes the aggregate and looks back over the
+// tiles before it for its prefix (decoupled look-back, as the additions kernel's survivor
+// count); then applies the marks. The space bounds of the pass are summed on the way, and the
+// grid's last block checks them against what the host provided: a pass that does not fit stops
+// after its marks (which depend only on the state at the pass's start) and the host continues it
+// at Phase II once the buffers have grown.
+constexpr int kFItems = 4;
+constexpr int kFTile = kThreads * kFItems;
+// tile state word: pass tag (8 bits) | flags (2) | segment (23) | val + 1 (31)
+constexpr unsigned long long kTAgg = 1ull << 54, kTIncl = 2ull << 54, kTFlags = 3ull << 54;
+__device__ __forceinline__ unsigned long long tile_word(unsigned long long tag, unsigned long long flag,
+                                                       SegMax x) {
+  return tag | flag | ((unsigned long long)(x.seg & 0x7fffff) << 31) |
+         (unsigned long long)((uint32_t)(x.val + 1) & 0x7fffffffu);
+}
+__device__ __forceinline__ SegMax tile_value(unsigned long long w) {
+  return SegMax{(int32_t)((w >> 31) & 0x7fffff), (int32_t)(w & 0x7fffffffu) - 1};
+}
+
+// by warp 0: publishes tile t's aggregate, returns the Phase I value of every tile before it
+// (SegMax{-1, -1}, a left identity of segmax_combine, for none) and publishes t's inclusive state
+__device__ __forceinline__ SegMax tile_look_back(const RArgs& a, int32_t pass, int64_t t,
+                                                 SegMax agg, bool& fault) {
+  const int lane = lane_id();
+  const unsigned long long tag = (unsigned long long)(pass & 0xff) << 56;
+  unsigned long long* st = a.tile_st;
+  const SegMax none{-1, -1};
+  if (t == 0) {
+    if (lane == 0) atomicExch(st, tile_word(tag, kTIncl, agg));
+    return none;
+  }
+  if (lane == 0) atomicExch(st + t, tile_word(tag, kTAgg, agg));
+  SegMax acc = none;
+  bool have = false;
+  for (int64_t p = t - 1;; p -= 32) {
+    const int64_t q = p - lane;  // lane 0 the nearest tile
+    SegMax x = none;
+    bool incl = true;  // before tile 0: an inclusive state of nothing
+    if (q >= 0) {
+      unsigned long long w = 0;
+      for (int it = 0;; it++) {
+        w = *(const volatile unsigned long long*)(st + q);
+        if ((w >> 56) == (tag >> 56) && (w & kTFlags)) break;
+        if (it > kSpinLimit) {
+          fault = true;
+          w = tag | kTIncl;
+          break;
+        }
+        __nanosleep(32);
+      }
+      x = tile_value(w);
+      incl = (w & kTFlags) == kTIncl;
+    }
+    const unsigned im = __ballot_sync(0xffffffffu, incl);
+    const int stop = im ? __ffs(im) - 1 : 32;
+    // the window in order, farthest (highest lane) first; lanes past the stop are left identities
+    SegMax val = lane <= stop ? x : none;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      SegMax u;
+      u.seg = __shfl_down_sync(0xffffffffu, val.seg, o);
+      u.val = __shfl_down_sync(0xffffffffu, val.val, o);
+      if (lane + o < 32) val = segmax_combine(u, val);
+    }
+    SegMax win;
+    win.seg = __shfl_sync(0xffffffffu, val.seg, 0);
+    win.val = __shfl_sync(0xffffffffu, val.val, 0);
+    acc = have ? segmax_combine(win, acc) : win;  // this window comes before the later ones
+    have = true;
+    if (im) break;
+  }
+  if (lane == 0) atomicExch(st + t, tile_word(tag, kTIncl, segmax_combine(acc, agg)));
+  return acc;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_phase1(RArgs a) {
   __shared__ SegMax sh[kWarps + 1];
   __shared__ int64_t shs[kWarps + 1];
-  __shared__ SegMax s_warp[kRItems][kWarps];  // aggregate of each warp's 32 slots per chunk
+  __shared__ int64_t s_tile;
+  __shared__ SegMax s_pre;
+  constexpr int kFI = kFItems;
   pdl_wait();
   pdl_trigger();
-  if (a.ds->status != ST_RUN) return;
-  const PV v = pass_view(a.ds);
-  // blocks beyond the tiles leave at once; block 0 always takes part (it checks capacity)
-  const unsigned parts = (unsigned)std::max<int64_t>(1, std::min<int64_t>(gridDim.x, v.ntiles));
-  if (blockIdx.x >= parts) return;
-  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  DevState* ds = a.ds;
+  if (ds->status != ST_RUN) return;
+  const PV v = pass_view(ds);
+  const int32_t pass = ds->pass;
+  const int32_t* fu = a.first_unp + (int64_t)(pass & 1) * a.nseg;  // this pass's copy
+  const int64_t ntiles = (v.n_act + kFTile - 1) / kFTile;
   int64_t bw = 0, bp = 0;
+  int64_t n_zero = 0, n_piv = 0, n_c10 = 0, n_pred = 0, n_empty = 0;
   bool want = false;  // a target whose addition may reach its dimension's bit-packing threshold
-  for (int64_t t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
-    const int64_t tile0 = t * kRTile;
+  bool fault = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ds->tile_queue, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    if (t >= ntiles) break;
+    const int64_t tile0 = t * kFTile;
     // bit-packing thresholds of the tile's columns (ascending ids, so dimensions too): exact in
     // the top dimension (ids from t_b on), the smallest of the others below it
     int32_t t_b = 0, t_hi = INT32_MAX, t_lo = INT32_MAX;
     if (a.dense_floor != INT32_MAX) {
       const int32_t j0 = v.act[tile0];
-      const int32_t j1 = v.act[min(tile0 + kRTile, v.n_act) - 1];
+      const int32_t j1 = v.act[min(tile0 + kFTile, v.n_act) - 1];
       t_b = dim_start_of(a, j1);
       t_hi = dense_min_of(a, j1);
       t_lo = dense_min_between(a, j0, t_b - 1);
     }
-    // every load of the tile's kRItems slots per thread is issued before any is used
-    int32_t j[kRItems], l[kRItems], sg[kRItems], n[kRItems];
+    const int64_t e0 = tile0 + (int64_t)threadIdx.x * kFI;
+    int32_t j[kFI], l[kFI], sg[kFI], n[kFI], b[kFI], s[kFI];
 #pragma unroll
-    for (int it = 0; it < kRItems; it++) {
-      const int64_t e = tile0 + it * kThreads + threadIdx.x;
-      j[it] = e < v.n_act ? v.act[e] : -1;
-    }
+    for (int i = 0; i < kFI; i++) j[i] = e0 + i < v.n_act ? v.act[e0 + i] : -1;
 #pragma unroll
-    for (int it = 0; it < kRItems; it++) {
-      const int64_t e = tile0 + it * kThreads + threadIdx.x;
-      l[it] = j[it] >= 0 ? a.low[j[it]] : -1;
-      sg[it] = j[it] >= 0 ? seg_of(a, j[it]) : INT32_MAX;
-      n[it] = j[it] >= 0 ? v.alen[e] : 0;
-    }
-#pragma unroll
-    for (int it = 0; it < kRItems; it++) {
-      const int32_t s = l[it] >= 0 ? v.tab[l[it]] : -1;
-      const bool collide = l[it] >= 0 && s != j[it];
-      // a column's reservation is its stored words: its rows, or its bitmap with the header
-      bw += stored_words(n[it]);
-      if (collide) {  // a target: its source may be added
-        const int32_t ns = stored_words(a.meta[s].len);
-        bw += ns;
-        want |= n[it] + ns > (j[it] >= t_b ? t_hi : t_lo);
-      } else if (l[it] >= 0) {
-        bp += stored_words(n[it]);  // left-most: it may be proven and move
-      }
-      // Phase I value: the low of a colliding column, in its (cloud, dim) segment
-      SegMax val{sg[it], collide ? l[it] : -1};
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {  // ordered reduction over the warp's 32 slots
-        SegMax u;
-        u.seg = __shfl_down_sync(0xffffffffu, val.seg, o);
-        u.val = __shfl_down_sync(0xffffffffu, val.val, o);
-        if ((lane & (2 * o - 1)) == 0) val = segmax_combine(val, u);
-      }
-      if (lane == 0) s_warp[it][warp] = val;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {  // lane k: chunk k over the warps; lane 0 folds the chunks in order
-      SegMax c{-1, -1};
-      if (lane < kRItems) {
-        c = s_warp[lane][0];
-        for (int w = 1; w < kWarps; w++) c = segmax_combine(c, s_warp[lane][w]);
-        a.chunk_sm[t * kRItems + lane] = c;  // this chunk alone
-      }
-      SegMax carry{-1, -1};
-#pragma unroll
-      for (int k = 0; k < kRItems; k++) {
-        SegMax ck;
-        ck.seg = __shfl_sync(0xffffffffu, c.seg, k);
-        ck.val = __shfl_sync(0xffffffffu, c.val, k);
-        carry = segmax_combine(carry, ck);
-      }
-      if (lane == 0) a.tile_sm[t] = carry;
-    }
-    __syncthreads();
-  }
-  if (want && !v.dense_on) a.ds->dense_want = 1;  // bit-packed additions from the next pass
-  int64_t tw, tp;
-  block_excl_sum<int64_t>(bw, shs, tw);
-  block_excl_sum<int64_t>(bp, shs, tp);
-  if (threadIdx.x == 0 && (tw || tp)) {
-    atomicAdd(&a.ds->bound_words, (unsigned long long)tw);
-    atomicAdd(&a.ds->bound_piv, (unsigned long long)tp);
-  }
-  // the last block scans the tile aggregates and checks capacity (no extra launches)
-  if (last_block(&a.ds->blocks_done, parts)) {
-    p1_top(a, v, sh);
-    if (threadIdx.x == 0) {
-      a.ds->blocks_done = 0;
-      check_capacity(a.ds);
-    }
-  }
-}
-
-
-
-
-// kMI consecutive slots per thread, kMI 256-slot chunks per block iteration (kMI divides the
-// chunks of a tile); every gather of the iteration is issued before any is used. The
-// iteration's prefix is the tile's prefix combined with the aggregates of the tile's earlier
-// chunks; the slots' own prefixes come from a thread-local fold and one block scan.
-constexpr int kMarkItems = 4;
-static_assert(kRItems % kMarkItems == 0, "a block iteration stays inside one Phase I tile");
-template <int kMI>
-__global__ void k_mark(RArgs a) {
-  __shared__ SegMax sh[kWarps + 1];
-  pdl_wait();
-  pdl_trigger();
-  if (a.ds->status != ST_RUN) return;
-  const PV v = pass_view(a.ds);
-  const int32_t* fu = a.first_unp + (int64_t)(a.ds->pass & 1) * a.nseg;  // this pass's copy
-  int64_t n_zero = 0, n_piv = 0, n_c10 = 0, n_pred = 0, n_empty = 0;
-  const int64_t nit = (v.n_act + (int64_t)kThreads * kMI - 1) / ((int64_t)kThreads * kMI);
-  for (int64_t it = blockIdx.x; it < nit; it += gridDim.x) {
-    const int64_t chunk0 = it * kMI;
-    const int64_t tile = chunk0 / kRItems;
-    SegMax carry = a.tile_sm[tile];
-    for (int64_t c = tile * kRItems; c < chunk0; c++) carry = segmax_combine(carry, a.chunk_sm[c]);
-    const int64_t e0 = chunk0 * kThreads + (int64_t)threadIdx.x * kMI;
-    int32_t j[kMI], l[kMI], sg[kMI], s[kMI], b[kMI];
-#pragma unroll
-    for (int i = 0; i < kMI; i++) j[i] = e0 + i < v.n_act ? v.act[e0 + i] : -1;
-#pragma unroll
-    for (int i = 0; i < kMI; i++) {
+    for (int i = 0; i < kFI; i++) {
       l[i] = j[i] >= 0 ? a.low[j[i]] : -1;
       sg[i] = j[i] >= 0 ? seg_of(a, j[i]) : INT32_MAX;
+      n[i] = j[i] >= 0 ? v.alen[e0 + i] : 0;
       b[i] = j[i] >= 0 ? a.beta[j[i]] : -1;
     }
 #pragma unroll
-    for (int i = 0; i < kMI; i++) {
-      if (!PH_DCHECK(&a.ds->debug_fault, l[i] < a.rows_end, 2)) l[i] = -1, j[i] = -1;
+    for (int i = 0; i < kFI; i++) {
+      if (!PH_DCHECK(&ds->debug_fault, l[i] < a.rows_end, 2)) l[i] = -1, j[i] = -1;
       s[i] = l[i] >= 0 ? v.tab[l[i]] : -1;
     }
-    // Phase I values: the low of a colliding column, in its (cloud, dim) segment
-    SegMax x[kMI];
+    // Phase I values (the low of a colliding column, in its (cloud, dim) segment) and the space
+    // bounds: a column's reservation is its stored words (its rows, or its bitmap with the
+    // header); a target's source may be added; a left-most column may be proven and move
+    SegMax x[kFI];
 #pragma unroll
-    for (int i = 0; i < kMI; i++)
-      x[i] = SegMax{sg[i], (l[i] >= 0 && s[i] != j[i]) ? l[i] : -1};
+    for (int i = 0; i < kFI; i++) {
+      const bool collide = l[i] >= 0 && s[i] != j[i];
+      bw += stored_words(n[i]);
+      if (collide) {
+        const int32_t ns = stored_words(a.meta[s[i]].len);
+        bw += ns;
+        want |= n[i] + ns > (j[i] >= t_b ? t_hi : t_lo);
+      } else if (l[i] >= 0) {
+        bp += stored_words(n[i]);
+      }
+      x[i] = SegMax{sg[i], collide ? l[i] : -1};
+    }
     SegMax agg = x[0];
 #pragma unroll
-    for (int i = 1; i < kMI; i++) agg = segmax_combine(agg, x[i]);
+    for (int i = 1; i < kFI; i++) agg = segmax_combine(agg, x[i]);
     SegMax tot;
-    SegMax run = block_scan_segmax(agg, carry, sh, tot);
+    const SegMax pre_t = block_scan_segmax(agg, SegMax{-1, -1}, sh, tot);  // within the tile
+    if (threadIdx.x < 32) {
+      const SegMax P = tile_look_back(a, pass, t, tot, fault);
+      if (threadIdx.x == 0) s_pre = P;
+    }
+    __syncthreads();
+    SegMax run = threadIdx.x == 0 ? s_pre : segmax_combine(s_pre, pre_t);
 #pragma unroll
-    for (int i = 0; i < kMI; i++) {
+    for (int i = 0; i < kFI; i++) {
       const SegMax pre = run;
       run = segmax_combine(run, x[i]);
       if (j[i] < 0) continue;
@@ -641,7 +608,7 @@ __global__ void k_mark(RArgs a) {
       // an active column carries no flag (proven, final and cleared columns leave the active
       // list in the pass that marks them; the new-pivot mark goes with them), so the marks below
       // are stored without a load
-      (void)PH_DCHECK(&a.ds->debug_fault, a.meta[j[i]].flags == 0, 7);
+      (void)PH_DCHECK(&ds->debug_fault, a.meta[j[i]].flags == 0, 7);
       if (l[i] < 0) {
         a.meta[j[i]].flags = F_FINAL;
         n_zero++;
@@ -675,6 +642,22 @@ __global__ void k_mark(RArgs a) {
     stat_add(v.stats, PH_PS_PREDICTED, n_pred);
     stat_add(v.stats, PH_PS_EMPTY_L, n_empty);
     stat_add(v.stats, PH_PS_COR10, n_c10);
+  }
+  if (want && !v.dense_on) ds->dense_want = 1;  // bit-packed additions from the next pass
+  if (__any_sync(0xffffffffu, fault) && lane_id() == 0) ds->fault = 1;
+  int64_t tw, tp;
+  block_excl_sum<int64_t>(bw, shs, tw);
+  block_excl_sum<int64_t>(bp, shs, tp);
+  if (threadIdx.x == 0 && (tw || tp)) {
+    atomicAdd(&ds->bound_words, (unsigned long long)tw);
+    atomicAdd(&ds->bound_piv, (unsigned long long)tp);
+  }
+  // the grid's last block checks the space this pass's Phase II needs
+  if (last_block(&ds->blocks_done, gridDim.x)) {
+    if (threadIdx.x == 0) {
+      ds->blocks_done = 0;
+      check_capacity(ds);
+    }
   }
 }
 
@@ -835,7 +818,7 @@ __device__ __forceinline__ Job job_of(const RArgs& a, const PV& v, int64_t e) {
   Job jb{-1, -1, false, false, false, 0, nullptr, nullptr, 0, 0, false, false};
   if (e >= v.n_act) return jb;
   // every load is issued up front: the column and its source candidate are known from the
-  // active list and k_mark's per-slot source, so no load waits on another's result
+  // active list and k_phase1's per-slot source, so no load waits on another's result
   const int32_t j = v.act[e];
   const int32_t se = a.src_e[e];  // -1: no collision; <= -2: a target whose set waits
   const int32_t s = se >= 0 ? se : -1;
@@ -1768,6 +1751,7 @@ __host__ __device__ inline void reset_counters(DevState* ds) {
   ds->bound_words = 0;
   ds->bound_piv = 0;
   ds->queue = 0;
+  ds->tile_queue = 0;
   ds->arena_used = 0;
   ds->n_deferred = 0;
   ds->totals[0] = ds->totals[1] = 0;
@@ -1866,6 +1850,11 @@ __device__ void end_of_pass(const RArgs& a, cudaGraphConditionalHandle cond, int
       // the pass is complete, so a later call can resume from the next one
       if (global_ns() - ds->t_start > ds->t_limit) ds->status = ST_TIMEOUT;
       else if (to_dense || to_warp || to_pieces || to_narrow) ds->status = ST_SWITCH;
+      // counter rows for the next pass: its first kernel writes them before any capacity check
+      if (ds->status != ST_TIMEOUT && ds->stats && ds->pass >= ds->stats_rows) {
+        ds->host_reason = 4;
+        ds->status = ST_HOST;
+      }
     }
   }
   if (in_graph) cudaGraphSetConditional(cond, ds->status == ST_RUN ? 1u : 0u);
@@ -1911,7 +1900,6 @@ __global__ void k_reduce_init(int64_t m, InitLayout L, int32_t* rows0,
 
 static RArgs make_args(ph_ctx* ctx) {
   ReduceState& rs = ctx->rs;
-  const int64_t ntiles = (ctx->m + kRTile - 1) / kRTile;
   RArgs a{};
   a.ds = static_cast<DevState*>(rs.dstate);
   a.low = ctx->low;
@@ -1927,8 +1915,7 @@ static RArgs make_args(ph_ctx* ctx) {
   a.nc = ctx->n_clouds;
   a.strict = ctx->opts.strict_phase2;
   a.cor10 = ctx->opts.use_cor10;
-  a.tile_sm = (SegMax*)rs.tiles;
-  a.chunk_sm = a.tile_sm + ntiles;
+  a.tile_st = static_cast<unsigned long long*>(rs.tiles);
   a.look = static_cast<unsigned long long*>(rs.look);
   a.dlist = static_cast<int32_t*>(rs.dlist);
   a.src_e = static_cast<int32_t*>(rs.src_e);
@@ -1999,21 +1986,22 @@ static void launch_k(ph_ctx* ctx, bool pdl, void (*kern)(KArgs...), unsigned gri
   PH_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
 }
 
-// the kernels of one pass, in order; grids are fixed (persistent blocks loop over the work)
+// the kernels of one pass, in order; grids are fixed (persistent blocks loop over the work).
+// The pass's first kernel (Phase I and the marks), then the rest: a pass stopped for more space
+// after its marks continues with the rest alone (launch_pass_rest)
 // variant: the additions kernel (add_variant)
-static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
-                        bool in_graph, int variant, bool time_add, cudaStream_t st) {
+static unsigned pass_blocks(ph_ctx* ctx, int64_t full, int64_t per_block) {
+  // the full machine for large complexes, no more blocks than the largest active list (all m
+  // columns) can use for small ones, so a small complex's pass costs little
+  const int64_t m = std::max<int64_t>(ctx->m, 1);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (m + per_block - 1) / per_block));
+}
+
+static void launch_pass_rest(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
+                             bool in_graph, int variant, bool time_add, cudaStream_t st) {
   ReduceState& rs = ctx->rs;
   const int sms = ctx->num_sms;
-  // grids: the full machine for large complexes, no more blocks than the largest active list
-  // (all m columns) can use for small ones, so a small complex's pass costs little
-  const int64_t m = std::max<int64_t>(ctx->m, 1);
-  auto blocks = [&](int64_t full, int64_t per_block) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(full, (m + per_block - 1) / per_block));
-  };
-  launch_k(ctx, true, k_p1_tiles, blocks(sms * 8, kRTile), kThreads, 0, st, a);
-  launch_k(ctx, true, k_mark<kMarkItems>, blocks(sms * 8, kThreads * kMarkItems), kThreads, 0, st,
-           a);
+  auto blocks = [&](int64_t full, int64_t per_block) { return pass_blocks(ctx, full, per_block); };
   if (ctx->opts.collect_stats)
     launch_k(ctx, true, k_ess_count, (unsigned)sms * 4, kThreads, 0, st, a, ctx->m);
   if (ctx->opts.phase2_sets > 0 && a.rows_end > 0) {  // host-driven loop only
@@ -2060,6 +2048,12 @@ static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle 
            in_graph ? 1 : 0);
 }
 
+static void launch_pass(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHandle cond,
+                        bool in_graph, int variant, bool time_add, cudaStream_t st) {
+  launch_k(ctx, true, k_phase1, pass_blocks(ctx, ctx->num_sms * 8, kFTile), kThreads, 0, st, a);
+  launch_pass_rest(ctx, a, cond, in_graph, variant, time_add, st);
+}
+
 // the new buffer is taken before the old one goes, so a failed allocation (PH_ERR_ALLOC)
 // leaves the store, and the device state that points into it, as it was: a later call resumes
 static void grow_store(ph_ctx* ctx, ColStore& s, int64_t need_words) {
@@ -2089,9 +2083,10 @@ void reduce_init(ph_ctx* ctx) {
   int nseg = (int)ctx->seg_start.size() - 1;
   rs.first_unp = alloc_n<int32_t>(ctx, 2 * nseg);  // two copies, alternating between passes
   PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, 2 * nseg * sizeof(int32_t), st));  // above every id
-  int64_t ntiles = (m + kRTile - 1) / kRTile;
-  rs.tiles_bytes = ntiles * (1 + kRItems) * sizeof(SegMax);
+  const int64_t ntiles = (m + kFTile - 1) / kFTile;
+  rs.tiles_bytes = (ntiles + 1) * sizeof(unsigned long long);
   rs.tiles = ctx->dalloc(rs.tiles_bytes);
+  PH_CUDA(cudaMemsetAsync(rs.tiles, 0, rs.tiles_bytes, st));  // no state published yet
   const int64_t nchunks = (m + 7) / 8 + 1;  // chunks of any shape (8 slots or more)
   rs.look = alloc_n<unsigned long long>(ctx, nchunks);
   PH_CUDA(cudaMemsetAsync(rs.look, 0, nchunks * sizeof(unsigned long long), st));
@@ -2295,6 +2290,10 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   } else if (h.status == ST_TIMEOUT) {  // stopped between two passes
     h.status = ST_RUN;
   }
+  if (h.stats && h.pass >= h.stats_rows) {  // counter rows for the first pass of this call
+    h.host_reason = 4;
+    serve_host_request(ctx, h);
+  }
   // every pass proves or zeroes at least one column, so m + 1 passes always suffice
   h.max_passes = max_passes < 0 ? (int32_t)std::min<int64_t>(ctx->m + 1, INT32_MAX) : max_passes;
   h.blocks_done = 0;
@@ -2305,10 +2304,17 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
   PH_CHECK_LAUNCH();
   const RArgs a = make_args(ctx);
 
+  bool rest_only = false;  // a pass stopped for space after its marks continues at Phase II
   for (;;) {
     const int32_t first_pass = h.pass;
     NvtxRange nvtx_range_(use_graph ? "pass loop (graph)" : "pass");
-    if (use_graph) {
+    bool ran_graph = false;
+    if (rest_only) {
+      rest_only = false;
+      launch_pass_rest(ctx, a, 0, false, add_variant(h), time_add, st);
+      if (time_add) rs.add_launches++;
+    } else if (use_graph) {
+      ran_graph = true;
       const int variant = add_variant(h);
       if (!rs.graph_exec[variant]) build_graph(ctx, a, variant);
       PH_CUDA(cudaGraphLaunch(rs.graph_exec[variant], st));
@@ -2318,9 +2324,9 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
     }
     PH_CUDA(cudaMemcpyAsync(&h, rs.dstate, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     PH_CUDA(cudaStreamSynchronize(st));
-    if (use_graph) {  // kernels per executed pass of the graph's loop
+    if (ran_graph) {  // kernels per executed pass of the graph's loop
       const int32_t last = (h.status == ST_DONE || h.status == ST_CAPPED) ? h.passes : h.pass;
-      const int per_pass = 4 + (ctx->opts.collect_stats ? 1 : 0);
+      const int per_pass = 3 + (ctx->opts.collect_stats ? 1 : 0);
       ctx->launches += per_pass * (int64_t)(last - first_pass + 1);
     }
     if (h.status == ST_RUN) continue;
@@ -2337,8 +2343,11 @@ int reduce_run(ph_ctx* ctx, int32_t max_passes) {
         rs.ev.pop_back();
         rs.add_launches--;
       }
+      // space for Phase II (reasons 1, 2): the pass continues there, its marks made; counter
+      // rows (reason 4): asked for between two passes, the next pass runs whole
+      rest_only = (h.host_reason & 3) != 0;
       serve_host_request(ctx, h);
-      reset_counters(&h);  // the pass runs again from its start
+      if (rest_only) reset_counters(&h);
       PH_CUDA(cudaMemcpyAsync(rs.dstate, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
       continue;
     }
