@@ -534,6 +534,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_phase1(RArgs a) {
   const int32_t pass = ds->pass;
   const int32_t* fu = a.first_unp + (int64_t)(pass & 1) * a.nseg;  // this pass's copy
   const int64_t ntiles = (v.n_act + kFTile - 1) / kFTile;
+  // no more blocks take part than there are tiles (the others leave at once: a short pass's
+  // grid is mostly idle); block 0 always does (the last block checks capacity)
+  const unsigned parts = (unsigned)std::max<int64_t>(1, std::min<int64_t>(gridDim.x, ntiles));
+  if (blockIdx.x >= parts) return;
   int64_t bw = 0, bp = 0;
   int64_t n_zero = 0, n_piv = 0, n_c10 = 0, n_pred = 0, n_empty = 0;
   bool want = false;  // a target whose addition may reach its dimension's bit-packing threshold
@@ -652,8 +656,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_phase1(RArgs a) {
     atomicAdd(&ds->bound_words, (unsigned long long)tw);
     atomicAdd(&ds->bound_piv, (unsigned long long)tp);
   }
-  // the grid's last block checks the space this pass's Phase II needs
-  if (last_block(&ds->blocks_done, gridDim.x)) {
+  // the last of the taking-part blocks checks the space this pass's Phase II needs
+  if (last_block(&ds->blocks_done, parts)) {
     if (threadIdx.x == 0) {
       ds->blocks_done = 0;
       check_capacity(ds);
