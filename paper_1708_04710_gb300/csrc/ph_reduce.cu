@@ -600,43 +600,60 @@ __global__ void __launch_bounds__(kThreads, 4) k_phase1(RArgs a) {
       const SegMax P = tile_look_back(a, pass, t, tot, fault);
       if (threadIdx.x == 0) s_pre = P;
     }
-    __syncthreads();
-    SegMax run = threadIdx.x == 0 ? s_pre : segmax_combine(s_pre, pre_t);
+    // the marks: a new pivot proven by Thm 5 (left-most, low = beta) or by Phase I (left-most,
+    // low > P_j); else the zero case of Corollary 10, else a pair prediction. Every active
+    // column carries no flag (proven, final and cleared columns leave the active list in the
+    // pass that marks them; the new-pivot mark goes with them), so marks are stored without a
+    // load. Only a left-most column whose low is not its beta needs P_j: the others are marked
+    // while warp 0 looks back, the rest after the tile's prefix is known.
+    auto pivot = [&](int i) {
+      a.meta[j[i]].flags = F_PROVEN | F_NEWPIV;
+      a.owner[l[i]] = j[i];
+      atomicMin(&v.tab_next[l[i]], j[i]);  // its row's pivot from the next pass on
+      a.meta[l[i]].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
+      n_piv++;
+    };
+    auto unproven = [&](int i) {
+      if (a.cor10 && b[i] < 0 && l[i] < fu[sg[i] - a.nc]) {
+        a.meta[j[i]].flags = F_FINAL;  // Corollary 10, zero case
+        n_c10++;
+      } else if (a.predict && b[i] >= 0 && a.pred[j[i]] < 0) {
+        const int32_t pi = predicted_low(a, b[i], l[i]);
+        if (pi >= 0) {
+          a.pred[j[i]] = pi;
+          n_pred++;
+        } else if (pi == -2) {
+          n_empty++;
+        }
+      }
+    };
+    unsigned waits = 0;  // items whose mark needs P_j
 #pragma unroll
     for (int i = 0; i < kFI; i++) {
-      const SegMax pre = run;
-      run = segmax_combine(run, x[i]);
       if (j[i] < 0) continue;
-      const int64_t e = e0 + i;
-      a.src_e[e] = s[i] != j[i] ? s[i] : -1;  // Phase II reads it in list order
-      // an active column carries no flag (proven, final and cleared columns leave the active
-      // list in the pass that marks them; the new-pivot mark goes with them), so the marks below
-      // are stored without a load
+      a.src_e[e0 + i] = s[i] != j[i] ? s[i] : -1;  // Phase II reads it in list order
       (void)PH_DCHECK(&ds->debug_fault, a.meta[j[i]].flags == 0, 7);
       if (l[i] < 0) {
         a.meta[j[i]].flags = F_FINAL;
         n_zero++;
+      } else if (s[i] != j[i]) {
+        unproven(i);
+      } else if (l[i] == b[i]) {
+        pivot(i);
       } else {
+        waits |= 1u << i;
+      }
+    }
+    __syncthreads();
+    if (waits) {
+      SegMax run = threadIdx.x == 0 ? s_pre : segmax_combine(s_pre, pre_t);
+#pragma unroll
+      for (int i = 0; i < kFI; i++) {
+        const SegMax pre = run;
+        run = segmax_combine(run, x[i]);
+        if (!((waits >> i) & 1u)) continue;
         const int32_t P = (pre.seg == x[i].seg) ? pre.val : -1;
-        const bool leftmost = s[i] == j[i];
-        if (leftmost && (l[i] == b[i] || l[i] > P)) {
-          a.meta[j[i]].flags = F_PROVEN | F_NEWPIV;
-          a.owner[l[i]] = j[i];
-          atomicMin(&v.tab_next[l[i]], j[i]);  // its row's pivot from the next pass on
-          a.meta[l[i]].cleared = 1;  // clearing (Lemma 1): column l is positive and paired with j
-          n_piv++;
-        } else if (a.cor10 && b[i] < 0 && l[i] < fu[sg[i] - a.nc]) {
-          a.meta[j[i]].flags = F_FINAL;  // Corollary 10, zero case
-          n_c10++;
-        } else if (a.predict && b[i] >= 0 && a.pred[j[i]] < 0) {
-          const int32_t pi = predicted_low(a, b[i], l[i]);
-          if (pi >= 0) {
-            a.pred[j[i]] = pi;
-            n_pred++;
-          } else if (pi == -2) {
-            n_empty++;
-          }
-        }
+        if (l[i] > P) pivot(i); else unproven(i);
       }
     }
   }
