@@ -301,7 +301,10 @@ __device__ __forceinline__ int32_t predicted_low(const RArgs& a, int32_t b, int3
   return (int32_t)(lo * 32 + __ffs(bits) - 1);
 }
 
-// kTI consecutive slots per thread and iteration, their loads issued together
+// The first pass's left-most-column table (at set-up; every later pass's table is filled by the
+// pass before it): tab[low(j)] = min j over the active columns by atomicMin, and every low
+// marked as seen for the essential estimate. kTI consecutive slots per thread and iteration,
+// their loads issued together.
 constexpr int kTabItems = 4;
 __global__ void k_tab(RArgs a) {
   pdl_wait();
