@@ -137,9 +137,10 @@ typedef struct {
   int32_t phase2_sets;
   int32_t phase2_priority;
   /* Initial capacity of each of the two survivor arenas, in int32 words (0, default: twice the
-   * boundary's nonzeros). A pass whose Phase I bound does not fit stops before any change, the
-   * host grows the arena and the pass runs again, so a small value trades memory for extra
-   * host round trips; results are the same. */
+   * boundary's nonzeros). A pass whose Phase I bound does not fit stops after its marks,
+   * before any column changes; the host grows the arena and the pass continues with its column
+   * additions, so a small value trades memory for extra host round trips; results are the
+   * same. */
   int64_t arena_words;
 } ph_opts;
 

@@ -432,9 +432,9 @@ __device__ __forceinline__ SegMax block_scan_segmax(SegMax v, SegMax carry, SegM
 }
 
 
-// the space this pass can need (arena, pivot store, counter rows) against what the host
-// provided; nothing has changed yet, so a pass stopped here runs again unchanged once the host
-// has grown the buffers
+// the space this pass's Phase II can need (arena, pivot store) against what the host provided;
+// no column has changed yet, and the marks made depend only on the pass's starting state, so a
+// pass stopped here continues at Phase II once the host has grown the buffers
 __device__ __forceinline__ void check_capacity(DevState* ds) {
   int reason = 0;
   if (ds->bound_words > (unsigned long long)ds->arena_cap[ds->pass & 1]) reason |= 1;
@@ -1782,8 +1782,8 @@ __host__ __device__ inline void reset_counters(DevState* ds) {
 }
 
 // the deferred column updates and the next pass's row state, then (last block) the end of the
-// pass and the reset of the per-pass counters. A pass stopped before any change (ST_HOST) runs
-// again on the row state it had, so neither is touched then (the host resets the counters).
+// pass and the reset of the per-pass counters. A pass stopped for space (ST_HOST) continues at
+// Phase II on the row state it had, so neither is touched then (the host resets the counters).
 __global__ void k_commit(RArgs a, cudaGraphConditionalHandle cond, int in_graph) {
   pdl_wait();
   DevState* ds = a.ds;
