@@ -2091,6 +2091,9 @@ static void grow_store(ph_ctx* ctx, ColStore& s, int64_t need_words) {
 
 void reduce_init(ph_ctx* ctx) {
   free_reduce_state(ctx);  // whatever an earlier, failed initialisation left
+  // Phase I's tile states carry a (cloud, dimension) segment in 23 bits
+  PH_REQUIRE((int64_t)ctx->seg_start.size() - 1 < (1 << 23), PH_ERR_CAPACITY,
+             "at most 8,388,607 (cloud, dimension) segments per reduction");
   ReduceState& rs = ctx->rs;
   cudaStream_t st = ctx->stream;
   const int64_t m = ctx->m;
@@ -2105,9 +2108,6 @@ void reduce_init(ph_ctx* ctx) {
   rs.owner = alloc_n<int32_t>(ctx, m);
   rs.tab = alloc_n<int32_t>(ctx, 2 * std::max<int64_t>(m, 1));  // two alternating tables
   int nseg = (int)ctx->seg_start.size() - 1;
-  // Phase I's tile states carry a segment in 23 bits
-  PH_REQUIRE(nseg < (1 << 23), PH_ERR_CAPACITY,
-             "at most 8,388,607 (cloud, dimension) segments per reduction");
   rs.first_unp = alloc_n<int32_t>(ctx, 2 * nseg);  // two copies, alternating between passes
   PH_CUDA(cudaMemsetAsync(rs.first_unp, 0x7f, 2 * nseg * sizeof(int32_t), st));  // above every id
   const int64_t ntiles = (m + kFTile - 1) / kFTile;
