@@ -190,3 +190,16 @@ def cubical_grid(w, h, filled):
     colptr = np.concatenate([[0], np.cumsum([len(c[1]) for c in cells])]).astype(np.int64)
     rows = np.array([r for c in cells for r in c[1]], np.int32)
     return dims, colptr, rows
+
+
+def staircase(n):
+    """Columns of dimension 1 over n + 1 rows (dimension 0) whose lows all meet at one row in
+    every pass: column 1 = {n-1, n}, column j = {n-j, n} for j = 2..n. Pass k proves the
+    left-most remaining column and adds it into every later one, which moves their common low
+    down by one: n - 1 passes. Returns (dims, colptr, rows) for a general boundary load."""
+    cols = [[n - 1, n]] + [[n - j, n] for j in range(2, n + 1)]
+    dims = np.array([0] * (n + 1) + [1] * n, np.int32)
+    lengths = np.cumsum([len(c) for c in cols])
+    colptr = np.concatenate([[0] * (n + 2), lengths]).astype(np.int64)
+    rows = np.array([r for c in cols for r in c], np.int32)
+    return dims, colptr, rows

@@ -1007,27 +1007,16 @@ def _addition_cases(seed=5):
     return dims, colptr, rows
 
 
-def _staircase(n):
-    """Columns of dimension 1 over n + 1 rows whose lows all meet at one row each pass, so that
-    Phase I proves one column per pass: column 1 = {n-1, n}, column j = {n-j, n} (j = 2..n).
-    Every addition moves the survivors' common low down by one: n - 1 passes."""
-    cols = [[n - 1, n]] + [[n - j, n] for j in range(2, n + 1)]
-    dims = np.array([0] * (n + 1) + [1] * n, np.int32)
-    lengths = np.cumsum([len(c) for c in cols])
-    colptr = np.concatenate([[0] * (n + 2), lengths]).astype(np.int64)
-    rows = np.array([r for c in cols for r in c], np.int32)
-    return dims, colptr, rows
-
-
 @pytest.mark.parametrize("use_graph", [False, True])
 @pytest.mark.parametrize("arena_words", [0, 1])
 def test_many_passes_counter_rows_and_space_stops(ph, orc, use_graph, arena_words):
     # 299 passes: more than the first 256 rows of per-pass counters, which are grown between
     # two passes; with one-word arenas, passes also stop after their marks for space and continue
     # at Phase II. Lows, pass count and every pass's counters against the oracle.
+    from helpers import staircase
     from oracle import Complex
 
-    dims, cp, rows = _staircase(300)
+    dims, cp, rows = staircase(300)
     m = len(dims)
     K = Complex(dim=dims, diam2=np.zeros(m, np.int64), verts=np.full((m, 4), -1, np.int32),
                 colptr=cp, rows=rows)

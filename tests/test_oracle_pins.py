@@ -21,7 +21,7 @@ import pytest
 import pointclouds as pc
 from helpers import (BUDGET_EXAMPLE, anti_transpose, betti_by_rank, closure, cubical_grid,
                      dense_boundary, gf2_rank, icosahedron_facets, ordered_by_dim_lex,
-                     random_compatible_order, random_reduction, rank_pairing)
+                     random_compatible_order, random_reduction, rank_pairing, staircase)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 pytestmark = pytest.mark.filterwarnings("ignore")
@@ -525,3 +525,31 @@ def test_random_complexes_all_modes_reach_rank_pairing(orc, block):
         Dv = D.astype(np.int64)
         _, _, R, V = orc.reduce_std(K, track_v=True)
         assert np.array_equal((Dv @ V.astype(np.int64)) % 2, R.astype(np.int64)), seed
+
+
+def test_staircase_proves_one_column_per_pass(orc):
+    # A matrix whose lows all meet at one row each pass (Algorithm 2 by hand): pass k proves the
+    # left-most remaining column (Phase I: nothing collides before it) and adds it into the
+    # n - 1 - k later ones, each addition of two 2-row columns sharing their low a union of 3
+    # rows; the reduced column j is {n-j, n-j+1}, so low(column 1) = n and low(column j) =
+    # n - j + 1. Pinned in closed form: the pass count, every pass's pivots, targets, additions
+    # and XORs, and the final lows.
+    from oracle import Complex
+
+    n = 40
+    dims, cp, rows = staircase(n)
+    m = len(dims)
+    K = Complex(dim=dims, diam2=np.zeros(m, np.int64), verts=np.full((m, 4), -1, np.int32),
+                colptr=cp, rows=rows)
+    ref = orc.reduce_pms(K)
+    assert ref.passes == n - 1
+    st = ref.stats[: n - 1]
+    k = np.arange(n - 1)
+    assert np.array_equal(st[:, 1], np.ones(n - 1))        # one new pivot per pass
+    assert np.array_equal(st[:, 5], n - 1 - k)             # targets
+    assert np.array_equal(st[:, 6], n - 1 - k)             # additions
+    assert np.array_equal(st[:, 7], 3 * (n - 1 - k))       # XORs: |src union tgt| = 3
+    assert ref.stats[:, 6].sum() == n * (n - 1) // 2
+    low = np.asarray(ref.low)[n + 1:]
+    assert low[0] == n and np.array_equal(low[1:], n - np.arange(2, n + 1) + 1)
+
