@@ -28,12 +28,24 @@ __host__ __device__ __forceinline__ uint64_t pack_simplex(uint32_t cloud, int k,
 }
 __device__ __forceinline__ uint32_t packed_cloud(uint64_t p) { return (uint32_t)(p >> 48); }
 
-// C(n, k) for the small k of a VR build (k <= 6); exact in int64 for n < 2^12
+// C(n, k) for the small k of a VR build (k <= 6); exact in int64 for n < 2^12. A product of k
+// consecutive integers divided by k!, each case a division by a constant (a multiply and a
+// shift), so the unranking's binary searches carry no run-time 64-bit division
 __host__ __device__ __forceinline__ int64_t binom_small(int64_t n, int k) {
   if (n < k || n < 0 || k < 0) return 0;
-  int64_t r = 1;
-  for (int i = 0; i < k; i++) r = r * (n - i) / (i + 1);  // each prefix is a binomial
-  return r;
+  switch (k) {
+    case 0: return 1;
+    case 1: return n;
+    case 2: return n * (n - 1) / 2;
+    case 3: return n * (n - 1) * (n - 2) / 6;
+    case 4: return n * (n - 1) * (n - 2) * (n - 3) / 24;
+    case 5: return n * (n - 1) * (n - 2) * (n - 3) * (n - 4) / 120;
+    default: {
+      int64_t r = 1;
+      for (int i = 0; i < k; i++) r = r * (n - i) / (i + 1);  // each prefix is a binomial
+      return r;
+    }
+  }
 }
 
 // k-subset of [n] with lexicographic rank r (0-based). Uses the complement map
