@@ -983,6 +983,8 @@ struct __align__(16) WarpStage {
 constexpr int kAddThreads = 128;
 constexpr int kAddWarps = kAddThreads / 32;
 constexpr size_t kAddSmem = sizeof(WarpStage) * kAddWarps;
+// block chunks with shared merge pieces: 64-thread blocks, whose chunk barriers wait on two warps
+constexpr int kPieceBlockThreads = 64;
 // the default switch to 8-slot warp chunks: fewer active columns than this many per warp of the
 // grid. An 8-slot chunk takes about half as long as a 32-slot one, but pays its fixed costs
 // (claim, column records, look-back) on a quarter of the columns: it wins once its chunks fit in
@@ -1330,14 +1332,14 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
 }
 
 // kSlots > 0: the chunk is kSlots (32 or 8) slots of one warp, lanes kSlots.. without a job
-// (warp scan, no block barrier); kSlots = 0: 128 slots of the whole block
-template <bool kDense, int kSlots, bool kLane>
+// (warp scan, no block barrier); kSlots = 0: kBT slots of the whole block of kBT threads
+template <bool kDense, int kSlots, bool kLane, int kBT>
 __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t chunk,
                                           WarpStage& S, int64_t* sh, int64_t* s_prefix,
                                           unsigned long long* s_cnt) {
   constexpr bool kWarp = kSlots > 0;
   const int lane = lane_id();
-  const int64_t e = !kWarp         ? chunk * kAddThreads + threadIdx.x
+  const int64_t e = !kWarp         ? chunk * kBT + threadIdx.x
                     : kSlots == 32 ? chunk * 32 + lane
                                    : (lane < kSlots ? chunk * kSlots + lane : v.n_act);
   Job jb = job_of<kDense>(a, v, e);
@@ -1365,7 +1367,7 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
     constexpr int64_t kWordMask = (int64_t(1) << kRankShift) - 1;
     const int64_t packed = jb.surv ? ((int64_t(1) << kRankShift) | jb.words) : 0;
     int64_t tot;
-    const int64_t excl = block_excl_sum<int64_t, kAddWarps>(packed, sh, tot);
+    const int64_t excl = block_excl_sum<int64_t, kBT / 32>(packed, sh, tot);
     n_surv = tot >> kRankShift;
     if (threadIdx.x == 0) {
       look_publish(a, pass, chunk, n_surv);
@@ -1686,10 +1688,10 @@ __device__ __forceinline__ void add_chunk(const RArgs& a, const PV& v, int64_t c
 // claimed by blocks. kLane: each staged job merged by its own lane (short columns), else merge
 // pieces spread over the lanes. The host picks the variant from DevState::dense_on, warp_on,
 // narrow_on and lane_on (a separate graph for each).
-template <bool kDense, int kSlots, bool kLane>
-__global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
+template <bool kDense, int kSlots, bool kLane, int kBT = kAddThreads>
+__global__ void __launch_bounds__(kBT, 1024 / kBT) k_add(RArgs a) {
   constexpr bool kWarp = kSlots > 0;
-  __shared__ int64_t sh[kAddWarps + 1];
+  __shared__ int64_t sh[kBT / 32 + 1];
   __shared__ int64_t s_chunk;
   __shared__ int64_t s_prefix[2];
   __shared__ unsigned long long s_cnt[kNumCnt];
@@ -1699,7 +1701,7 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
   pdl_trigger();
   if (a.ds->status != ST_RUN) return;
   if (threadIdx.x == 0) s_v = pass_view(a.ds);
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.ds->chunk_slots = kWarp ? kSlots : kAddThreads;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ds->chunk_slots = kWarp ? kSlots : kBT;
   const PV& v = s_v;
   WarpStage& S = reinterpret_cast<WarpStage*>(add_smem)[threadIdx.x >> 5];
   if (threadIdx.x < kNumCnt) s_cnt[threadIdx.x] = 0;
@@ -1711,7 +1713,7 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
       if (lane_id() == 0) chunk = atomicAdd(&a.ds->queue, 1u);
       chunk = __shfl_sync(0xffffffffu, chunk, 0);
       if ((int64_t)chunk >= nchunks) break;
-      add_chunk<kDense, kSlots, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
+      add_chunk<kDense, kSlots, kLane, kBT>(a, v, chunk, S, sh, s_prefix, s_cnt);
     }
     __syncthreads();
   } else {
@@ -1719,10 +1721,10 @@ __global__ void __launch_bounds__(kAddThreads, 8) k_add(RArgs a) {
       if (threadIdx.x == 0) s_chunk = atomicAdd(&a.ds->queue, 1u);
       __syncthreads();  // also publishes s_v, written by thread 0 before the loop
       const int64_t chunk = s_chunk;
-      const int64_t nchunks = (v.n_act + kAddThreads - 1) / kAddThreads;
+      const int64_t nchunks = (v.n_act + kBT - 1) / kBT;
       __syncthreads();
       if (chunk >= nchunks) break;
-      add_chunk<kDense, 0, kLane>(a, v, chunk, S, sh, s_prefix, s_cnt);
+      add_chunk<kDense, 0, kLane, kBT>(a, v, chunk, S, sh, s_prefix, s_cnt);
     }
   }
   if (threadIdx.x == 0 && s_cnt[kCntTargets]) atomicAdd(&a.ds->totals[1], s_cnt[kCntTargets]);
@@ -2061,12 +2063,16 @@ static void launch_pass_rest(ph_ctx* ctx, const RArgs& a, cudaGraphConditionalHa
     PH_CUDA(cudaEventRecord(e0, st));
   }
   static void (*const add_kernels[ReduceState::kAddVariants])(RArgs) = {
-      k_add<false, 0, false>,  k_add<true, 0, false>, k_add<false, 32, false>,
+      k_add<false, 0, false, kPieceBlockThreads>, k_add<true, 0, false, kPieceBlockThreads>,
+      k_add<false, 32, false>,
       k_add<true, 32, false>,  k_add<false, 0, true>, k_add<true, 0, true>,
       k_add<false, 32, true>,  k_add<true, 32, true>, k_add<false, 8, false>,
       k_add<true, 8, false>};
   // (an event recorded between two kernels needs the first one complete: no early start then)
-  launch_k(ctx, !time_add, add_kernels[variant], add_grid_of(ctx), kAddThreads, kAddSmem, st, a);
+  // block chunks with merge pieces (variants 0, 1) in smaller blocks, as many warps per SM
+  const int bt = variant <= 1 ? kPieceBlockThreads : kAddThreads;
+  launch_k(ctx, !time_add, add_kernels[variant], add_grid_of(ctx) * (kAddThreads / bt), bt,
+           sizeof(WarpStage) * (bt / 32), st, a);
   if (time_add) PH_CUDA(cudaEventRecord(rs.ev.back(), st));
   launch_k(ctx, !time_add, k_commit, blocks(sms * 2, kThreads), kThreads, 0, st, a, cond,
            in_graph ? 1 : 0);
@@ -2206,7 +2212,8 @@ void reduce_init(ph_ctx* ctx) {
              a0);
   }
   const void* add_kernels[ReduceState::kAddVariants] = {
-      (const void*)k_add<false, 0, false>,  (const void*)k_add<true, 0, false>,
+      (const void*)k_add<false, 0, false, kPieceBlockThreads>,
+      (const void*)k_add<true, 0, false, kPieceBlockThreads>,
       (const void*)k_add<false, 32, false>, (const void*)k_add<true, 32, false>,
       (const void*)k_add<false, 0, true>,   (const void*)k_add<true, 0, true>,
       (const void*)k_add<false, 32, true>,  (const void*)k_add<true, 32, true>,
