@@ -25,8 +25,9 @@
 //                their place in the next active list by a decoupled look-back and their slot in
 //                the other arena by one atomic per chunk; new pivots move to the pivot store
 //                (their columns never change again). Blocks of 128 threads take 128-slot chunks
-//                from a device work queue, or each warp 32 slots once the list is short and
-//                its jobs long, and 8 slots in the last, short passes. While jobs are short
+//                from a device work queue (64 and 64 once the lanes share merge pieces), or
+//                each warp 32 slots once the list is short and its jobs long, and 8 slots in
+//                the last, short passes. While jobs are short
 //                each lane merges its own job; later the lanes share every job's merge-path
 //                pieces. Ten specialisations (row lists / bitmaps x block / 32-slot warp
 //                chunks x lane / piece merges, and 8-slot warp chunks with pieces); the loop
