@@ -39,7 +39,8 @@ def _from_simplices(orc, simplices):
 
 def _cases(orc):
     """(name, complex, options): Vietoris-Rips clouds, a random filtration of a closed
-    surface, cubical grids, the staircase, and the option grid of Algorithm 2."""
+    surface, a cubical grid, the staircase, degenerate matrices, and the option grid of
+    Algorithm 2."""
     vr3 = orc.vr_build(pc.random_cloud(13, 3, seed=21), 3)
     vr2 = orc.vr_build(pc.random_cloud(18, 3, seed=4), 2)
     ico = _from_simplices(orc, random_compatible_order(
@@ -59,6 +60,9 @@ def _cases(orc):
         ("octahedron", ico, {}),
         ("grid", grid, {}),
         ("staircase", stair, {}),
+        # degenerate: no row can be a low (empty tables), and fewer columns than ranks' work
+        ("vertices_only", _from_simplices(orc, [(v,) for v in range(5)]), {}),
+        ("one_edge", _from_simplices(orc, [(0,), (1,), (0, 1)]), {}),
     ]
 
 
