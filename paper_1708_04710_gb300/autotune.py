@@ -45,6 +45,26 @@ def cache_path() -> Path:
     return Path(p) if p else Path.home() / ".cache" / "ph_gb300" / "autotune.json"
 
 
+def load_cache(path: Path) -> dict:
+    """The cached entries, or none when the file is missing or unreadable."""
+    try:
+        return json.loads(path.read_text())
+    except (OSError, ValueError):
+        return {}
+
+
+def store_entry(path: Path, key: str, entry: dict) -> None:
+    """Adds one entry to the cache file. The file is read again first, so entries that other
+    processes stored meanwhile stay, and replaced in one rename, so no reader sees half of
+    it."""
+    path.parent.mkdir(parents=True, exist_ok=True)
+    cache = load_cache(path)
+    cache[key] = entry
+    tmp = path.with_name(f"{path.name}.{os.getpid()}.tmp")
+    tmp.write_text(json.dumps(cache, indent=1))
+    os.replace(tmp, path)
+
+
 def workload_key(gpu: str, m: int, max_dim: int, n_clouds: int) -> str:
     kind = "batched" if n_clouds > 1 else "single"
     return f"{gpu}|m2^{round(math.log2(max(m, 1)))}|dim{max_dim}|{kind}"
@@ -96,22 +116,15 @@ def tune(coords, offsets=None, max_dim: int = 2, max_diam2: int = -1, use_cache:
     probe.close()
     key = workload_key(gpu, m, max_dim, nc)
     path = cache_path()
-    cache = {}
-    if use_cache and path.exists():
-        try:
-            cache = json.loads(path.read_text())
-        except Exception:
-            cache = {}
+    if use_cache:
         # an entry tuned over other knob values (an older library) is tuned again
-        opts = cache.get(key, {}).get("options")
+        opts = load_cache(path).get(key, {}).get("options")
         if opts and set(opts) == set(KNOBS) and all(opts[k] in v for k, v in KNOBS.items()):
             return dict(opts)
     best, best_t, trials = coordinate_descent(
         lambda o: _time_reduce(torch, coords, offsets, max_dim, max_diam2, o), KNOBS, DEFAULTS,
         verbose)
     if use_cache:
-        cache[key] = {"options": best, "ms": 1e3 * best_t,
-                      "trials": [{"options": o, "ms": 1e3 * t} for o, t in trials]}
-        path.parent.mkdir(parents=True, exist_ok=True)
-        path.write_text(json.dumps(cache, indent=1))
+        store_entry(path, key, {"options": best, "ms": 1e3 * best_t,
+                                "trials": [{"options": o, "ms": 1e3 * t} for o, t in trials]})
     return best

@@ -22,6 +22,21 @@ def test_coordinate_descent_finds_separable_optimum():
     assert len(trials) == 1 + sum(len(v) - 1 for v in KNOBS.values())
 
 
+def test_autotune_cache_keeps_other_entries(tmp_path):
+    from paper_1708_04710_gb300.autotune import load_cache, store_entry
+
+    path = tmp_path / "sub" / "autotune.json"
+    assert load_cache(path) == {}
+    store_entry(path, "a", {"options": {"x": 1}})
+    store_entry(path, "b", {"options": {"x": 2}})  # as another process would, after "a"
+    assert load_cache(path) == {"a": {"options": {"x": 1}}, "b": {"options": {"x": 2}}}
+    path.write_text("{ half a fil")  # unreadable: treated as empty, then replaced whole
+    assert load_cache(path) == {}
+    store_entry(path, "c", {"options": {}})
+    assert load_cache(path) == {"c": {"options": {}}}
+    assert [p.name for p in path.parent.iterdir()] == ["autotune.json"]
+
+
 def test_workload_key_classes():
     from paper_1708_04710_gb300.autotune import workload_key
 
