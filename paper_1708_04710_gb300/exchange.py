@@ -15,10 +15,12 @@ between ranks, and nothing else:
 3. The new pivots, as an elementwise-min allreduce of their low -> column table. From it every
    rank updates its copy of the pivot table and of Paired (Sec. 3.2) and clears the columns it
    holds that are lows of new pivots (Lemma 1, clearing).
-4. Phase II's source columns, fetched into local memory. An all-to-all sends the wanted column
-   indices to the ranks that hold them, and two more return each column's length (-1 when this
-   pass zeroed it, so the addition waits) and its rows.
-5. A sum-allreduce of the pass counters; a pass without targets ends the loop (Sec. 2.3).
+4. Phase II's source columns, fetched into local memory. Two all-to-alls send the request
+   counts and the wanted column indices to the ranks that hold them, and two more return each
+   column's length (-1 when this pass zeroed it, so the addition waits) and its rows.
+5. The end of the loop: a pass without targets anywhere is the last (Sec. 2.3). That test
+   rides on the next pass's first table as one more entry, so a pass takes three
+   min-allreduces and four all-to-alls; the counters of every pass are summed once at the end.
 
 With p < |C| processors (Sec. 3.4.1-3.4.2) the choice of the neighbour sets adds two
 collectives: a max-allreduce of the columns zeroed by the pass and a sum-allreduce of the set
@@ -174,8 +176,9 @@ class PassExchange:
 
 
 class ShardedResult(dict):
-    """passes, stats (one row of N_COUNTERS per pass run), exchange (bytes sent by all ranks
-    per pass: tables, columns), converged."""
+    """passes (the index of the last pass run), stats (one row of N_COUNTERS per pass run,
+    summed over the ranks), exchange (bytes sent by all ranks per pass: tables, columns),
+    converged."""
 
     def __getattr__(self, k):
         return self[k]
@@ -189,28 +192,29 @@ def reduce_sharded(shard: Shard, ex: PassExchange, max_passes: int = 100000,
     passes with additions, one more pass applies its marks and clearing but no additions, as
     an early-stopped reduction does (Sec. 3.3). ``passes`` counts the passes that found
     collisions."""
-    stats, moved = [], []
-    converged = False
-    p = 0
+    rows = []  # this rank's counters and bytes sent, one row per pass
+    had_targets = True
     for p in itertools.count():
         additions = p < max_passes
-        tab = ex.min_merge(shard.leftmost_table())
-        collisions = ex.min_merge(shard.collision_table(tab))
+        # the left-most-column table carries one more entry, 1 on a rank whose previous pass
+        # had no target: its minimum over the ranks is 1 when that pass was the last
+        merged = ex.min_merge(np.append(shard.leftmost_table(), np.int32(not had_targets)))
+        if merged[-1]:
+            rows[-1][N_COUNTERS] += ex.table_bytes
+            break
+        collisions = ex.min_merge(shard.collision_table(merged[:-1]))
         new_pivots = ex.min_merge(shard.marks(collisions))
         zeroed = shard.apply(new_pivots)
         if sets > 0 and additions:
             shard.choose_sets(ex.sum_merge(shard.set_sizes(ex.max_merge(zeroed))))
         shard.add(ex.fetch(shard.wanted_sources(additions), shard.serve), additions)
-        # the counter allreduce below is this pass's last table
-        sent = np.array([ex.table_bytes + 8 * (N_COUNTERS + 2), ex.column_bytes], np.int64)
-        total = ex.sum_merge(np.concatenate([shard.counters(), sent]))
+        counters = shard.counters()
+        had_targets = counters[TARGETS] > 0
+        rows.append(np.concatenate([counters, [ex.table_bytes, ex.column_bytes]]))
         ex.table_bytes = ex.column_bytes = 0
-        stats.append(total[:N_COUNTERS])
-        moved.append(total[N_COUNTERS:])
-        if total[TARGETS] == 0:
-            converged = True
-            break
         if not additions:
             break
-    return ShardedResult(passes=p, stats=np.array(stats, np.int64),
-                         exchange=np.array(moved, np.int64), converged=converged)
+    total = ex.sum_merge(np.array(rows, np.int64))  # every pass's counters in one collective
+    return ShardedResult(passes=len(rows) - 1, stats=total[:, :N_COUNTERS],
+                         exchange=total[:, N_COUNTERS:],
+                         converged=bool(total[-1, TARGETS] == 0))
