@@ -196,9 +196,15 @@ def reduce_sharded(shard: Shard, ex: PassExchange, max_passes: int = 100000,
     had_targets = True
     for p in itertools.count():
         additions = p < max_passes
+        table = shard.leftmost_table()
+        if p == 0:
+            # every rank must hold tables of one length; all of them see the same answer
+            lo, neg_hi = ex.min_merge(np.array([len(table), -len(table)], np.int32))
+            if lo != -neg_hi:
+                raise ValueError(f"ranks disagree on the table length ({lo} to {-neg_hi} rows)")
         # the left-most-column table carries one more entry, 1 on a rank whose previous pass
         # had no target: its minimum over the ranks is 1 when that pass was the last
-        merged = ex.min_merge(np.append(shard.leftmost_table(), np.int32(not had_targets)))
+        merged = ex.min_merge(np.append(table, np.int32(not had_targets)))
         if merged[-1]:
             rows[-1][N_COUNTERS] += ex.table_bytes
             break

@@ -135,3 +135,38 @@ def test_sharded_reduction_equals_oracle_pass_by_pass(orc, world):
         assert moved.shape == (len(ref.stats), 2) and (moved[:, 0] > 0).all(), name
         if ref.converged:
             assert moved[-1, 1] == 8 * world * world, name
+
+
+def _mismatch_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1708_04710_gb300.exchange import NONE, PassExchange, reduce_sharded
+
+    class Lopsided:  # rank 1 counts one row more than rank 0
+        def leftmost_table(self):
+            return np.full(4 + rank, NONE, np.int32)
+
+    try:
+        reduce_sharded(Lopsided(), PassExchange())
+        q.put((rank, "no error"))
+    except ValueError as e:
+        q.put((rank, str(e)))
+    dist.destroy_process_group()
+
+
+def test_ranks_with_unequal_tables_all_raise():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    procs = [ctx.Process(target=_mismatch_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got[0] == got[1] == "ranks disagree on the table length (4 to 5 rows)"
