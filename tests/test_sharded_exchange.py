@@ -1,6 +1,6 @@
 """The single-filtration exchange over gloo ranks on the CPU.
 
-One boundary matrix is dealt round-robin over 2 and 3 ranks. Every rank runs
+One boundary matrix is dealt round-robin over 2, 3 and 4 ranks. Every rank runs
 ``exchange.reduce_sharded`` with the numpy shard of ``shard_cpu.py``, and the ranks meet only in
 the protocol's collectives. The pass counters (all of them, pass by pass), the final low, the
 proven pivots, the Corollary 10 predictions, the essential estimate and the reduced matrix R
@@ -102,7 +102,7 @@ def _run_ranks(world, cases):
     return [got[r] for r in range(world)]
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_sharded_reduction_equals_oracle_pass_by_pass(orc, world):
     cases = [(name, K, orc.beta(K), opts) for name, K, opts in _cases(orc)]
     ranks = _run_ranks(world, cases)
