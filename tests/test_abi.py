@@ -1,6 +1,7 @@
 """The C ABI library builds for sm_103a, loads, and exports exactly what the header declares.
 
-No GPU work is done here: only the shared library's symbol table is inspected.
+No GPU work is done here: only the shared library's symbol table and the sources are
+inspected.
 """
 import ctypes
 import re
@@ -95,3 +96,26 @@ def test_no_alloc_entry_point_source_allocates_nothing():
     # the scratch is a file-scope device array, and host code passes its looked-up address
     assert re.search(r"__device__\s+__align__\(256\)\s+int32_t\s+g_left_scratch\[", code)
     assert "cudaGetSymbolAddress" in code
+
+
+def _code_files(folder: Path):
+    return [p for p in sorted(folder.rglob("*"))
+            if p.suffix in (".py", ".cu", ".cuh", ".h", ".c") and "_build" not in p.parts]
+
+
+def test_product_and_oracle_share_nothing():
+    """The package and the header never import, load or include the oracle, the test tree or
+    working files, and the oracle never uses the package: the two implementations meet only
+    in the tests."""
+    product = _code_files(ROOT / "paper_1708_04710_gb300") + _code_files(ROOT / "include")
+    assert any(p.name == "ph_reduce.cu" for p in product)
+    banned = [r"^\s*(import|from)\s+(oracle|tests|helpers|shard_cpu)\b", r"libph_oracle",
+              r"ph_oracle\.[ch]", r"#\s*include\s*[<\"][^>\"]*oracle", r"\b_work\b"]
+    for p in product:
+        text = p.read_text()
+        for pat in banned:
+            assert not re.search(pat, text, flags=re.M), f"{p.relative_to(ROOT)} matches {pat}"
+    for p in _code_files(ROOT / "oracle"):
+        text = p.read_text()
+        for pat in [r"paper_1708_04710_gb300", r"libph_gb300", r"ph_gb300\.h", r"ph_internal"]:
+            assert not re.search(pat, text), f"{p.relative_to(ROOT)} matches {pat}"
