@@ -108,3 +108,28 @@ def test_two_rank_sharding_over_gloo():
     assert g0 == g1  # both ranks agree on the assignment without exchanging data
     assert sorted(g0[0] + g0[1]) == list(range(64)) and not set(g0[0]) & set(g0[1])
     assert t0 == t1 == 11.0 and w0 == w1 == 64.0
+
+
+def test_kadd_roofline_arithmetic():
+    """The bench's k_add figure: 8 B per nontrivial XOR + 26 B per active column per pass,
+    over CUDA-event time per launch, against the peak; counters and times from fakes."""
+    import bench
+
+    class FakePh:
+        PS_FIELDS = ("active", "xors", "copied")
+
+    class FakeProfile:
+        def pass_stats(self):
+            return np.array([[100, 1000, 5], [50, 500, 0]], np.int64)  # two passes
+
+    rl = bench.kadd_roofline(FakePh, FakeProfile(), lambda: {"add_launches": 4, "ms_add": 2.0},
+                             peak=6000.0, peak_kind="measured", reps=2)
+    nbytes = 2 * (8 * 1500 + 26 * 150)            # two reductions
+    per_launch_s = 2 * 2.0 / 8 / 1e3               # 8 launches in 4 ms
+    achieved = nbytes / 8 / per_launch_s / 1e9
+    assert rl["achieved"] == pytest.approx(achieved)
+    assert rl["frac"] == pytest.approx(achieved / 6000.0)
+    assert rl["bytes_per_launch"] == pytest.approx(nbytes / 8)
+    assert rl["xors_per_reduction"] == 1500 and rl["active_column_passes_per_reduction"] == 150
+    assert rl["copied_row_bytes_per_launch"] == pytest.approx(8 * 10 / 8)  # reported apart
+    assert rl["bound"] == "hbm" and rl["unit"] == "GB/s" and rl["traffic"] is None
