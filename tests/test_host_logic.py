@@ -1,5 +1,6 @@
-"""Host-side logic that needs no GPU: the autotuner's search and cache key, the sharding of the
-batched form, and the multi-rank aggregation of bench timings over gloo (world size 2)."""
+"""Host-side logic that needs no GPU: the autotuner's search, cache key and cache file, the
+sharding of the batched form, the multi-rank aggregation of bench timings over gloo (world size
+2), and the bench's roofline arithmetic."""
 import os
 
 import numpy as np
