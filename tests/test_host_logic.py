@@ -134,3 +134,19 @@ def test_kadd_roofline_arithmetic():
     assert rl["xors_per_reduction"] == 1500 and rl["active_column_passes_per_reduction"] == 150
     assert rl["copied_row_bytes_per_launch"] == pytest.approx(8 * 10 / 8)  # reported apart
     assert rl["bound"] == "hbm" and rl["unit"] == "GB/s" and rl["traffic"] is None
+
+
+def test_clock_samples_parsed():
+    import bench
+
+    lines = ["0, 2070, 2070, 910.5, 0x0000000000000000, Not Active, Not Active, Not Active, "
+             "Not Active\n",
+             "0, 1980, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, "
+             "Active\n",
+             "0, 2040, 2070, 1200.0, 0x0000000000000008, Active, Not Active, Not Active, "
+             "Not Active\n",
+             "garbled line\n"]
+    c = bench.parse_clocks(lines)
+    assert c == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "samples": 3,
+                 "reasons": ["hw_slowdown", "sw_power_cap"]}
+    assert bench.parse_clocks([]) is None
