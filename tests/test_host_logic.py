@@ -1,6 +1,6 @@
 """Host-side logic that needs no GPU: the autotuner's search, cache key and cache file, the
 sharding of the batched form, the multi-rank aggregation of bench timings over gloo (world size
-2), and the bench's roofline arithmetic."""
+2), and the bench's roofline arithmetic and clock-sample parsing."""
 import os
 
 import numpy as np
