@@ -457,7 +457,9 @@ __device__ __forceinline__ void check_capacity(DevState* ds) {
 // at Phase II once the buffers have grown.
 constexpr int kFItems = 4;
 constexpr int kFTile = kThreads * kFItems;
-// tile state word: pass tag (8 bits) | flags (2) | segment (23) | val + 1 (31)
+// tile state word: pass tag (8 bits) | flags (2) | segment (23) | val + 1 (31). Eight bits of
+// tag tell this pass from the previous ones: the active list never grows within a reduction, so
+// a tile in use in pass p was in use, and published, in pass p - 1, and set-up clears every state
 constexpr unsigned long long kTAgg = 1ull << 54, kTIncl = 2ull << 54, kTFlags = 3ull << 54;
 __device__ __forceinline__ unsigned long long tile_word(unsigned long long tag, unsigned long long flag,
                                                        SegMax x) {
